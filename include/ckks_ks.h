@@ -1,0 +1,195 @@
+/*
+ * ckks_ks.h -- C ABI of the GB300 (sm_103a) CKKS key-switching library.
+ *
+ * The calls follow the operations of "Does Fully Homomorphic Encryption Need
+ * Compute Acceleration?" (arXiv 2112.06396): the table "CKKS Subroutines"
+ * (ModDown, ModUp, Decomp, KSKInnerProd, Automorph), Algorithms 1, 3, 4, 6
+ * and 8, and Sec. 5.1 (PModUp).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Ring Z_Q[X]/(X^N+1), N = 2^logN.  A polynomial is limb-major
+ *    uint64_t[nlimbs][N], contiguous, device memory, 16-byte aligned, every
+ *    residue fully reduced in [0, q).
+ *  - ell ("level") counts the limbs of a ciphertext, 1 <= ell <= L.  The
+ *    extended basis at level ell is ordered q_0..q_{ell-1}, p_0..p_{k-1};
+ *    "position t" of an extended polynomial [ell+k][N] is the t-th modulus of
+ *    that list.
+ *  - alpha = ceil(L/dnum) limbs per digit; beta = ceil(ell/alpha) digits at
+ *    level ell; digit j covers chain limbs [j*alpha, min((j+1)*alpha, ell))
+ *    (Decomp, table "CKKS Subroutines"; Table 1 with ell and L counting limbs).
+ *  - Evaluation (NTT) form is the default.  Slot j of the evaluation form of
+ *    a holds a(psi^(2*brv(j)+1)), brv the logN-bit reversal and psi the
+ *    smallest primitive 2N-th root of unity mod q (Sec. 2.3).
+ *  - A key-switching key is uint64_t[dnum][2][L+k][N] in evaluation form:
+ *    [j][0] is a_j (uniform), [j][1] is b_j = -a_j*s + e_j + g_j*s' with
+ *    g_j = [P]_{q_i} on the limbs of digit j and 0 elsewhere (the 2 x dnum key
+ *    of Eq. (kskShape), Sec. 2.4).  Keys are always stored at full level L;
+ *    a call at level ell reads the limbs q_0..q_{ell-1}, p_0..p_{k-1}.
+ *  - A ciphertext is two polynomials (a, b) that decrypt as a*s + b.
+ *  - Ownership: the caller owns every device buffer (inputs, outputs, keys,
+ *    workspace).  The library owns only its context (constant tables).
+ *  - Streams: every device call enqueues work on `stream` and returns without
+ *    synchronising.  Inputs must stay valid until that work completes.
+ *    Outputs must not alias inputs unless a call says so.
+ *  - Workspace: calls taking `ws` need ckks_workspace_bytes() bytes of device
+ *    memory, 16-byte aligned, not shared with concurrently running calls.
+ *  - Errors: CKKS_EINVAL for bad arguments (checked on the host before any
+ *    launch), CKKS_ECUDA when a launch fails (ckks_last_cuda_error() gives the
+ *    cudaError_t).  No call allocates device memory after ckks_ctx_create().
+ */
+#ifndef CKKS_KS_H
+#define CKKS_KS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *ckks_stream_t; /* the same type as cudaStream_t */
+typedef struct ckks_ctx ckks_ctx;
+
+enum {
+    CKKS_OK = 0,
+    CKKS_EINVAL = 1,
+    CKKS_ENOMEM = 2,
+    CKKS_ECUDA = 3,
+    CKKS_EUNSUPPORTED = 4
+};
+
+/* Operation ids for ckks_workspace_bytes(). */
+enum {
+    CKKS_OP_MODUP = 1,
+    CKKS_OP_MODDOWN = 2,
+    CKKS_OP_KEYSWITCH = 3,
+    CKKS_OP_ROTATE = 4,
+    CKKS_OP_HROTATE = 5,
+    CKKS_OP_RESCALE = 6,
+    CKKS_OP_PTMATVEC = 7,
+    CKKS_OP_KEYGEN = 8
+};
+
+typedef struct {
+    int logN;          /* 10 <= logN <= 17 */
+    int L;             /* chain limbs q_0..q_{L-1}, 1 <= L <= 64 */
+    int k;             /* special primes p_0..p_{k-1}, 1 <= k <= 32 */
+    int dnum;          /* key-switching digits, 1 <= dnum <= L */
+    const uint64_t *q; /* host array [L]: distinct primes, q = 1 mod 2N, q < 2^60 */
+    const uint64_t *p; /* host array [k]: distinct primes, p = 1 mod 2N, p < 2^60 */
+} ckks_params;
+
+/* Text for a status code (static storage). */
+const char *ckks_strerror(int status);
+
+/* Host only.  The `count` largest primes q = 1 + m*2N below 2^bits, largest
+ * first, written to the host array out[count].  Chain primes are the first L
+ * of this list and special primes the next k (a reading: the paper fixes no
+ * prime order).  Returns CKKS_EINVAL if bits is outside [20, 60] or too few
+ * primes exist. */
+int ckks_gen_primes(int bits, int logN, int count, uint64_t *out);
+
+/* Create a context on CUDA device `device`: validates the parameters, builds
+ * the twiddle, Shoup and basis-conversion tables on the host and uploads them
+ * (the only device allocation the library makes).  *out receives the handle. */
+int ckks_ctx_create(const ckks_params *params, int device, ckks_ctx **out);
+/* Frees the context's device tables; the caller must have synchronised every
+ * stream that used it. */
+int ckks_ctx_destroy(ckks_ctx *ctx);
+/* cudaError_t of the last failed CUDA call made through this context. */
+int ckks_last_cuda_error(const ckks_ctx *ctx);
+/* Device bytes of the context's constant tables. */
+size_t ckks_ctx_table_bytes(const ckks_ctx *ctx);
+
+/* Workspace bytes the call `op` needs at level ell (r = rotation count for
+ * CKKS_OP_HROTATE, giant-step count for CKKS_OP_PTMATVEC, else ignored). */
+int ckks_workspace_bytes(const ckks_ctx *ctx, int op, int level, int r, size_t *bytes);
+
+/* NTT (Sec. 2.3): in place, coefficient -> evaluation form, on positions
+ * [first, first+count) of an extended polynomial at level ell.  d_poly points
+ * to position 0.  Negacyclic, output in bit-reversed order (see above). */
+int ckks_ntt(ckks_ctx *ctx, uint64_t *d_poly, int level, int first, int count, ckks_stream_t stream);
+/* iNTT: the exact inverse of ckks_ntt (includes the factor N^-1). */
+int ckks_intt(ckks_ctx *ctx, uint64_t *d_poly, int level, int first, int count, ckks_stream_t stream);
+
+/* Automorph (table "CKKS Subroutines"): out = psi_g(in), X -> X^g, on nlimbs
+ * evaluation-form limbs.  g odd, 0 < g < 2N (g = 5^r mod 2N rotates by r
+ * slots, g = 2N-1 conjugates).  d_out must not alias d_in. */
+int ckks_automorph(ckks_ctx *ctx, const uint64_t *d_in, uint64_t *d_out, int nlimbs, uint32_t galois,
+                   ckks_stream_t stream);
+
+/* ModUp of digit `digit` (Algorithm 6): d_a is [ell][N] evaluation form;
+ * d_out receives [ell+k][N] over q_0..q_{ell-1}, p_0..p_{k-1}: the digit's own
+ * limbs copied, every other limb = NTT(sum_i [x_i (Q_j/q_i)^-1]_{q_i} [Q_j/q_i]_t)
+ * with x = iNTT(digit limbs).  Workspace CKKS_OP_MODUP. */
+int ckks_modup(ckks_ctx *ctx, const uint64_t *d_a, int level, int digit, uint64_t *d_out, void *ws,
+               ckks_stream_t stream);
+
+/* KSKInnerProd (table "CKKS Subroutines"): d_digits is [beta][ell+k][N] (the
+ * beta ModUp outputs); u = sum_j digit_j * key[j][0], v = sum_j digit_j *
+ * key[j][1], both [ell+k][N]. */
+int ckks_ksk_inner_prod(ckks_ctx *ctx, const uint64_t *d_digits, int level, const uint64_t *d_key,
+                        uint64_t *d_u, uint64_t *d_v, ckks_stream_t stream);
+
+/* ModDown by P (table "CKKS Subroutines", rounding as in Sec. 2.4): d_in is
+ * [ell+k][N]; d_out [ell][N] = round(in / P) up to the fast base conversion
+ * error eps in [0, k).  Workspace CKKS_OP_MODDOWN. */
+int ckks_moddown(ckks_ctx *ctx, const uint64_t *d_in, int level, uint64_t *d_out, void *ws,
+                 ckks_stream_t stream);
+
+/* PModUp (Sec. 5.1): d_out [ell+k][N] = P * d_in on q limbs, 0 on p limbs. */
+int ckks_pmodup(ckks_ctx *ctx, const uint64_t *d_in, int level, uint64_t *d_out, ckks_stream_t stream);
+
+/* Rescale = ModDown_{B,1} (Algorithm 1): d_out [ell-1][N] = round(in / q_{ell-1})
+ * exactly, for ell >= 2.  Workspace CKKS_OP_RESCALE. */
+int ckks_rescale(ckks_ctx *ctx, const uint64_t *d_in, int level, uint64_t *d_out, void *ws,
+                 ckks_stream_t stream);
+
+/* KeySwitch (the core of Algorithms 2-4): Decomp -> ModUp every digit ->
+ * KSKInnerProd -> ModDown(u), ModDown(v).  d_a [ell][N]; d_u, d_v [ell][N] with
+ * u*s + v ~= a*s'.  Workspace CKKS_OP_KEYSWITCH. */
+int ckks_keyswitch(ckks_ctx *ctx, const uint64_t *d_a, int level, const uint64_t *d_key, uint64_t *d_u,
+                   uint64_t *d_v, void *ws, ckks_stream_t stream);
+
+/* Rotate (Algorithm 3): automorph (a, b) by g, key-switch a_rot with the key
+ * for psi_g(s) -> s, return (u, v + b_rot).  Workspace CKKS_OP_ROTATE. */
+int ckks_rotate(ckks_ctx *ctx, const uint64_t *d_a, const uint64_t *d_b, int level, uint32_t galois,
+                const uint64_t *d_key, uint64_t *d_oa, uint64_t *d_ob, void *ws, ckks_stream_t stream);
+
+/* HRotate (Algorithm 4): Decomp and ModUp once, then for i < r: automorph the
+ * extended digits by galois[i], KSKInnerProd with d_keys[i], ModDown, add the
+ * automorphed b.  galois, d_keys, d_oa, d_ob are host arrays of length r
+ * (d_keys/d_oa/d_ob hold device pointers).  Workspace CKKS_OP_HROTATE(r). */
+int ckks_hrotate(ckks_ctx *ctx, const uint64_t *d_a, const uint64_t *d_b, int level, int r,
+                 const uint32_t *galois, const uint64_t *const *d_keys, uint64_t *const *d_oa,
+                 uint64_t *const *d_ob, void *ws, ckks_stream_t stream);
+
+/* PtMatVecMult with hoisted ModUp and ModDown (Algorithm 8) in baby-step /
+ * giant-step form (Sec. 5.2): nb baby steps, ng giant steps, diagonal (t, i) =
+ * d_diag[t*nb + i], an [ell+k][N] evaluation-form plaintext over the extended
+ * basis.  Baby step 0 and giant step 0 are the identity: g_baby[0],
+ * key_baby[0], g_giant[0], key_giant[0] are ignored.  For each giant step t:
+ * acc = sum_i diag(t,i) * (u_i, v_i + PModUp(psi_{g_i}(b))) over the extended
+ * basis, (c_a, c_b) = ModDown(acc), rotated by g_giant[t] (Algorithm 3) when
+ * t > 0; the sum over t is rescaled by q_{ell-1} when rescale != 0.  Output
+ * [ell'][N] with ell' = ell-1 if rescale else ell.  All arrays are host
+ * arrays of device pointers / values.  Workspace CKKS_OP_PTMATVEC(ng). */
+int ckks_ptmatvecmult(ckks_ctx *ctx, const uint64_t *d_a, const uint64_t *d_b, int level, int nb, int ng,
+                      const uint32_t *g_baby, const uint32_t *g_giant, const uint64_t *const *key_baby,
+                      const uint64_t *const *key_giant, const uint64_t *const *d_diag, int rescale,
+                      uint64_t *d_oa, uint64_t *d_ob, void *ws, ckks_stream_t stream);
+
+/* Key generation (Eq. (kskShape), Sec. 2.4): writes d_key [dnum][2][L+k][N].
+ * d_s: int64 [N] secret coefficients; d_e: int64 [dnum][N] error
+ * coefficients; d_a: [dnum][L+k][N] uniform evaluation-form residues.
+ * galois = 0 makes a relinearisation key (s' = s^2); otherwise s' = psi_g(s),
+ * a rotation key for Rotate/HRotate with that g.  Workspace CKKS_OP_KEYGEN. */
+int ckks_keygen_ksk(ckks_ctx *ctx, const int64_t *d_s, const int64_t *d_e, const uint64_t *d_a, uint32_t galois,
+                    uint64_t *d_key, void *ws, ckks_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CKKS_KS_H */

@@ -1,0 +1,268 @@
+"""Thin ctypes binding of the C ABI in include/ckks_ks.h.
+
+Argument marshalling only: every step of the key-switching path runs in the
+CUDA kernels of libckks_ks.so.  PyTorch supplies device memory (uint64 tensors)
+and streams.  There is no CPU fallback: if the library is missing, importing
+the binding raises.
+
+The module-level functions carry the C names (``ckks_ntt`` ...); the
+:class:`Context` class wraps a context handle and allocates workspace with
+torch.  All tensors are torch.uint64, contiguous, limb-major [nlimbs][N] on the
+context's device.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_lib = None
+
+CKKS_OK, CKKS_EINVAL, CKKS_ENOMEM, CKKS_ECUDA, CKKS_EUNSUPPORTED = 0, 1, 2, 3, 4
+OP_MODUP, OP_MODDOWN, OP_KEYSWITCH, OP_ROTATE, OP_HROTATE, OP_RESCALE, OP_PTMATVEC, OP_KEYGEN = range(1, 9)
+
+
+class CkksError(RuntimeError):
+    pass
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("logN", _i), ("L", _i), ("k", _i), ("dnum", _i), ("q", _u64p), ("p", _u64p)]
+
+
+_SIGS = {
+    "ckks_strerror": (ctypes.c_char_p, [_i]),
+    "ckks_gen_primes": (_i, [_i, _i, _i, _u64p]),
+    "ckks_ctx_create": (_i, [ctypes.POINTER(_Params), _i, ctypes.POINTER(_vp)]),
+    "ckks_ctx_destroy": (_i, [_vp]),
+    "ckks_last_cuda_error": (_i, [_vp]),
+    "ckks_ctx_table_bytes": (ctypes.c_size_t, [_vp]),
+    "ckks_workspace_bytes": (_i, [_vp, _i, _i, _i, ctypes.POINTER(ctypes.c_size_t)]),
+    "ckks_ntt": (_i, [_vp, _vp, _i, _i, _i, _vp]),
+    "ckks_intt": (_i, [_vp, _vp, _i, _i, _i, _vp]),
+    "ckks_automorph": (_i, [_vp, _vp, _vp, _i, ctypes.c_uint32, _vp]),
+    "ckks_modup": (_i, [_vp, _vp, _i, _i, _vp, _vp, _vp]),
+    "ckks_ksk_inner_prod": (_i, [_vp, _vp, _i, _vp, _vp, _vp, _vp]),
+    "ckks_moddown": (_i, [_vp, _vp, _i, _vp, _vp, _vp]),
+    "ckks_pmodup": (_i, [_vp, _vp, _i, _vp, _vp]),
+    "ckks_rescale": (_i, [_vp, _vp, _i, _vp, _vp, _vp]),
+    "ckks_keyswitch": (_i, [_vp, _vp, _i, _vp, _vp, _vp, _vp, _vp]),
+    "ckks_rotate": (_i, [_vp, _vp, _vp, _i, ctypes.c_uint32, _vp, _vp, _vp, _vp, _vp]),
+    "ckks_hrotate": (_i, [_vp, _vp, _vp, _i, _i, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(_vp),
+                          ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp, _vp]),
+    "ckks_ptmatvecmult": (_i, [_vp, _vp, _vp, _i, _i, _i, ctypes.POINTER(ctypes.c_uint32),
+                               ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                               ctypes.POINTER(_vp), _i, _vp, _vp, _vp, _vp]),
+    "ckks_keygen_ksk": (_i, [_vp, _vp, _vp, _vp, ctypes.c_uint32, _vp, _vp, _vp]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libckks_ks.so (built in-tree by ``build.build()``); raise if absent."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise CkksError(f"{path} is missing: run paper_2112_06396_gb300.build.build() (needs nvcc)")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(rc, ctx=None):
+    if rc != CKKS_OK:
+        msg = lib().ckks_strerror(rc).decode()
+        if ctx is not None and rc == CKKS_ECUDA:
+            msg += f" (cudaError {lib().ckks_last_cuda_error(ctx)})"
+        raise CkksError(msg)
+
+
+def _p(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def ckks_gen_primes(bits: int, logN: int, count: int) -> list[int]:
+    out = (ctypes.c_uint64 * count)()
+    _check(lib().ckks_gen_primes(bits, logN, count, out))
+    return [int(x) for x in out]
+
+
+class Context:
+    """One parameter set on one device: N = 2^logN, chain q (L primes),
+    special primes p (k primes), dnum digits."""
+
+    def __init__(self, logN, q, p, dnum, device=0):
+        self.logN, self.L, self.k, self.dnum = int(logN), len(q), len(p), int(dnum)
+        self.N = 1 << self.logN
+        self.q, self.p = [int(x) for x in q], [int(x) for x in p]
+        self.device = torch.device("cuda", device)
+        qa = (ctypes.c_uint64 * self.L)(*self.q)
+        pa = (ctypes.c_uint64 * self.k)(*self.p)
+        prm = _Params(self.logN, self.L, self.k, self.dnum, ctypes.cast(qa, _u64p), ctypes.cast(pa, _u64p))
+        h = ctypes.c_void_p()
+        _check(lib().ckks_ctx_create(ctypes.byref(prm), device, ctypes.byref(h)))
+        self._h = h
+        self.alpha = (self.L + self.dnum - 1) // self.dnum
+
+    @classmethod
+    def from_bits(cls, logN, L, k, dnum, bits, device=0):
+        primes = ckks_gen_primes(bits, logN, L + k)
+        return cls(logN, primes[:L], primes[L:], dnum, device)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ckks_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def beta(self, ell):
+        return (ell + self.alpha - 1) // self.alpha
+
+    def ext_primes(self, ell):
+        return self.q[:ell] + self.p
+
+    def table_bytes(self):
+        return int(lib().ckks_ctx_table_bytes(self._h))
+
+    # ------------------------------------------------------------ memory
+    def empty(self, nlimbs):
+        return torch.empty((nlimbs, self.N), dtype=torch.uint64, device=self.device)
+
+    def workspace_bytes(self, op, level, r=1):
+        n = ctypes.c_size_t()
+        _check(lib().ckks_workspace_bytes(self._h, op, level, r, ctypes.byref(n)))
+        return int(n.value)
+
+    def workspace(self, op, level, r=1):
+        nbytes = self.workspace_bytes(op, level, r)
+        return torch.empty((max(nbytes, 16) + 7) // 8, dtype=torch.uint64, device=self.device)
+
+    # ------------------------------------------------------------ operations
+    def ntt(self, x, level, first=0, count=None, stream=None):
+        count = x.shape[0] - first if count is None else count
+        _check(lib().ckks_ntt(self._h, _p(x), level, first, count, _stream(stream)), self._h)
+        return x
+
+    def intt(self, x, level, first=0, count=None, stream=None):
+        count = x.shape[0] - first if count is None else count
+        _check(lib().ckks_intt(self._h, _p(x), level, first, count, _stream(stream)), self._h)
+        return x
+
+    def automorph(self, x, galois, out=None, stream=None):
+        out = torch.empty_like(x) if out is None else out
+        _check(lib().ckks_automorph(self._h, _p(x), _p(out), x.shape[0], galois, _stream(stream)), self._h)
+        return out
+
+    def modup(self, a, level, digit, out=None, ws=None, stream=None):
+        out = self.empty(level + self.k) if out is None else out
+        ws = self.workspace(OP_MODUP, level) if ws is None else ws
+        _check(lib().ckks_modup(self._h, _p(a), level, digit, _p(out), _p(ws), _stream(stream)), self._h)
+        return out
+
+    def ksk_inner_prod(self, digits, level, key, u=None, v=None, stream=None):
+        u = self.empty(level + self.k) if u is None else u
+        v = self.empty(level + self.k) if v is None else v
+        _check(lib().ckks_ksk_inner_prod(self._h, _p(digits), level, _p(key), _p(u), _p(v), _stream(stream)),
+               self._h)
+        return u, v
+
+    def moddown(self, x, level, out=None, ws=None, stream=None):
+        out = self.empty(level) if out is None else out
+        ws = self.workspace(OP_MODDOWN, level) if ws is None else ws
+        _check(lib().ckks_moddown(self._h, _p(x), level, _p(out), _p(ws), _stream(stream)), self._h)
+        return out
+
+    def pmodup(self, x, level, out=None, stream=None):
+        out = self.empty(level + self.k) if out is None else out
+        _check(lib().ckks_pmodup(self._h, _p(x), level, _p(out), _stream(stream)), self._h)
+        return out
+
+    def rescale(self, x, level, out=None, ws=None, stream=None):
+        out = self.empty(level - 1) if out is None else out
+        ws = self.workspace(OP_RESCALE, level) if ws is None else ws
+        _check(lib().ckks_rescale(self._h, _p(x), level, _p(out), _p(ws), _stream(stream)), self._h)
+        return out
+
+    def keyswitch(self, a, level, key, u=None, v=None, ws=None, stream=None):
+        u = self.empty(level) if u is None else u
+        v = self.empty(level) if v is None else v
+        ws = self.workspace(OP_KEYSWITCH, level) if ws is None else ws
+        _check(lib().ckks_keyswitch(self._h, _p(a), level, _p(key), _p(u), _p(v), _p(ws), _stream(stream)), self._h)
+        return u, v
+
+    def rotate(self, a, b, level, galois, key, oa=None, ob=None, ws=None, stream=None):
+        oa = self.empty(level) if oa is None else oa
+        ob = self.empty(level) if ob is None else ob
+        ws = self.workspace(OP_ROTATE, level) if ws is None else ws
+        _check(lib().ckks_rotate(self._h, _p(a), _p(b), level, galois, _p(key), _p(oa), _p(ob), _p(ws),
+                                 _stream(stream)), self._h)
+        return oa, ob
+
+    def hrotate(self, a, b, level, galois, keys, outs=None, ws=None, stream=None):
+        r = len(galois)
+        if outs is None:
+            outs = [(self.empty(level), self.empty(level)) for _ in range(r)]
+        ws = self.workspace(OP_HROTATE, level, r) if ws is None else ws
+        g = (ctypes.c_uint32 * r)(*galois)
+        kp = (_vp * r)(*[k.data_ptr() for k in keys])
+        oa = (_vp * r)(*[o[0].data_ptr() for o in outs])
+        ob = (_vp * r)(*[o[1].data_ptr() for o in outs])
+        _check(lib().ckks_hrotate(self._h, _p(a), _p(b), level, r, g, kp, oa, ob, _p(ws), _stream(stream)), self._h)
+        return outs
+
+    def ptmatvecmult(self, a, b, level, nb, ng, g_baby, g_giant, key_baby, key_giant, diags, rescale=True,
+                     oa=None, ob=None, ws=None, stream=None):
+        out_l = level - 1 if rescale else level
+        oa = self.empty(out_l) if oa is None else oa
+        ob = self.empty(out_l) if ob is None else ob
+        ws = self.workspace(OP_PTMATVEC, level, ng) if ws is None else ws
+        gb = (ctypes.c_uint32 * nb)(*[int(x) for x in g_baby])
+        gg = (ctypes.c_uint32 * ng)(*[int(x) for x in g_giant])
+        kb = (_vp * nb)(*[None if k is None else k.data_ptr() for k in key_baby])
+        kg = (_vp * ng)(*[None if k is None else k.data_ptr() for k in key_giant])
+        dp = (_vp * (nb * ng))(*[d.data_ptr() for d in diags])
+        _check(lib().ckks_ptmatvecmult(self._h, _p(a), _p(b), level, nb, ng, gb, gg, kb, kg, dp, int(bool(rescale)),
+                                       _p(oa), _p(ob), _p(ws), _stream(stream)), self._h)
+        return oa, ob
+
+    def keygen_ksk(self, s, e, a, galois, key=None, ws=None, stream=None):
+        """s: int64 [N]; e: int64 [dnum][N]; a: uint64 [dnum][L+k][N]; galois 0 = relinearisation."""
+        key = torch.empty((self.dnum, 2, self.L + self.k, self.N), dtype=torch.uint64,
+                          device=self.device) if key is None else key
+        ws = self.workspace(OP_KEYGEN, 1) if ws is None else ws
+        _check(lib().ckks_keygen_ksk(self._h, _p(s), _p(e), _p(a), galois, _p(key), _p(ws), _stream(stream)),
+               self._h)
+        return key

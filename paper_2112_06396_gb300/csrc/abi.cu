@@ -1,0 +1,809 @@
+// abi.cu -- the C ABI (include/ckks_ks.h): context construction (host-side
+// constant tables, uploaded once) and the orchestration of the key-switching
+// operations as sequences of kernel launches on the caller's stream.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/ckks_ks.h"
+#include "common.cuh"
+#include "internal.h"
+
+using namespace ckks;
+
+typedef unsigned __int128 u128;
+
+// ------------------------------------------------------------------ host arithmetic
+static u64 hmul(u64 a, u64 b, u64 m) { return u64((u128)a * b % m); }
+static u64 hpow(u64 a, u64 e, u64 m) {
+    u64 r = 1 % m;
+    a %= m;
+    for (; e; e >>= 1) {
+        if (e & 1) r = hmul(r, a, m);
+        a = hmul(a, a, m);
+    }
+    return r;
+}
+static u64 hinv(u64 a, u64 p) { return hpow(a % p, p - 2, p); }  // p prime (Fermat)
+static u64 shoup_of(u64 w, u64 p) { return u64(((u128)w << 64) / p); }
+
+// Miller-Rabin with the seven bases of Sinclair (deterministic below 2^64).
+static bool strong_probable_prime(u64 n, u64 a) {
+    a %= n;
+    if (a == 0) return true;
+    u64 d = n - 1;
+    int s = 0;
+    while (!(d & 1)) {
+        d >>= 1;
+        ++s;
+    }
+    u64 x = hpow(a, d, n);
+    if (x == 1 || x == n - 1) return true;
+    for (int r = 1; r < s; ++r) {
+        x = hmul(x, x, n);
+        if (x == n - 1) return true;
+    }
+    return false;
+}
+static bool is_prime_u64(u64 n) {
+    if (n < 2) return false;
+    for (u64 sp : {2ull, 3ull, 5ull, 7ull, 11ull, 13ull}) {
+        if (n % sp == 0) return n == sp;
+    }
+    for (u64 a : {2ull, 325ull, 9375ull, 28178ull, 450775ull, 9780504ull, 1795265022ull})
+        if (!strong_probable_prime(n, a)) return false;
+    return true;
+}
+
+// Smallest primitive 2N-th root of unity mod q.
+static u64 min_root(u64 q, int logN) {
+    const u64 N = u64(1) << logN;
+    u64 g = 0;
+    for (u64 x = 2;; ++x) {
+        u64 c = hpow(x, (q - 1) >> (logN + 1), q);
+        if (hpow(c, N, q) == q - 1) {
+            g = c;
+            break;
+        }
+    }
+    u64 best = g, cur = g;
+    const u64 g2 = hmul(g, g, q);
+    for (u64 i = 1; i < N; ++i) {
+        cur = hmul(cur, g2, q);
+        best = std::min(best, cur);
+    }
+    return best;
+}
+
+static uint32_t bitrev(uint32_t x, int bits) {
+    uint32_t r = 0;
+    for (int i = 0; i < bits; ++i) r |= ((x >> i) & 1u) << (bits - 1 - i);
+    return r;
+}
+
+extern "C" const char *ckks_strerror(int s) {
+    switch (s) {
+    case CKKS_OK: return "ok";
+    case CKKS_EINVAL: return "invalid argument";
+    case CKKS_ENOMEM: return "out of device memory";
+    case CKKS_ECUDA: return "CUDA error (see ckks_last_cuda_error)";
+    case CKKS_EUNSUPPORTED: return "unsupported parameters";
+    default: return "unknown status";
+    }
+}
+
+extern "C" int ckks_gen_primes(int bits, int logN, int count, uint64_t *out) {
+    if (bits < 20 || bits > 60 || logN < 1 || logN > 20 || count < 0 || (count > 0 && out == nullptr))
+        return CKKS_EINVAL;
+    const u64 step = u64(2) << logN;
+    u64 q = ((u64(1) << bits) - 2) / step * step + 1;  // largest 1 + m*2N below 2^bits
+    int got = 0;
+    for (; got < count && q > step; q -= step)
+        if (is_prime_u64(q)) out[got++] = q;
+    return got == count ? CKKS_OK : CKKS_EINVAL;
+}
+
+// ------------------------------------------------------------------ context
+static size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+static void fill_plan(BConvPlan &pl) { std::memset(&pl, 0, sizeof(pl)); }
+
+extern "C" int ckks_ctx_create(const ckks_params *prm, int device, ckks_ctx **out) {
+    if (prm == nullptr || out == nullptr || prm->q == nullptr || prm->p == nullptr) return CKKS_EINVAL;
+    const int logN = prm->logN, L = prm->L, k = prm->k, dnum = prm->dnum;
+    if (logN < 10 || logN > 17 || L < 1 || L > 64 || k < 1 || k > kMaxSrc || L + k > kMaxLimbs || dnum < 1 ||
+        dnum > L)
+        return CKKS_EINVAL;
+    const int alpha = (L + dnum - 1) / dnum;
+    if (alpha > kMaxSrc) return CKKS_EUNSUPPORTED;
+    const u64 N = u64(1) << logN;
+    std::vector<u64> primes(prm->q, prm->q + L);
+    primes.insert(primes.end(), prm->p, prm->p + k);
+    for (size_t i = 0; i < primes.size(); ++i) {
+        const u64 q = primes[i];
+        if (q >= (u64(1) << 60) || q % (2 * N) != 1 || !is_prime_u64(q)) return CKKS_EINVAL;
+        for (size_t j = 0; j < i; ++j)
+            if (primes[j] == q) return CKKS_EINVAL;
+    }
+    ckks_ctx *c = new (std::nothrow) ckks_ctx();
+    if (!c) return CKKS_ENOMEM;
+    c->device = device;
+    c->logN = logN;
+    c->N = int(N);
+    c->L = L;
+    c->k = k;
+    c->dnum = dnum;
+    c->alpha = alpha;
+    c->primes = primes;
+    c->last_cuda_error = 0;
+    const int LK = L + k;
+
+    // ---- host tables
+    std::vector<PrimeInfo> pinfo(LK);
+    std::vector<ulonglong2> twf(size_t(LK) * N), twi(size_t(LK) * N);
+    for (int e = 0; e < LK; ++e) {
+        const u64 q = primes[e];
+        const u64 psi = min_root(q, logN), ipsi = hinv(psi, q);
+        std::vector<u64> pw(N), ipw(N);
+        pw[0] = ipw[0] = 1;
+        for (u64 i = 1; i < N; ++i) {
+            pw[i] = hmul(pw[i - 1], psi, q);
+            ipw[i] = hmul(ipw[i - 1], ipsi, q);
+        }
+        for (u64 i = 0; i < N; ++i) {
+            const u64 w = pw[bitrev(uint32_t(i), logN)], iw = ipw[bitrev(uint32_t(i), logN)];
+            twf[size_t(e) * N + i] = make_ulonglong2(w, shoup_of(w, q));
+            twi[size_t(e) * N + i] = make_ulonglong2(iw, shoup_of(iw, q));
+        }
+        PrimeInfo &P = pinfo[e];
+        P.p = q;
+        P.r64 = u64(((u128)1 << 64) % q);
+        P.r64_s = shoup_of(P.r64, q);
+        P.one_s = shoup_of(1, q);
+        P.ninv = hinv(N % q, q);
+        P.ninv_s = shoup_of(P.ninv, q);
+        P.ninv_w = hmul(P.ninv, twi[size_t(e) * N + 1].x, q);
+        P.ninv_w_s = shoup_of(P.ninv_w, q);
+    }
+    auto prod_mod = [&](int lo, int hi, int skip, u64 m) {
+        u64 r = 1 % m;
+        for (int i = lo; i < hi; ++i)
+            if (i != skip) r = hmul(r, primes[i] % m, m);
+        return r;
+    };
+    auto ext_p = [&](int ell, int t) { return t < ell ? t : L + (t - ell); };
+
+    // ModUp plans (ell, j)
+    std::vector<BConvPlan> modup(size_t(L + 1) * dnum);
+    for (auto &pl : modup) fill_plan(pl);
+    for (int ell = 1; ell <= L; ++ell) {
+        const int beta = (ell + alpha - 1) / alpha;
+        for (int j = 0; j < beta; ++j) {
+            BConvPlan &pl = modup[size_t(ell) * dnum + j];
+            const int lo = j * alpha, hi = std::min(lo + alpha, ell);
+            pl.n_src = hi - lo;
+            for (int i = 0; i < pl.n_src; ++i) {
+                const u64 qi = primes[lo + i];
+                pl.src_prime[i] = uint16_t(lo + i);
+                pl.src_add[i] = 0;
+                pl.src_mul[i] = hinv(prod_mod(lo, hi, lo + i, qi), qi);
+                pl.src_mul_s[i] = shoup_of(pl.src_mul[i], qi);
+            }
+            int d = 0;
+            for (int t = 0; t < ell + k; ++t) {
+                if (t >= lo && t < hi) continue;
+                const int pe = ext_p(ell, t);
+                pl.dst_pos[d] = uint16_t(t);
+                pl.dst_prime[d] = uint16_t(pe);
+                pl.dst_sub[d] = 0;
+                for (int i = 0; i < pl.n_src; ++i) pl.mat[d][i] = prod_mod(lo, hi, lo + i, primes[pe]);
+                ++d;
+            }
+            pl.n_dst = d;
+        }
+    }
+    // ModDown plans: P -> q_0..q_{ell-1}, with the rounding constant H = floor(P/2) = (P-1)/2
+    auto halfP = [&](u64 m) { return hmul((prod_mod(L, L + k, -1, m) + m - 1) % m, hinv(2, m), m); };
+    std::vector<BConvPlan> mdown(L + 1), resc(L + 1);
+    for (auto &pl : mdown) fill_plan(pl);
+    for (auto &pl : resc) fill_plan(pl);
+    for (int ell = 1; ell <= L; ++ell) {
+        BConvPlan &pl = mdown[ell];
+        pl.n_src = k;
+        for (int m = 0; m < k; ++m) {
+            const u64 pm = primes[L + m];
+            pl.src_prime[m] = uint16_t(L + m);
+            pl.src_add[m] = halfP(pm);
+            pl.src_mul[m] = hinv(prod_mod(L, L + k, L + m, pm), pm);
+            pl.src_mul_s[m] = shoup_of(pl.src_mul[m], pm);
+        }
+        pl.n_dst = ell;
+        for (int t = 0; t < ell; ++t) {
+            pl.dst_pos[t] = uint16_t(t);
+            pl.dst_prime[t] = uint16_t(t);
+            pl.dst_sub[t] = halfP(primes[t]);
+            for (int m = 0; m < k; ++m) pl.mat[t][m] = prod_mod(L, L + k, L + m, primes[t]);
+        }
+        if (ell >= 2) {
+            BConvPlan &rs = resc[ell];
+            const u64 ql = primes[ell - 1], h = ql / 2;
+            rs.n_src = 1;
+            rs.src_prime[0] = uint16_t(ell - 1);
+            rs.src_add[0] = h;
+            rs.src_mul[0] = 1;
+            rs.src_mul_s[0] = shoup_of(1, ql);
+            rs.n_dst = ell - 1;
+            for (int t = 0; t < ell - 1; ++t) {
+                rs.dst_pos[t] = uint16_t(t);
+                rs.dst_prime[t] = uint16_t(t);
+                rs.dst_sub[t] = h % primes[t];
+                rs.mat[t][0] = 1;
+            }
+        }
+    }
+    std::vector<ulonglong2> Pinv(LK), Pmod(LK), qlinv(size_t(L + 1) * LK);
+    for (int i = 0; i < LK; ++i) {
+        const u64 q = primes[i];
+        const u64 pm = prod_mod(L, L + k, -1, q);
+        Pmod[i] = make_ulonglong2(pm, shoup_of(pm, q));
+        const u64 pinv = pm == 0 ? 0 : hinv(pm, q);
+        Pinv[i] = make_ulonglong2(pinv, shoup_of(pinv, q));
+    }
+    for (int ell = 2; ell <= L; ++ell)
+        for (int i = 0; i < ell - 1; ++i) {
+            const u64 q = primes[i], v = hinv(primes[ell - 1] % q, q);
+            qlinv[size_t(ell) * LK + i] = make_ulonglong2(v, shoup_of(v, q));
+        }
+
+    // ---- one device allocation
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += align_up(bytes);
+        return o;
+    };
+    const size_t o_pinfo = take(sizeof(PrimeInfo) * LK);
+    const size_t o_twf = take(sizeof(ulonglong2) * twf.size());
+    const size_t o_twi = take(sizeof(ulonglong2) * twi.size());
+    const size_t o_modup = take(sizeof(BConvPlan) * modup.size());
+    const size_t o_mdown = take(sizeof(BConvPlan) * mdown.size());
+    const size_t o_resc = take(sizeof(BConvPlan) * resc.size());
+    const size_t o_pinv = take(sizeof(ulonglong2) * LK);
+    const size_t o_pmod = take(sizeof(ulonglong2) * LK);
+    const size_t o_qlinv = take(sizeof(ulonglong2) * qlinv.size());
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaError_t err = cudaSetDevice(device);
+    if (err == cudaSuccess) err = cudaMalloc(&c->d_block, off);
+    if (err != cudaSuccess) {
+        cudaSetDevice(prev);
+        delete c;
+        return err == cudaErrorMemoryAllocation ? CKKS_ENOMEM : CKKS_ECUDA;
+    }
+    char *base = static_cast<char *>(c->d_block);
+    c->table_bytes = off;
+    c->d_pinfo = reinterpret_cast<PrimeInfo *>(base + o_pinfo);
+    c->d_tw_fwd = reinterpret_cast<ulonglong2 *>(base + o_twf);
+    c->d_tw_inv = reinterpret_cast<ulonglong2 *>(base + o_twi);
+    c->d_modup = reinterpret_cast<BConvPlan *>(base + o_modup);
+    c->d_moddown = reinterpret_cast<BConvPlan *>(base + o_mdown);
+    c->d_rescale = reinterpret_cast<BConvPlan *>(base + o_resc);
+    c->d_Pinv = reinterpret_cast<ulonglong2 *>(base + o_pinv);
+    c->d_Pmod = reinterpret_cast<ulonglong2 *>(base + o_pmod);
+    c->d_qlinv = reinterpret_cast<ulonglong2 *>(base + o_qlinv);
+    struct Up {
+        void *dst;
+        const void *src;
+        size_t n;
+    } ups[] = {{c->d_pinfo, pinfo.data(), sizeof(PrimeInfo) * LK},
+               {c->d_tw_fwd, twf.data(), sizeof(ulonglong2) * twf.size()},
+               {c->d_tw_inv, twi.data(), sizeof(ulonglong2) * twi.size()},
+               {c->d_modup, modup.data(), sizeof(BConvPlan) * modup.size()},
+               {c->d_moddown, mdown.data(), sizeof(BConvPlan) * mdown.size()},
+               {c->d_rescale, resc.data(), sizeof(BConvPlan) * resc.size()},
+               {c->d_Pinv, Pinv.data(), sizeof(ulonglong2) * LK},
+               {c->d_Pmod, Pmod.data(), sizeof(ulonglong2) * LK},
+               {c->d_qlinv, qlinv.data(), sizeof(ulonglong2) * qlinv.size()}};
+    for (auto &u : ups)
+        if (err == cudaSuccess) err = cudaMemcpy(u.dst, u.src, u.n, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = ntt_set_attributes(c);
+    cudaSetDevice(prev);
+    if (err != cudaSuccess) {
+        cudaFree(c->d_block);
+        delete c;
+        return CKKS_ECUDA;
+    }
+    *out = c;
+    return CKKS_OK;
+}
+
+extern "C" int ckks_ctx_destroy(ckks_ctx *c) {
+    if (c == nullptr) return CKKS_EINVAL;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(c->device);
+    cudaFree(c->d_block);
+    cudaSetDevice(prev);
+    delete c;
+    return CKKS_OK;
+}
+
+extern "C" int ckks_last_cuda_error(const ckks_ctx *c) { return c ? c->last_cuda_error : 0; }
+extern "C" size_t ckks_ctx_table_bytes(const ckks_ctx *c) { return c ? c->table_bytes : 0; }
+
+// ------------------------------------------------------------------ helpers
+#define CK(call)                                                                                                  \
+    do {                                                                                                          \
+        cudaError_t e_ = (call);                                                                                  \
+        if (e_ != cudaSuccess) {                                                                                  \
+            ctx->last_cuda_error = int(e_);                                                                       \
+            return CKKS_ECUDA;                                                                                    \
+        }                                                                                                         \
+    } while (0)
+#define RC(call)                                                                                                  \
+    do {                                                                                                          \
+        int r_ = (call);                                                                                          \
+        if (r_ != CKKS_OK) return r_;                                                                             \
+    } while (0)
+
+static bool al16(const void *p) { return p != nullptr && (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+static bool level_ok(const ckks_ctx *c, int ell) { return c != nullptr && ell >= 1 && ell <= c->L; }
+static bool galois_ok(const ckks_ctx *c, uint32_t g) { return (g & 1u) && g < uint32_t(2 * c->N); }
+
+// Launch forward (or inverse) NTTs over a list of limbs, in chunks of kMaxBatch.
+struct LimbList {
+    std::vector<const u64 *> src;
+    std::vector<u64 *> dst;
+    std::vector<uint16_t> prime;
+    void add(const u64 *s, u64 *d, int p) {
+        src.push_back(s);
+        dst.push_back(d);
+        prime.push_back(uint16_t(p));
+    }
+};
+static int run_ntt(ckks_ctx *ctx, const LimbList &ll, bool inverse, cudaStream_t st) {
+    const size_t n = ll.src.size();
+    for (size_t b0 = 0; b0 < n; b0 += kMaxBatch) {
+        NttBatch b;
+        b.count = int(std::min(n - b0, size_t(kMaxBatch)));
+        for (int l = 0; l < b.count; ++l) {
+            b.src[l] = ll.src[b0 + l];
+            b.dst[l] = ll.dst[b0 + l];
+            b.prime[l] = ll.prime[b0 + l];
+        }
+        CK(inverse ? launch_ntt_inv(ctx, b, st) : launch_ntt_fwd(ctx, b, nullptr, st));
+    }
+    return CKKS_OK;
+}
+
+static size_t words_modup_all(const ckks_ctx *c, int ell) {
+    return size_t(beta_of(c, ell)) * (ell + c->k) + size_t(ell);
+}
+static size_t words_moddown2(const ckks_ctx *c, int ell) { return size_t(2) * c->k + size_t(2) * ell; }
+
+// ModUp of every digit of a (Algorithm 6 per digit): iNTT -> BConv -> NTT.
+// ext: [beta][ell+k][N] (digit limbs are not written); acoeff: [ell][N] scratch.
+static int modup_all(ckks_ctx *ctx, const u64 *a, int ell, u64 *ext, u64 *acoeff, cudaStream_t st) {
+    const size_t N = ctx->N;
+    const int k = ctx->k, beta = beta_of(ctx, ell), ext_n = ell + k;
+    LimbList inv;
+    for (int i = 0; i < ell; ++i) inv.add(a + i * N, acoeff + i * N, i);
+    RC(run_ntt(ctx, inv, true, st));
+    for (int j0 = 0; j0 < beta; j0 += kMaxGroups) {
+        BConvLaunch l{};
+        l.ngroups = std::min(beta - j0, kMaxGroups);
+        l.chunk = ext_n;
+        l.chunks = 1;
+        for (int g = 0; g < l.ngroups; ++g) {
+            const int j = j0 + g;
+            l.g[g].plan = ctx->d_modup + size_t(ell) * ctx->dnum + j;
+            l.g[g].src = acoeff + size_t(j) * ctx->alpha * N;
+            l.g[g].dst = ext + size_t(j) * ext_n * N;
+        }
+        CK(launch_bconv(ctx, l, std::min(ctx->alpha, ell), st));
+    }
+    LimbList fw;
+    for (int j = 0; j < beta; ++j) {
+        const int lo = j * ctx->alpha, hi = std::min(lo + ctx->alpha, ell);
+        for (int t = 0; t < ext_n; ++t) {
+            if (t >= lo && t < hi) continue;
+            u64 *p = ext + (size_t(j) * ext_n + t) * N;
+            fw.add(p, p, ext_prime(ctx, ell, t));
+        }
+    }
+    return run_ntt(ctx, fw, false, st);
+}
+
+// ModDown of npolys extended polynomials in[p] ([ell+k][N]) to out[p] ([ell][N]):
+// iNTT of the k P-limbs -> BConv P -> q with rounding -> NTT with the
+// (x - w) * P^-1 epilogue; add[p] (read through Automorph_g) and accumulation
+// are folded into the epilogue.  Scratch: pcoeff [npolys*k][N], w [npolys*ell][N].
+static int moddown_polys(ckks_ctx *ctx, int ell, int npolys, const u64 *const in[2], u64 *const out[2],
+                         const u64 *const add[2], uint32_t g, int accumulate, u64 *pcoeff, u64 *w, cudaStream_t st) {
+    const size_t N = ctx->N;
+    const int k = ctx->k;
+    LimbList inv;
+    for (int p = 0; p < npolys; ++p)
+        for (int m = 0; m < k; ++m) inv.add(in[p] + size_t(ell + m) * N, pcoeff + size_t(p * k + m) * N, ctx->L + m);
+    RC(run_ntt(ctx, inv, true, st));
+    BConvLaunch l{};
+    l.ngroups = npolys;
+    l.chunk = ell;
+    l.chunks = 1;
+    for (int p = 0; p < npolys; ++p) {
+        l.g[p].plan = ctx->d_moddown + ell;
+        l.g[p].src = pcoeff + size_t(p) * k * N;
+        l.g[p].dst = w + size_t(p) * ell * N;
+    }
+    CK(launch_bconv(ctx, l, k, st));
+    NttBatch b;
+    b.count = npolys * ell;
+    for (int p = 0; p < npolys; ++p)
+        for (int t = 0; t < ell; ++t) {
+            u64 *q = w + (size_t(p) * ell + t) * N;
+            b.src[p * ell + t] = q;
+            b.dst[p * ell + t] = q;
+            b.prime[p * ell + t] = uint16_t(t);
+        }
+    Epi e{};
+    e.mode = EPI_SCALE;
+    e.nper = ell;
+    for (int p = 0; p < 2; ++p) {
+        e.x[p] = p < npolys ? in[p] : nullptr;
+        e.out[p] = p < npolys ? out[p] : nullptr;
+        e.add[p] = p < npolys ? add[p] : nullptr;
+    }
+    e.galois = g;
+    e.accumulate = accumulate;
+    e.cmul = ctx->d_Pinv;
+    CK(launch_ntt_fwd(ctx, b, &e, st));
+    return CKKS_OK;
+}
+
+// Rescale of npolys polynomials in[p] ([ell][N]) to out[p] ([ell-1][N]).
+// Scratch: c [npolys][N], w [npolys*(ell-1)][N].
+static int rescale_polys(ckks_ctx *ctx, int ell, int npolys, const u64 *const in[2], u64 *const out[2], u64 *c,
+                         u64 *w, cudaStream_t st) {
+    const size_t N = ctx->N;
+    LimbList inv;
+    for (int p = 0; p < npolys; ++p) inv.add(in[p] + size_t(ell - 1) * N, c + size_t(p) * N, ell - 1);
+    RC(run_ntt(ctx, inv, true, st));
+    BConvLaunch l{};
+    l.ngroups = npolys;
+    l.chunk = ell - 1;
+    l.chunks = 1;
+    for (int p = 0; p < npolys; ++p) {
+        l.g[p].plan = ctx->d_rescale + ell;
+        l.g[p].src = c + size_t(p) * N;
+        l.g[p].dst = w + size_t(p) * (ell - 1) * N;
+    }
+    CK(launch_bconv(ctx, l, 1, st));
+    NttBatch b;
+    b.count = npolys * (ell - 1);
+    for (int p = 0; p < npolys; ++p)
+        for (int t = 0; t < ell - 1; ++t) {
+            u64 *q = w + (size_t(p) * (ell - 1) + t) * N;
+            b.src[p * (ell - 1) + t] = q;
+            b.dst[p * (ell - 1) + t] = q;
+            b.prime[p * (ell - 1) + t] = uint16_t(t);
+        }
+    Epi e{};
+    e.mode = EPI_SCALE;
+    e.nper = ell - 1;
+    for (int p = 0; p < 2; ++p) {
+        e.x[p] = p < npolys ? in[p] : nullptr;
+        e.out[p] = p < npolys ? out[p] : nullptr;
+        e.add[p] = nullptr;
+    }
+    e.galois = 1;
+    e.accumulate = 0;
+    e.cmul = ctx->d_qlinv + size_t(ell) * (ctx->L + ctx->k);
+    CK(launch_ntt_fwd(ctx, b, &e, st));
+    return CKKS_OK;
+}
+
+// ---- workspace layouts (in words)
+struct KsLayout {
+    size_t uv, ext, acoeff, pcoeff, w, total;
+};
+static KsLayout ks_layout(const ckks_ctx *c, int ell) {
+    const size_t N = c->N;
+    KsLayout o;
+    const size_t uvw = size_t(2) * (ell + c->k);
+    const size_t r1 = std::max(words_modup_all(c, ell), words_moddown2(c, ell));
+    o.uv = 0;
+    o.ext = uvw * N;
+    o.acoeff = o.ext + size_t(beta_of(c, ell)) * (ell + c->k) * N;
+    o.pcoeff = o.ext;                        // aliases ext: used after the inner product
+    o.w = o.pcoeff + size_t(2) * c->k * N;
+    o.total = (uvw + r1) * N;
+    return o;
+}
+
+// KeySwitch core: ModUp(a), inner product (digits through Automorph_gin), ModDown.
+static int keyswitch_core(ckks_ctx *ctx, const u64 *a, int ell, const u64 *key, uint32_t gin, u64 *out0, u64 *out1,
+                          const u64 *add1, uint32_t gadd, int accumulate, u64 *ws, cudaStream_t st) {
+    const size_t N = ctx->N;
+    const KsLayout lo = ks_layout(ctx, ell);
+    u64 *u = ws + lo.uv, *v = u + size_t(ell + ctx->k) * N;
+    RC(modup_all(ctx, a, ell, ws + lo.ext, ws + lo.acoeff, st));
+    InnerArgs ia{ws + lo.ext, a, key, u, v, ell, gin};
+    CK(launch_inner_prod(ctx, ia, st));
+    const u64 *in[2] = {u, v};
+    u64 *out[2] = {out0, out1};
+    const u64 *add[2] = {nullptr, add1};
+    return moddown_polys(ctx, ell, 2, in, out, add, gadd, accumulate, ws + lo.pcoeff, ws + lo.w, st);
+}
+
+static size_t words_rotate(const ckks_ctx *c, int ell) { return size_t(2) * ell * c->N + ks_layout(c, ell).total; }
+
+// Algorithm 3 with the outputs optionally accumulated into (oa, ob).
+static int rotate_core(ckks_ctx *ctx, const u64 *a, const u64 *b, int ell, uint32_t g, const u64 *key, u64 *oa,
+                       u64 *ob, int accumulate, u64 *ws, cudaStream_t st) {
+    const size_t N = ctx->N;
+    u64 *ar = ws, *br = ws + size_t(ell) * N;
+    CK(launch_automorph(ctx, a, ar, ell, g, st));
+    CK(launch_automorph(ctx, b, br, ell, g, st));
+    return keyswitch_core(ctx, ar, ell, key, 1, oa, ob, br, 1, accumulate, ws + size_t(2) * ell * N, st);
+}
+
+struct HrLayout {
+    size_t ext, uv, tmp, total;
+};
+static HrLayout hr_layout(const ckks_ctx *c, int ell) {
+    const size_t N = c->N;
+    HrLayout o;
+    o.ext = 0;
+    o.uv = size_t(beta_of(c, ell)) * (ell + c->k) * N;
+    o.tmp = o.uv + size_t(2) * (ell + c->k) * N;
+    o.total = o.tmp + std::max(size_t(ell), words_moddown2(c, ell)) * N;
+    return o;
+}
+
+struct PmvLayout {
+    size_t ext, acc, tmp, ct, res, rot, total;
+};
+static PmvLayout pmv_layout(const ckks_ctx *c, int ell, int ng) {
+    const size_t N = c->N;
+    PmvLayout o;
+    o.ext = 0;
+    o.acc = size_t(beta_of(c, ell)) * (ell + c->k) * N;
+    o.tmp = o.acc + size_t(2) * (ell + c->k) * N;
+    o.ct = o.tmp + std::max(size_t(ell), words_moddown2(c, ell)) * N;
+    o.res = o.ct + size_t(2) * ell * N;
+    o.rot = o.res + size_t(2) * ell * N;
+    o.total = o.rot + (ng > 1 ? words_rotate(c, ell) : 0);
+    return o;
+}
+
+extern "C" int ckks_workspace_bytes(const ckks_ctx *c, int op, int ell, int r, size_t *bytes) {
+    if (c == nullptr || bytes == nullptr || !level_ok(c, ell)) return CKKS_EINVAL;
+    const size_t N = c->N;
+    size_t w = 0;
+    switch (op) {
+    case CKKS_OP_MODUP: w = size_t(c->alpha) * N; break;
+    case CKKS_OP_MODDOWN: w = size_t(c->k + ell) * N; break;
+    case CKKS_OP_KEYSWITCH: w = ks_layout(c, ell).total; break;
+    case CKKS_OP_ROTATE: w = words_rotate(c, ell); break;
+    case CKKS_OP_HROTATE: w = hr_layout(c, ell).total; break;
+    case CKKS_OP_RESCALE:
+        if (ell < 2) return CKKS_EINVAL;
+        w = size_t(ell) * N;
+        break;
+    case CKKS_OP_PTMATVEC:
+        if (r < 1) return CKKS_EINVAL;
+        w = pmv_layout(c, ell, r).total;
+        break;
+    case CKKS_OP_KEYGEN: w = size_t(3) * (c->L + c->k) * N; break;
+    default: return CKKS_EINVAL;
+    }
+    *bytes = w * sizeof(u64);
+    return CKKS_OK;
+}
+
+// ------------------------------------------------------------------ API
+extern "C" int ckks_ntt(ckks_ctx *ctx, uint64_t *d, int ell, int first, int count, ckks_stream_t stream) {
+    if (!level_ok(ctx, ell) || !al16(d) || first < 0 || count < 0 || first + count > ell + ctx->k) return CKKS_EINVAL;
+    LimbList ll;
+    for (int t = first; t < first + count; ++t) ll.add(d + size_t(t) * ctx->N, d + size_t(t) * ctx->N, ext_prime(ctx, ell, t));
+    return run_ntt(ctx, ll, false, (cudaStream_t)stream);
+}
+
+extern "C" int ckks_intt(ckks_ctx *ctx, uint64_t *d, int ell, int first, int count, ckks_stream_t stream) {
+    if (!level_ok(ctx, ell) || !al16(d) || first < 0 || count < 0 || first + count > ell + ctx->k) return CKKS_EINVAL;
+    LimbList ll;
+    for (int t = first; t < first + count; ++t) ll.add(d + size_t(t) * ctx->N, d + size_t(t) * ctx->N, ext_prime(ctx, ell, t));
+    return run_ntt(ctx, ll, true, (cudaStream_t)stream);
+}
+
+extern "C" int ckks_automorph(ckks_ctx *ctx, const uint64_t *in, uint64_t *out, int nlimbs, uint32_t g,
+                              ckks_stream_t stream) {
+    if (ctx == nullptr || !al16(in) || !al16(out) || in == out || nlimbs < 0 || nlimbs > 65535 || !galois_ok(ctx, g))
+        return CKKS_EINVAL;
+    CK(launch_automorph(ctx, in, out, nlimbs, g, (cudaStream_t)stream));
+    return CKKS_OK;
+}
+
+extern "C" int ckks_modup(ckks_ctx *ctx, const uint64_t *a, int ell, int digit, uint64_t *out, void *ws,
+                          ckks_stream_t stream) {
+    if (!level_ok(ctx, ell) || !al16(a) || !al16(out) || !al16(ws) || digit < 0 || digit >= beta_of(ctx, ell))
+        return CKKS_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t N = ctx->N;
+    const int lo = digit * ctx->alpha, hi = std::min(lo + ctx->alpha, ell), ext_n = ell + ctx->k;
+    u64 *acoeff = static_cast<u64 *>(ws);
+    LimbList inv;
+    for (int i = lo; i < hi; ++i) inv.add(a + i * N, acoeff + (i - lo) * N, i);
+    RC(run_ntt(ctx, inv, true, st));
+    BConvLaunch l{};
+    l.ngroups = 1;
+    l.chunk = ext_n;
+    l.chunks = 1;
+    l.g[0].plan = ctx->d_modup + size_t(ell) * ctx->dnum + digit;
+    l.g[0].src = acoeff;
+    l.g[0].dst = out;
+    CK(launch_bconv(ctx, l, hi - lo, st));
+    LimbList fw;
+    for (int t = 0; t < ext_n; ++t)
+        if (t < lo || t >= hi) fw.add(out + t * N, out + t * N, ext_prime(ctx, ell, t));
+    RC(run_ntt(ctx, fw, false, st));
+    CK(cudaMemcpyAsync(out + lo * N, a + lo * N, size_t(hi - lo) * N * sizeof(u64), cudaMemcpyDeviceToDevice, st));
+    return CKKS_OK;
+}
+
+extern "C" int ckks_ksk_inner_prod(ckks_ctx *ctx, const uint64_t *digits, int ell, const uint64_t *key, uint64_t *u,
+                                   uint64_t *v, ckks_stream_t stream) {
+    if (!level_ok(ctx, ell) || !al16(digits) || !al16(key) || !al16(u) || !al16(v)) return CKKS_EINVAL;
+    InnerArgs ia{digits, nullptr, key, u, v, ell, 1};
+    CK(launch_inner_prod(ctx, ia, (cudaStream_t)stream));
+    return CKKS_OK;
+}
+
+extern "C" int ckks_moddown(ckks_ctx *ctx, const uint64_t *in, int ell, uint64_t *out, void *ws,
+                            ckks_stream_t stream) {
+    if (!level_ok(ctx, ell) || !al16(in) || !al16(out) || !al16(ws)) return CKKS_EINVAL;
+    u64 *w = static_cast<u64 *>(ws);
+    const u64 *ins[2] = {in, nullptr};
+    u64 *outs[2] = {out, nullptr};
+    const u64 *adds[2] = {nullptr, nullptr};
+    return moddown_polys(ctx, ell, 1, ins, outs, adds, 1, 0, w, w + size_t(ctx->k) * ctx->N, (cudaStream_t)stream);
+}
+
+extern "C" int ckks_pmodup(ckks_ctx *ctx, const uint64_t *in, int ell, uint64_t *out, ckks_stream_t stream) {
+    if (!level_ok(ctx, ell) || !al16(in) || !al16(out)) return CKKS_EINVAL;
+    CK(launch_pmodup(ctx, in, out, ell, (cudaStream_t)stream));
+    return CKKS_OK;
+}
+
+extern "C" int ckks_rescale(ckks_ctx *ctx, const uint64_t *in, int ell, uint64_t *out, void *ws,
+                            ckks_stream_t stream) {
+    if (!level_ok(ctx, ell) || ell < 2 || !al16(in) || !al16(out) || !al16(ws)) return CKKS_EINVAL;
+    u64 *w = static_cast<u64 *>(ws);
+    const u64 *ins[2] = {in, nullptr};
+    u64 *outs[2] = {out, nullptr};
+    return rescale_polys(ctx, ell, 1, ins, outs, w, w + ctx->N, (cudaStream_t)stream);
+}
+
+extern "C" int ckks_keyswitch(ckks_ctx *ctx, const uint64_t *a, int ell, const uint64_t *key, uint64_t *u,
+                              uint64_t *v, void *ws, ckks_stream_t stream) {
+    if (!level_ok(ctx, ell) || !al16(a) || !al16(key) || !al16(u) || !al16(v) || !al16(ws)) return CKKS_EINVAL;
+    return keyswitch_core(ctx, a, ell, key, 1, u, v, nullptr, 1, 0, static_cast<u64 *>(ws), (cudaStream_t)stream);
+}
+
+extern "C" int ckks_rotate(ckks_ctx *ctx, const uint64_t *a, const uint64_t *b, int ell, uint32_t g,
+                           const uint64_t *key, uint64_t *oa, uint64_t *ob, void *ws, ckks_stream_t stream) {
+    if (!level_ok(ctx, ell) || !al16(a) || !al16(b) || !al16(key) || !al16(oa) || !al16(ob) || !al16(ws) ||
+        !galois_ok(ctx, g))
+        return CKKS_EINVAL;
+    return rotate_core(ctx, a, b, ell, g, key, oa, ob, 0, static_cast<u64 *>(ws), (cudaStream_t)stream);
+}
+
+extern "C" int ckks_hrotate(ckks_ctx *ctx, const uint64_t *a, const uint64_t *b, int ell, int r,
+                            const uint32_t *galois, const uint64_t *const *keys, uint64_t *const *oa,
+                            uint64_t *const *ob, void *ws, ckks_stream_t stream) {
+    if (!level_ok(ctx, ell) || !al16(a) || !al16(b) || !al16(ws) || r < 0 || (r > 0 && (!galois || !keys || !oa || !ob)))
+        return CKKS_EINVAL;
+    for (int i = 0; i < r; ++i)
+        if (!galois_ok(ctx, galois[i]) || !al16(keys[i]) || !al16(oa[i]) || !al16(ob[i])) return CKKS_EINVAL;
+    if (r == 0) return CKKS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t N = ctx->N;
+    u64 *w = static_cast<u64 *>(ws);
+    const HrLayout lo = hr_layout(ctx, ell);
+    RC(modup_all(ctx, a, ell, w + lo.ext, w + lo.tmp, st));
+    u64 *u = w + lo.uv, *v = u + size_t(ell + ctx->k) * N;
+    for (int i = 0; i < r; ++i) {
+        InnerArgs ia{w + lo.ext, a, keys[i], u, v, ell, galois[i]};
+        CK(launch_inner_prod(ctx, ia, st));
+        const u64 *in[2] = {u, v};
+        u64 *out[2] = {oa[i], ob[i]};
+        const u64 *add[2] = {nullptr, b};
+        RC(moddown_polys(ctx, ell, 2, in, out, add, galois[i], 0, w + lo.tmp, w + lo.tmp + size_t(2) * ctx->k * N, st));
+    }
+    return CKKS_OK;
+}
+
+extern "C" int ckks_ptmatvecmult(ckks_ctx *ctx, const uint64_t *a, const uint64_t *b, int ell, int nb, int ng,
+                                 const uint32_t *g_baby, const uint32_t *g_giant, const uint64_t *const *key_baby,
+                                 const uint64_t *const *key_giant, const uint64_t *const *diag, int rescale,
+                                 uint64_t *oa, uint64_t *ob, void *ws, ckks_stream_t stream) {
+    if (!level_ok(ctx, ell) || !al16(a) || !al16(b) || !al16(oa) || !al16(ob) || !al16(ws) || nb < 1 ||
+        nb > kMaxRot || ng < 1 || diag == nullptr || (rescale && ell < 2))
+        return CKKS_EINVAL;
+    if (nb > 1 && (g_baby == nullptr || key_baby == nullptr)) return CKKS_EINVAL;
+    if (ng > 1 && (g_giant == nullptr || key_giant == nullptr)) return CKKS_EINVAL;
+    for (int i = 1; i < nb; ++i)
+        if (!galois_ok(ctx, g_baby[i]) || !al16(key_baby[i])) return CKKS_EINVAL;
+    for (int t = 1; t < ng; ++t)
+        if (!galois_ok(ctx, g_giant[t]) || !al16(key_giant[t])) return CKKS_EINVAL;
+    for (int d = 0; d < nb * ng; ++d)
+        if (!al16(diag[d])) return CKKS_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t N = ctx->N;
+    const int k = ctx->k;
+    u64 *w = static_cast<u64 *>(ws);
+    const PmvLayout lo = pmv_layout(ctx, ell, ng);
+    RC(modup_all(ctx, a, ell, w + lo.ext, w + lo.tmp, st));
+    u64 *acc_a = w + lo.acc, *acc_b = acc_a + size_t(ell + k) * N;
+    u64 *res_a = rescale ? w + lo.res : oa, *res_b = rescale ? w + lo.res + size_t(ell) * N : ob;
+    u64 *ct_a = w + lo.ct, *ct_b = ct_a + size_t(ell) * N;
+    for (int t = 0; t < ng; ++t) {
+        PmvArgs pa{};
+        pa.ext = w + lo.ext;
+        pa.a = a;
+        pa.b = b;
+        pa.acc_a = acc_a;
+        pa.acc_b = acc_b;
+        pa.ell = ell;
+        pa.nb = nb;
+        for (int i = 0; i < nb; ++i) {
+            pa.galois[i] = i == 0 ? 1u : g_baby[i];
+            pa.key[i] = i == 0 ? nullptr : key_baby[i];
+            pa.diag[i] = diag[size_t(t) * nb + i];
+        }
+        CK(launch_pmv_accum(ctx, pa, st));
+        const u64 *in[2] = {acc_a, acc_b};
+        const u64 *noadd[2] = {nullptr, nullptr};
+        if (t == 0) {
+            u64 *out[2] = {res_a, res_b};
+            RC(moddown_polys(ctx, ell, 2, in, out, noadd, 1, 0, w + lo.tmp, w + lo.tmp + size_t(2) * k * N, st));
+        } else {
+            u64 *out[2] = {ct_a, ct_b};
+            RC(moddown_polys(ctx, ell, 2, in, out, noadd, 1, 0, w + lo.tmp, w + lo.tmp + size_t(2) * k * N, st));
+            RC(rotate_core(ctx, ct_a, ct_b, ell, g_giant[t], key_giant[t], res_a, res_b, 1, w + lo.rot, st));
+        }
+    }
+    if (rescale) {
+        const u64 *in[2] = {res_a, res_b};
+        u64 *out[2] = {oa, ob};
+        RC(rescale_polys(ctx, ell, 2, in, out, acc_a, acc_a + size_t(2) * N, st));
+    }
+    return CKKS_OK;
+}
+
+extern "C" int ckks_keygen_ksk(ckks_ctx *ctx, const int64_t *s, const int64_t *e, const uint64_t *a, uint32_t g,
+                               uint64_t *key, void *ws, ckks_stream_t stream) {
+    if (ctx == nullptr || !al16(s) || !al16(e) || !al16(a) || !al16(key) || !al16(ws) || (g != 0 && !galois_ok(ctx, g)))
+        return CKKS_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t N = ctx->N;
+    const int LK = ctx->L + ctx->k;
+    u64 *sh = static_cast<u64 *>(ws), *sp = sh + size_t(LK) * N, *eh = sp + size_t(LK) * N;
+    LimbList ls, le;
+    for (int l = 0; l < LK; ++l) {
+        ls.add(sh + l * N, sh + l * N, l);
+        le.add(eh + l * N, eh + l * N, l);
+    }
+    CK(launch_signed_to_res(ctx, s, sh, st));
+    RC(run_ntt(ctx, ls, false, st));
+    if (g != 0) CK(launch_automorph(ctx, sh, sp, LK, g, st));
+    else CK(launch_square(ctx, sh, sp, st));
+    for (int j = 0; j < ctx->dnum; ++j) {
+        CK(launch_signed_to_res(ctx, e + size_t(j) * N, eh, st));
+        RC(run_ntt(ctx, le, false, st));
+        CK(launch_keygen_row(ctx, a + size_t(j) * LK * N, sh, sp, eh, j, key + size_t(2 * j) * LK * N,
+                             key + size_t(2 * j + 1) * LK * N, st));
+    }
+    return CKKS_OK;
+}

@@ -1,0 +1,132 @@
+// common.cuh -- shared device/host definitions of the CKKS key-switching
+// library: per-prime constants, modular arithmetic, launch descriptors.
+//
+// Modular arithmetic (Sec. 2.2, "Scalar Modular Arithmetic"):
+//  * Shoup constant multiplication [Shoup, NTL]: for a constant w < p with
+//    w' = floor(w * 2^64 / p), x*w - umulhi(x, w')*p lies in [0, 2p) for every
+//    64-bit x.  Used for every twiddle and every precomputed constant.
+//  * Lazy reduction: NTT values travel in [0, 4p) (Harvey, "Faster arithmetic
+//    for number-theoretic transforms", J. Symb. Comp. 2014), which needs
+//    4p < 2^64; this library requires p < 2^60.
+//  * Sums of products are accumulated exactly in 128 bits and reduced once at
+//    the end (the paper's "reduce once at the end of a sum").
+//  * The 128-bit reduction writes hi*2^64 + lo = hi*[2^64]_p + lo and reduces
+//    both words with Shoup multiplications (by [2^64]_p and by 1).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+typedef uint64_t u64;
+
+namespace ckks {
+
+constexpr int kMaxLimbs = 96;      // L + k
+constexpr int kMaxSrc = 32;        // limbs per basis-conversion source (alpha, k)
+constexpr int kMaxDst = 96;        // limbs per basis-conversion target set
+constexpr int kMaxBatch = 128;     // limbs per NTT launch
+constexpr int kMaxRot = 64;        // rotations per fused inner-product launch
+
+// Constants of one prime modulus.
+struct PrimeInfo {
+    u64 p;
+    u64 r64, r64_s;        // [2^64]_p and its Shoup companion
+    u64 one_s;             // floor(2^64 / p): Shoup companion of 1
+    u64 ninv, ninv_s;      // [N^-1]_p
+    u64 ninv_w, ninv_w_s;  // [N^-1 * psi^-brv(1)]_p (last inverse stage)
+};
+
+// ------------------------------------------------------------------ device
+__device__ __forceinline__ u64 shoup_lazy(u64 x, u64 w, u64 ws, u64 p) {
+    u64 q = __umul64hi(x, ws);
+    return x * w - q * p;
+}
+__device__ __forceinline__ u64 csub(u64 x, u64 m) { return x >= m ? x - m : x; }
+__device__ __forceinline__ u64 shoup_mul(u64 x, u64 w, u64 ws, u64 p) { return csub(shoup_lazy(x, w, ws, p), p); }
+__device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 p) { return csub(a + b, p); }
+__device__ __forceinline__ u64 sub_mod(u64 a, u64 b, u64 p) { return a >= b ? a - b : a + p - b; }
+
+// (hi:lo) += a*b, exact
+__device__ __forceinline__ void mac128(u64 &lo, u64 &hi, u64 a, u64 b) {
+    asm("mad.lo.cc.u64 %0, %2, %3, %0;\n\t"
+        "madc.hi.u64 %1, %2, %3, %1;"
+        : "+l"(lo), "+l"(hi)
+        : "l"(a), "l"(b));
+}
+
+// (hi:lo) mod p for hi < 2^64 (any value below 2^128)
+__device__ __forceinline__ u64 reduce128(u64 lo, u64 hi, const PrimeInfo &P) {
+    u64 t = shoup_lazy(hi, P.r64, P.r64_s, P.p) + shoup_lazy(lo, 1, P.one_s, P.p);  // < 4p
+    t = csub(t, 2 * P.p);
+    return csub(t, P.p);
+}
+
+__device__ __forceinline__ u64 mul_mod(u64 a, u64 b, const PrimeInfo &P) {
+    u64 lo = 0, hi = 0;
+    mac128(lo, hi, a, b);
+    return reduce128(lo, hi, P);
+}
+
+// Slot permutation of Automorph in bit-reversed evaluation order: output
+// slot j reads input slot brv(((2 brv(j) + 1) * g mod 2N - 1) / 2).
+__device__ __forceinline__ uint32_t automorph_src(uint32_t j, uint32_t g, int logN) {
+    uint32_t rj = __brev(j) >> (32 - logN);
+    uint32_t e = (uint32_t)(((2ull * rj + 1ull) * g) & ((2ull << logN) - 1ull));
+    return __brev((e - 1) >> 1) >> (32 - logN);
+}
+
+// ------------------------------------------------------------------ descriptors
+// A batch of limbs for one NTT launch: limb l reads src[l], writes dst[l]
+// (equal for in-place work) and uses prime table entry prime[l].
+struct NttBatch {
+    int count;
+    const u64 *src[kMaxBatch];
+    u64 *dst[kMaxBatch];
+    uint16_t prime[kMaxBatch];
+};
+
+// Epilogue of the last forward pass.  EPI_STORE writes the transform.
+// EPI_SCALE treats batch limb l as limb (l % nper) of polynomial (l / nper):
+//   out = (x - ntt) * c  [+ add[perm_g(n)]]  [+ out if accumulate]
+// with c = cmul[prime] (value, Shoup companion).  This is the last step of
+// ModDown (c = P^-1) and Rescale (c = q_{ell-1}^-1).
+enum { EPI_STORE = 0, EPI_SCALE = 1 };
+struct Epi {
+    int mode;
+    int nper;
+    const u64 *x[2];
+    u64 *out[2];
+    const u64 *add[2];
+    uint32_t galois;
+    int accumulate;
+    const ulonglong2 *cmul;
+};
+
+// Basis conversion (the NewLimb step of ModUp/ModDown, Algorithm 6 and the
+// table "CKKS Subroutines"): from n_src coefficient-form limbs x_i to n_dst
+// limbs z_t = (sum_i [(x_i + add_i) * mul_i]_{q_i} * mat[t][i] - sub_t) mod t.
+struct BConvPlan {
+    int n_src, n_dst;
+    uint16_t src_prime[kMaxSrc];
+    u64 src_add[kMaxSrc];
+    u64 src_mul[kMaxSrc], src_mul_s[kMaxSrc];
+    uint16_t dst_pos[kMaxDst];
+    uint16_t dst_prime[kMaxDst];
+    u64 dst_sub[kMaxDst];
+    u64 mat[kMaxDst][kMaxSrc];
+};
+
+struct BConvGroup {
+    const BConvPlan *plan;  // device pointer
+    const u64 *src;         // [n_src][N] contiguous
+    u64 *dst;               // limb t written at dst + dst_pos[t]*N
+};
+constexpr int kMaxGroups = 8;
+struct BConvLaunch {
+    int ngroups;
+    int chunks;             // target chunks per group (grid.y = ngroups*chunks)
+    int chunk;              // targets per chunk
+    BConvGroup g[kMaxGroups];
+};
+
+}  // namespace ckks

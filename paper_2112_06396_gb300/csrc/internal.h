@@ -1,0 +1,68 @@
+// internal.h -- the library context and the kernel launchers shared by the
+// translation units (not part of the public C ABI).
+#pragma once
+
+#include <cstddef>
+#include <vector>
+
+#include "common.cuh"
+
+struct ckks_ctx {
+    int device;
+    int logN, N, L, k, dnum, alpha;
+    std::vector<u64> primes;          // L + k: q_0..q_{L-1}, p_0..p_{k-1}
+    // device tables (one allocation)
+    void *d_block;
+    size_t table_bytes;
+    ckks::PrimeInfo *d_pinfo;         // [L+k]
+    ulonglong2 *d_tw_fwd;             // [L+k][N]: psi^brv(i) and Shoup companion
+    ulonglong2 *d_tw_inv;             // [L+k][N]: psi^-brv(i) and Shoup companion
+    ckks::BConvPlan *d_modup;         // [(L+1)*dnum]: plan (ell, digit j) at ell*dnum + j
+    ckks::BConvPlan *d_moddown;       // [L+1]: P -> q_0..q_{ell-1} with rounding
+    ckks::BConvPlan *d_rescale;       // [L+1]: q_{ell-1} -> q_0..q_{ell-2} with rounding
+    ulonglong2 *d_Pinv;               // [L+k]: [P^-1]_{q} (chain entries used)
+    ulonglong2 *d_Pmod;               // [L+k]: [P]_{q}
+    ulonglong2 *d_qlinv;              // [(L+1)*(L+k)]: [q_{ell-1}^-1]_{q_i} at ell*(L+k) + i
+    int last_cuda_error;
+};
+
+namespace ckks {
+
+inline int ext_prime(const ckks_ctx *c, int ell, int pos) { return pos < ell ? pos : c->L + (pos - ell); }
+inline int beta_of(const ckks_ctx *c, int ell) { return (ell + c->alpha - 1) / c->alpha; }
+
+cudaError_t ntt_set_attributes(const ckks_ctx *ctx);
+cudaError_t launch_ntt_fwd(const ckks_ctx *ctx, const NttBatch &b, const Epi *epi, cudaStream_t st);
+cudaError_t launch_ntt_inv(const ckks_ctx *ctx, const NttBatch &b, cudaStream_t st);
+cudaError_t launch_bconv(const ckks_ctx *ctx, const BConvLaunch &l, int max_src, cudaStream_t st);
+
+// keyswitch.cu
+struct InnerArgs {
+    const u64 *ext;      // [beta][ell+k][N] ModUp outputs
+    const u64 *own;      // [ell][N] evaluation-form input whose digit limbs stand in for ext (or null)
+    const u64 *key;      // [dnum][2][L+k][N]
+    u64 *u, *v;          // [ell+k][N]
+    int ell;
+    uint32_t galois;     // 1 = no automorphism
+};
+cudaError_t launch_inner_prod(const ckks_ctx *ctx, const InnerArgs &a, cudaStream_t st);
+
+struct PmvArgs {
+    const u64 *ext;      // hoisted ModUp outputs [beta][ell+k][N]
+    const u64 *a, *b;    // input ciphertext [ell][N]
+    u64 *acc_a, *acc_b;  // [ell+k][N]
+    int ell, nb;
+    uint32_t galois[kMaxRot];
+    const u64 *key[kMaxRot];
+    const u64 *diag[kMaxRot];
+};
+cudaError_t launch_pmv_accum(const ckks_ctx *ctx, const PmvArgs &a, cudaStream_t st);
+
+cudaError_t launch_automorph(const ckks_ctx *ctx, const u64 *in, u64 *out, int nlimbs, uint32_t g, cudaStream_t st);
+cudaError_t launch_pmodup(const ckks_ctx *ctx, const u64 *in, u64 *out, int ell, cudaStream_t st);
+cudaError_t launch_signed_to_res(const ckks_ctx *ctx, const int64_t *c, u64 *out, cudaStream_t st);
+cudaError_t launch_square(const ckks_ctx *ctx, const u64 *in, u64 *out, cudaStream_t st);
+cudaError_t launch_keygen_row(const ckks_ctx *ctx, const u64 *a, const u64 *s, const u64 *sp, const u64 *e, int j,
+                              u64 *row0, u64 *row1, cudaStream_t st);
+
+}  // namespace ckks

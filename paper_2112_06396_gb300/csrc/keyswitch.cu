@@ -1,0 +1,261 @@
+// keyswitch.cu -- KSKInnerProd, Automorph, PModUp, the fused inner loop of
+// PtMatVecMult (Algorithm 8) and the element-wise steps of key generation.
+//
+// Automorph in bit-reversed evaluation order maps every aligned block of 2^m
+// slots onto an aligned block of 2^m slots (the low bits of a slot index only
+// reach the high bits of its evaluation exponent), so a thread that owns the
+// slot pair (2n, 2n+1) reads one aligned source pair, swapped when the image
+// of 2n is odd.  Gathers therefore stay 16-byte vector loads and every warp
+// touches whole 256-byte segments.
+#include "common.cuh"
+#include "internal.h"
+
+namespace ckks {
+
+__device__ __forceinline__ ulonglong2 ld2(const u64 *p) { return *reinterpret_cast<const ulonglong2 *>(p); }
+__device__ __forceinline__ void st2(u64 *p, ulonglong2 v) { *reinterpret_cast<ulonglong2 *>(p) = v; }
+
+// Load the automorphed pair (out slots n0, n0+1) of one limb.
+__device__ __forceinline__ ulonglong2 ld2_perm(const u64 *limb, uint32_t n0, uint32_t g, int logN) {
+    if (g == 1) return ld2(limb + n0);
+    const uint32_t s = automorph_src(n0, g, logN);
+    ulonglong2 v = ld2(limb + (s & ~1u));
+    if (s & 1u) {
+        const u64 t = v.x;
+        v.x = v.y;
+        v.y = t;
+    }
+    return v;
+}
+
+// ------------------------------------------------------------------ KSKInnerProd
+// u_t = sum_{j<beta} d_j[t] * key[j][0][t'], v_t = sum_j d_j[t] * key[j][1][t']
+// (t' = key row of position t), with d_j read through Automorph_g.  The
+// digit's own limbs come from `own` when given (ModUp copies them unchanged).
+__global__ void __launch_bounds__(256) inner_prod_kernel(InnerArgs A, const PrimeInfo *__restrict__ pinfo, int logN,
+                                                         int L, int k, int alpha) {
+    const size_t N = size_t(1) << logN;
+    const uint32_t n0 = (blockIdx.x * blockDim.x + threadIdx.x) * 2;
+    if (n0 >= N) return;
+    const int t = blockIdx.y;
+    const int ell = A.ell, ext = ell + k, LK = L + k;
+    const int beta = (ell + alpha - 1) / alpha;
+    const int prime = t < ell ? t : L + (t - ell);
+    const PrimeInfo P = pinfo[prime];
+    u64 ul0 = 0, uh0 = 0, ul1 = 0, uh1 = 0, vl0 = 0, vh0 = 0, vl1 = 0, vh1 = 0;
+    for (int j = 0; j < beta; j++) {
+        const bool own = (A.own != nullptr) && t < ell && (t / alpha) == j;
+        const u64 *d = own ? A.own + size_t(t) * N : A.ext + (size_t(j) * ext + t) * N;
+        const ulonglong2 dv = ld2_perm(d, n0, A.galois, logN);
+        const ulonglong2 ka = ld2(A.key + ((size_t(j) * 2 + 0) * LK + prime) * N + n0);
+        const ulonglong2 kb = ld2(A.key + ((size_t(j) * 2 + 1) * LK + prime) * N + n0);
+        mac128(ul0, uh0, dv.x, ka.x);
+        mac128(ul1, uh1, dv.y, ka.y);
+        mac128(vl0, vh0, dv.x, kb.x);
+        mac128(vl1, vh1, dv.y, kb.y);
+    }
+    st2(A.u + size_t(t) * N + n0, make_ulonglong2(reduce128(ul0, uh0, P), reduce128(ul1, uh1, P)));
+    st2(A.v + size_t(t) * N + n0, make_ulonglong2(reduce128(vl0, vh0, P), reduce128(vl1, vh1, P)));
+}
+
+cudaError_t launch_inner_prod(const ckks_ctx *ctx, const InnerArgs &a, cudaStream_t st) {
+    const int threads = 256;
+    dim3 grid(unsigned((ctx->N / 2 + threads - 1) / threads), unsigned(a.ell + ctx->k));
+    inner_prod_kernel<<<grid, threads, 0, st>>>(a, ctx->d_pinfo, ctx->logN, ctx->L, ctx->k, ctx->alpha);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ PtMatVecMult inner loop
+// One giant step of Algorithm 8: for every extended position t and slot n,
+//   acc_a = sum_i M_i * u_i,   acc_b = sum_i M_i * (v_i + [P*b_rot,i]),
+// where (u_i, v_i) is the inner product of the hoisted digits automorphed by
+// g_i with key_i, and baby step i = 0 (no key) contributes M_0 * (P*a, P*b).
+// u_i and v_i never leave registers (the beta-limb caching of Sec. 4.2).
+__global__ void __launch_bounds__(256) pmv_accum_kernel(PmvArgs A, const PrimeInfo *__restrict__ pinfo,
+                                                        const ulonglong2 *__restrict__ Pmod, int logN, int L, int k,
+                                                        int alpha) {
+    const size_t N = size_t(1) << logN;
+    const uint32_t n0 = (blockIdx.x * blockDim.x + threadIdx.x) * 2;
+    if (n0 >= N) return;
+    const int t = blockIdx.y;
+    const int ell = A.ell, ext = ell + k, LK = L + k;
+    const int beta = (ell + alpha - 1) / alpha;
+    const int prime = t < ell ? t : L + (t - ell);
+    const PrimeInfo P = pinfo[prime];
+    const ulonglong2 pm = Pmod[prime];
+    u64 al0 = 0, ah0 = 0, al1 = 0, ah1 = 0, bl0 = 0, bh0 = 0, bl1 = 0, bh1 = 0;
+    for (int i = 0; i < A.nb; i++) {
+        const ulonglong2 M = ld2(A.diag[i] + size_t(t) * N + n0);
+        u64 u0, u1, w0, w1;
+        if (A.key[i] == nullptr) {
+            if (t < ell) {
+                const ulonglong2 av = ld2(A.a + size_t(t) * N + n0);
+                const ulonglong2 bv = ld2(A.b + size_t(t) * N + n0);
+                u0 = shoup_mul(av.x, pm.x, pm.y, P.p);
+                u1 = shoup_mul(av.y, pm.x, pm.y, P.p);
+                w0 = shoup_mul(bv.x, pm.x, pm.y, P.p);
+                w1 = shoup_mul(bv.y, pm.x, pm.y, P.p);
+            } else {
+                u0 = u1 = w0 = w1 = 0;
+            }
+        } else {
+            const uint32_t g = A.galois[i];
+            const u64 *key = A.key[i];
+            u64 ul0 = 0, uh0 = 0, ul1 = 0, uh1 = 0, vl0 = 0, vh0 = 0, vl1 = 0, vh1 = 0;
+            for (int j = 0; j < beta; j++) {
+                const bool own = t < ell && (t / alpha) == j;
+                const u64 *d = own ? A.a + size_t(t) * N : A.ext + (size_t(j) * ext + t) * N;
+                const ulonglong2 dv = ld2_perm(d, n0, g, logN);
+                const ulonglong2 ka = ld2(key + ((size_t(j) * 2 + 0) * LK + prime) * N + n0);
+                const ulonglong2 kb = ld2(key + ((size_t(j) * 2 + 1) * LK + prime) * N + n0);
+                mac128(ul0, uh0, dv.x, ka.x);
+                mac128(ul1, uh1, dv.y, ka.y);
+                mac128(vl0, vh0, dv.x, kb.x);
+                mac128(vl1, vh1, dv.y, kb.y);
+            }
+            u0 = reduce128(ul0, uh0, P);
+            u1 = reduce128(ul1, uh1, P);
+            w0 = reduce128(vl0, vh0, P);
+            w1 = reduce128(vl1, vh1, P);
+            if (t < ell) {
+                const ulonglong2 bv = ld2_perm(A.b + size_t(t) * N, n0, g, logN);
+                w0 = add_mod(w0, shoup_mul(bv.x, pm.x, pm.y, P.p), P.p);
+                w1 = add_mod(w1, shoup_mul(bv.y, pm.x, pm.y, P.p), P.p);
+            }
+        }
+        mac128(al0, ah0, M.x, u0);
+        mac128(al1, ah1, M.y, u1);
+        mac128(bl0, bh0, M.x, w0);
+        mac128(bl1, bh1, M.y, w1);
+    }
+    st2(A.acc_a + size_t(t) * N + n0, make_ulonglong2(reduce128(al0, ah0, P), reduce128(al1, ah1, P)));
+    st2(A.acc_b + size_t(t) * N + n0, make_ulonglong2(reduce128(bl0, bh0, P), reduce128(bl1, bh1, P)));
+}
+
+cudaError_t launch_pmv_accum(const ckks_ctx *ctx, const PmvArgs &a, cudaStream_t st) {
+    const int threads = 256;
+    dim3 grid(unsigned((ctx->N / 2 + threads - 1) / threads), unsigned(a.ell + ctx->k));
+    pmv_accum_kernel<<<grid, threads, 0, st>>>(a, ctx->d_pinfo, ctx->d_Pmod, ctx->logN, ctx->L, ctx->k, ctx->alpha);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ Automorph
+__global__ void __launch_bounds__(256) automorph_kernel(const u64 *__restrict__ in, u64 *__restrict__ out, uint32_t g,
+                                                        int logN) {
+    const size_t N = size_t(1) << logN;
+    const uint32_t n0 = (blockIdx.x * blockDim.x + threadIdx.x) * 2;
+    if (n0 >= N) return;
+    const size_t base = size_t(blockIdx.y) * N;
+    st2(out + base + n0, ld2_perm(in + base, n0, g, logN));
+}
+
+cudaError_t launch_automorph(const ckks_ctx *ctx, const u64 *in, u64 *out, int nlimbs, uint32_t g, cudaStream_t st) {
+    if (nlimbs == 0) return cudaSuccess;
+    const int threads = 256;
+    dim3 grid(unsigned((ctx->N / 2 + threads - 1) / threads), unsigned(nlimbs));
+    automorph_kernel<<<grid, threads, 0, st>>>(in, out, g, ctx->logN);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ PModUp (Sec. 5.1)
+__global__ void __launch_bounds__(256) pmodup_kernel(const u64 *__restrict__ in, u64 *__restrict__ out, int ell,
+                                                     const PrimeInfo *__restrict__ pinfo,
+                                                     const ulonglong2 *__restrict__ Pmod, int logN) {
+    const size_t N = size_t(1) << logN;
+    const uint32_t n0 = (blockIdx.x * blockDim.x + threadIdx.x) * 2;
+    if (n0 >= N) return;
+    const int t = blockIdx.y;
+    ulonglong2 r = make_ulonglong2(0, 0);
+    if (t < ell) {
+        const u64 p = pinfo[t].p;
+        const ulonglong2 c = Pmod[t];
+        const ulonglong2 x = ld2(in + size_t(t) * N + n0);
+        r.x = shoup_mul(x.x, c.x, c.y, p);
+        r.y = shoup_mul(x.y, c.x, c.y, p);
+    }
+    st2(out + size_t(t) * N + n0, r);
+}
+
+cudaError_t launch_pmodup(const ckks_ctx *ctx, const u64 *in, u64 *out, int ell, cudaStream_t st) {
+    const int threads = 256;
+    dim3 grid(unsigned((ctx->N / 2 + threads - 1) / threads), unsigned(ell + ctx->k));
+    pmodup_kernel<<<grid, threads, 0, st>>>(in, out, ell, ctx->d_pinfo, ctx->d_Pmod, ctx->logN);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ key generation
+// Signed coefficients -> residues over all L+k primes (limb l uses prime l).
+__global__ void signed_to_res_kernel(const int64_t *__restrict__ c, u64 *__restrict__ out,
+                                     const PrimeInfo *__restrict__ pinfo, int logN) {
+    const size_t N = size_t(1) << logN;
+    const size_t n = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int l = blockIdx.y;
+    const u64 p = pinfo[l].p;
+    const int64_t x = c[n];
+    u64 r;
+    if (x >= 0) {
+        r = u64(x) % p;
+    } else {
+        r = u64(-(x + 1)) % p;  // |x| - 1, safe for INT64_MIN
+        r = p - 1 - r;
+    }
+    out[size_t(l) * N + n] = r;
+}
+
+cudaError_t launch_signed_to_res(const ckks_ctx *ctx, const int64_t *c, u64 *out, cudaStream_t st) {
+    const int threads = 256;
+    dim3 grid(unsigned((ctx->N + threads - 1) / threads), unsigned(ctx->L + ctx->k));
+    signed_to_res_kernel<<<grid, threads, 0, st>>>(c, out, ctx->d_pinfo, ctx->logN);
+    return cudaGetLastError();
+}
+
+__global__ void square_kernel(const u64 *__restrict__ in, u64 *__restrict__ out, const PrimeInfo *__restrict__ pinfo,
+                              int logN) {
+    const size_t N = size_t(1) << logN;
+    const size_t n = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int l = blockIdx.y;
+    const PrimeInfo P = pinfo[l];
+    const u64 x = in[size_t(l) * N + n];
+    out[size_t(l) * N + n] = mul_mod(x, x, P);
+}
+
+cudaError_t launch_square(const ckks_ctx *ctx, const u64 *in, u64 *out, cudaStream_t st) {
+    const int threads = 256;
+    dim3 grid(unsigned((ctx->N + threads - 1) / threads), unsigned(ctx->L + ctx->k));
+    square_kernel<<<grid, threads, 0, st>>>(in, out, ctx->d_pinfo, ctx->logN);
+    return cudaGetLastError();
+}
+
+// b_j = e_j - a_j * s + g_j * s', g_j = [P]_{q_i} on digit j's chain limbs (Eq. kskShape)
+__global__ void keygen_row_kernel(const u64 *__restrict__ a, const u64 *__restrict__ s, const u64 *__restrict__ sp,
+                                  const u64 *__restrict__ e, int j, u64 *__restrict__ row0, u64 *__restrict__ row1,
+                                  const PrimeInfo *__restrict__ pinfo, const ulonglong2 *__restrict__ Pmod, int logN,
+                                  int L, int alpha) {
+    const size_t N = size_t(1) << logN;
+    const size_t n = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int l = blockIdx.y;
+    const PrimeInfo P = pinfo[l];
+    const size_t o = size_t(l) * N + n;
+    const u64 av = a[o];
+    u64 b = sub_mod(e[o], mul_mod(av, s[o], P), P.p);
+    if (l < L && l / alpha == j) {
+        const ulonglong2 c = Pmod[l];
+        b = add_mod(b, shoup_mul(sp[o], c.x, c.y, P.p), P.p);
+    }
+    row0[o] = av;
+    row1[o] = b;
+}
+
+cudaError_t launch_keygen_row(const ckks_ctx *ctx, const u64 *a, const u64 *s, const u64 *sp, const u64 *e, int j,
+                              u64 *row0, u64 *row1, cudaStream_t st) {
+    const int threads = 256;
+    dim3 grid(unsigned((ctx->N + threads - 1) / threads), unsigned(ctx->L + ctx->k));
+    keygen_row_kernel<<<grid, threads, 0, st>>>(a, s, sp, e, j, row0, row1, ctx->d_pinfo, ctx->d_Pmod, ctx->logN,
+                                                ctx->L, ctx->alpha);
+    return cudaGetLastError();
+}
+
+}  // namespace ckks
