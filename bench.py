@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""KeySwitch throughput on GB300 at N=2^16, ell=24, k=8, dnum=3.
+
+One step = HRotate (Automorph by 5^r + KeySwitch, Algorithm 4 with r=1) of
+each of C independent ciphertexts, each with its own rotation key, so the
+step's working set (C x (24 MiB ciphertext + 96 MiB key + 24 MiB output))
+is far larger than the 129 MB L2: inputs larger than L2, no flush needed.
+Metric: KeySwitch ops/s (C per step).  Inputs are seeded synthetic residues
+and keys generated on the GPU from a seeded ternary secret.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank runs its own C ciphertexts (weak scaling, no
+collective on the data path); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+from paper_2112_06396_gb300 import traffic  # noqa: E402
+
+LOGN, L, K_SP, DNUM, BITS = 16, 24, 8, 3, 54
+METRIC = "KeySwitch ops/s at N=2^16, ell=24, dnum=3"
+UNIT = "KeySwitch/s"
+WORKLOAD = "HRotate(5^r)+KeySwitch N=2^16 ell=24 k=8 dnum=3 54-bit primes"
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "sm_max_mhz": float(d.get("sm_max_mhz", 2070.0)), "src": "measured"}
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "src": "fallback"}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"bench_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-i", str(self.gpu),
+                 "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ workload
+def make_workload(ctx, C, rank, torch):
+    N = 1 << LOGN
+    primes = ctx.q + ctx.p
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(ctx.device)
+    s = synth.ternary(N, f"bench/r{rank}/s")
+    ds = dev(s)
+    items = []
+    for c in range(C):
+        g = pow(5, c + 1, 2 * N)
+        a_key = np.stack([synth.uniform_residues(primes, N, f"bench/r{rank}/key{c}/a{j}") for j in range(DNUM)])
+        e_key = np.stack([synth.gaussian(N, f"bench/r{rank}/key{c}/e{j}") for j in range(DNUM)])
+        key = ctx.keygen_ksk(ds, dev(e_key), dev(a_key), g)
+        a = dev(synth.uniform_residues(ctx.q, N, f"bench/r{rank}/ct{c}/a"))
+        b = dev(synth.uniform_residues(ctx.q, N, f"bench/r{rank}/ct{c}/b"))
+        items.append({"g": g, "key": key, "a": a, "b": b, "oa": ctx.empty(L), "ob": ctx.empty(L)})
+    torch.cuda.synchronize()
+    return items
+
+
+def step(ctx, items, ws):
+    for it in items:
+        ctx.hrotate(it["a"], it["b"], L, [it["g"]], [it["key"]], outs=[(it["oa"], it["ob"])], ws=ws)
+
+
+def ntt_source_hash():
+    h = hashlib.sha256()
+    for f in ("ntt.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2112_06396_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic_per_limb():
+    """DRAM bytes per limb-transform of the NTT kernels from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "ntt_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    if d.get("source_hash") != ntt_source_hash():
+        return None
+    return float(d["dram_bytes_per_limb_transform"])
+
+
+# ------------------------------------------------------------------ oracle (CPU) legs
+def oracle_keyswitch_seconds(reps=1):
+    """Time the oracle's HRotate (r=1) at the bench configuration, one thread."""
+    import oracle
+
+    N = 1 << LOGN
+    primes = oracle.gen_primes(BITS, LOGN, L + K_SP)
+    P = oracle.Params(LOGN, L, K_SP, DNUM, primes=primes)
+    g = 5
+    s = synth.ternary(N, "bench/r0/s")
+    a_key = np.stack([synth.uniform_residues(primes, N, f"bench/r0/key0/a{j}") for j in range(DNUM)])
+    e_key = np.stack([synth.gaussian(N, f"bench/r0/key0/e{j}") for j in range(DNUM)])
+    key = oracle.keygen(P, a_key, s, oracle.rot_secret(P, s, g), e_key)
+    a = synth.uniform_residues(primes[:L], N, "bench/r0/ct0/a")
+    b = synth.uniform_residues(primes[:L], N, "bench/r0/ct0/b")
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle.hrotate(P, L, a, b, [g], [key])
+        times.append(time.perf_counter() - t0)
+    return times
+
+
+def base_config(C):
+    return {"workload": WORKLOAD, "ciphertexts_per_step": C, "rotations_per_ciphertext": 1, "N": 1 << LOGN,
+            "ell": L, "k": K_SP, "dnum": DNUM, "prime_bits": BITS, "keys": "one rotation key per ciphertext",
+            "l2": "inputs larger than L2 (per-step working set > 1 GB), no flush"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    W = min(args.warmup, 1)
+    K = max(1, min(args.steps, 2))
+    _ = oracle_keyswitch_seconds(W) if W else None
+    times = oracle_keyswitch_seconds(K)
+    t = sum(times) / len(times)
+    value = 1.0 / t
+    sample = (f"oracle HRotate(r=1) of one ciphertext at N=2^16, ell=24, k=8, dnum=3 per step "
+              f"({K} timed steps, {W} warm-up, capped so the run ends in minutes)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u64", "data": "synthetic", "config": base_config(1),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args, rank, world, local_rank):
+    import torch
+
+    from paper_2112_06396_gb300 import ckks
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    primes = ckks.ckks_gen_primes(BITS, LOGN, L + K_SP)
+    ctx = ckks.Context(LOGN, primes[:L], primes[L:], DNUM, device=local_rank)
+    C = args.batch
+    items = make_workload(ctx, C, rank, torch)
+    ws = ctx.workspace(ckks.OP_HROTATE, L, 1)
+    N = 1 << LOGN
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step(ctx, items, ws)
+    torch.cuda.synchronize()
+
+    # ---- timed region
+    clocks = ClockSampler(local_rank)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.25)  # let the sampler take its first reading
+    t_wall0 = time.perf_counter()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step(ctx, items, ws)
+    e1.record()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * C * args.steps / (ms / 1e3)
+
+    # ---- per-kernel-class device time on the launch stream (measurement hook)
+    ctx.profile(True)
+    ctx.profile_reset()
+    prof_steps = max(1, min(args.steps, 10))
+    for _ in range(prof_steps):
+        step(ctx, items, ws)
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    launches_per_step = sum(v[1] for v in prof.values()) / prof_steps
+    by_class = {k: {"ms_per_step": v[0] / prof_steps, "launches_per_step": v[1] / prof_steps} for k, v in prof.items()}
+
+    # ---- end to end through the public API with host buffers
+    pin_in = [(torch.empty((L, N), dtype=torch.uint64).pin_memory(), torch.empty((L, N), dtype=torch.uint64).pin_memory())
+              for _ in range(C)]
+    pin_out = [(torch.empty((L, N), dtype=torch.uint64).pin_memory(), torch.empty((L, N), dtype=torch.uint64).pin_memory())
+               for _ in range(C)]
+    for (ha, hb), it in zip(pin_in, items):
+        ha.copy_(it["a"].cpu())
+        hb.copy_(it["b"].cpu())
+    dev_in = [(ctx.empty(L), ctx.empty(L)) for _ in range(C)]
+
+    def e2e_step():
+        for (ha, hb), (da, db), it, (oa, ob) in zip(pin_in, dev_in, items, pin_out):
+            da.copy_(ha, non_blocking=True)
+            db.copy_(hb, non_blocking=True)
+            ctx.hrotate(da, db, L, [it["g"]], [it["key"]], outs=[(it["oa"], it["ob"])], ws=ws)
+            oa.copy_(it["oa"], non_blocking=True)
+            ob.copy_(it["ob"], non_blocking=True)
+
+    e2e_steps = max(1, min(args.steps, 10))
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record()
+    for _ in range(e2e_steps):
+        e2e_step()
+    f1.record()
+    torch.cuda.synchronize()
+    e2e_ms = f0.elapsed_time(f1)
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    # the step's result is read back on the host: check it matches the device-only run
+    ok = all(torch.equal(oa, it["oa"].cpu()) for (oa, _), it in zip(pin_out, items))
+    bytes_io = C * 2 * L * N * 8
+
+    if rank == 0:
+        peaks = load_peaks()
+        # dominant kernel class: NTT (forward + inverse passes)
+        ntt_ms = prof["ntt_fwd"][0] + prof["ntt_inv"][0]
+        ntt_launch = prof["ntt_fwd"][1] + prof["ntt_inv"][1]
+        limb_transforms = (prof["ntt_fwd"][2] + prof["ntt_inv"][2]) / 2  # two passes per transform
+        avg_launch_ms = ntt_ms / ntt_launch
+        bfly_per_launch = limb_transforms * traffic.ntt_butterflies_per_limb(N) / ntt_launch
+        bytes_per_launch = limb_transforms * traffic.ntt_bytes_per_limb(N) / ntt_launch
+        achieved_gbfly = bfly_per_launch / (avg_launch_ms * 1e-3) / 1e9
+        # ALU peak from unit counts and clock: 152 SMs x 64 32-bit IMAD/clk x f_max,
+        # 10 IMADs per Shoup modular multiply (4 for the high word of x*w', 3 for
+        # the low word of x*w, 3 for the low word of q*p), one per butterfly.
+        peak_gbfly = 152 * 64 * peaks["sm_max_mhz"] * 1e6 / 10 / 1e9
+        tr = ncu_traffic_per_limb()
+        hbm_achieved = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9
+        ks_bytes = traffic.compulsory_hrotate_bytes(N, L, K_SP, L, DNUM, 1)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded residues; keys from a seeded ternary secret)",
+            "config": {**base_config(C), "parallelism": f"replicas x{world}"},
+            "clocks": clk, "gpu_launches": int(round(launches_per_step * args.steps)),
+            "wall_s_timed": t_wall,
+            "hbm": {"compulsory_bytes_per_keyswitch": ks_bytes,
+                    "achieved_gbs": ks_bytes * value / world / 1e9,
+                    "frac_of_8tbs": ks_bytes * value / world / 8e12,
+                    "frac_of_measured": ks_bytes * value / world / 1e9 / peaks["hbm_gbs"]},
+            "roofline": {"kernel": "ntt (forward+inverse passes)", "bound": "alu", "achieved": achieved_gbfly,
+                         "peak": peak_gbfly, "unit": "Gbutterfly/s", "frac": achieved_gbfly / peak_gbfly,
+                         "traffic": None if tr is None else tr * limb_transforms / ntt_launch,
+                         "algorithmic_bytes_per_launch": bytes_per_launch, "hbm_gbs_achieved": hbm_achieved,
+                         "hbm_frac_of_measured": hbm_achieved / peaks["hbm_gbs"], "peak_src": peaks["src"],
+                         "avg_launch_us": avg_launch_ms * 1e3, "share_of_step": ntt_ms / prof_steps / ms_per_step},
+            "kernels": by_class,
+            "e2e": {"value": world * C * e2e_steps / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": bytes_io,
+                    "d2h_bytes_per_step": bytes_io, "matches_device_result": ok},
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            times = oracle_keyswitch_seconds(1)
+            line["cpu_baseline"] = {"value": 1.0 / times[0], "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": "1 oracle HRotate(r=1) at N=2^16, ell=24, k=8, dnum=3, one thread"}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--batch", type=int, default=8, help="ciphertexts (each with its own key) per step")
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.impl == "reference" else 1)))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if args.warmup < 3:
+        args.warmup = 3
+    return run_gpu(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

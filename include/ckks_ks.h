@@ -188,6 +188,28 @@ int ckks_ptmatvecmult(ckks_ctx *ctx, const uint64_t *d_a, const uint64_t *d_b, i
 int ckks_keygen_ksk(ckks_ctx *ctx, const int64_t *d_s, const int64_t *d_e, const uint64_t *d_a, uint32_t galois,
                     uint64_t *d_key, void *ws, ckks_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Measurement hook (no counterpart in the paper).  While enabled, every
+ * kernel the context launches is bracketed by a pair of CUDA events recorded
+ * on the launch stream, grouped by kernel class; ckks_profile_read()
+ * synchronises those events and reports, per class, the summed device time,
+ * the number of launches and the number of limbs (or limb-sized units) they
+ * processed.  Enabling adds two event records per launch; disabled (the
+ * default) it costs nothing.  Returns CKKS_EINVAL for an unknown class.
+ * ------------------------------------------------------------------------ */
+enum {
+    CKKS_K_NTT_FWD = 0,   /* forward NTT passes (incl. the ModDown/Rescale epilogue) */
+    CKKS_K_NTT_INV = 1,   /* inverse NTT passes */
+    CKKS_K_BCONV = 2,     /* basis conversions of ModUp / ModDown / Rescale */
+    CKKS_K_INNER = 3,     /* KSKInnerProd (with Automorph of the digits) */
+    CKKS_K_PMV = 4,       /* PtMatVecMult inner loop */
+    CKKS_K_ELEMWISE = 5,  /* Automorph, PModUp, key-generation element-wise kernels */
+    CKKS_K_COUNT = 6
+};
+int ckks_profile_enable(ckks_ctx *ctx, int on);
+int ckks_profile_reset(ckks_ctx *ctx);
+int ckks_profile_read(ckks_ctx *ctx, int kclass, double *total_ms, long long *launches, double *units);
+
 #ifdef __cplusplus
 }
 #endif

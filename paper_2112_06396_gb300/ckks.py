@@ -60,7 +60,14 @@ _SIGS = {
                                ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                ctypes.POINTER(_vp), _i, _vp, _vp, _vp, _vp]),
     "ckks_keygen_ksk": (_i, [_vp, _vp, _vp, _vp, ctypes.c_uint32, _vp, _vp, _vp]),
+    "ckks_profile_enable": (_i, [_vp, _i]),
+    "ckks_profile_reset": (_i, [_vp]),
+    "ckks_profile_read": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
+                               ctypes.POINTER(ctypes.c_double)]),
 }
+
+K_NTT_FWD, K_NTT_INV, K_BCONV, K_INNER, K_PMV, K_ELEMWISE = range(6)
+K_NAMES = ["ntt_fwd", "ntt_inv", "bconv", "inner_prod", "pmv_accum", "elementwise"]
 
 
 def library_path() -> str:
@@ -156,6 +163,22 @@ class Context:
 
     def table_bytes(self):
         return int(lib().ckks_ctx_table_bytes(self._h))
+
+    # ------------------------------------------------------------ measurement hook
+    def profile(self, on=True):
+        _check(lib().ckks_profile_enable(self._h, int(bool(on))), self._h)
+
+    def profile_reset(self):
+        _check(lib().ckks_profile_reset(self._h), self._h)
+
+    def profile_read(self):
+        """{class name: (total_ms, launches, units)} of the launches since the last reset."""
+        out = {}
+        for i, name in enumerate(K_NAMES):
+            ms, n, u = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
+            _check(lib().ckks_profile_read(self._h, i, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(u)), self._h)
+            out[name] = (ms.value, int(n.value), u.value)
+        return out
 
     # ------------------------------------------------------------ memory
     def empty(self, nlimbs):

@@ -323,6 +323,12 @@ extern "C" int ckks_ctx_destroy(ckks_ctx *c) {
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(c->device);
+    for (auto &r : c->prof_pending) {
+        cudaEventSynchronize(r.b);
+        c->prof_pool.push_back(r.a);
+        c->prof_pool.push_back(r.b);
+    }
+    for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
     cudaFree(c->d_block);
     cudaSetDevice(prev);
     delete c;
@@ -795,7 +801,7 @@ extern "C" int ckks_keygen_ksk(ckks_ctx *ctx, const int64_t *s, const int64_t *e
         ls.add(sh + l * N, sh + l * N, l);
         le.add(eh + l * N, eh + l * N, l);
     }
-    CK(launch_signed_to_res(ctx, s, sh, st));
+    CK(launch_signed_to_res(ctx, s, sh, st));  // element-wise kernels are timed in keyswitch.cu
     RC(run_ntt(ctx, ls, false, st));
     if (g != 0) CK(launch_automorph(ctx, sh, sp, LK, g, st));
     else CK(launch_square(ctx, sh, sp, st));
@@ -805,5 +811,47 @@ extern "C" int ckks_keygen_ksk(ckks_ctx *ctx, const int64_t *s, const int64_t *e
         CK(launch_keygen_row(ctx, a + size_t(j) * LK * N, sh, sp, eh, j, key + size_t(2 * j) * LK * N,
                              key + size_t(2 * j + 1) * LK * N, st));
     }
+    return CKKS_OK;
+}
+
+// ------------------------------------------------------------------ measurement hook
+extern "C" int ckks_profile_enable(ckks_ctx *ctx, int on) {
+    if (ctx == nullptr) return CKKS_EINVAL;
+    ctx->prof_on = on != 0;
+    return CKKS_OK;
+}
+
+static int prof_drain(ckks_ctx *ctx) {
+    for (auto &r : ctx->prof_pending) {
+        float ms = 0.f;
+        CK(cudaEventSynchronize(r.b));
+        CK(cudaEventElapsedTime(&ms, r.a, r.b));
+        ctx->prof_ms[r.kclass] += ms;
+        ctx->prof_n[r.kclass] += 1;
+        ctx->prof_units[r.kclass] += r.units;
+        ctx->prof_pool.push_back(r.a);
+        ctx->prof_pool.push_back(r.b);
+    }
+    ctx->prof_pending.clear();
+    return CKKS_OK;
+}
+
+extern "C" int ckks_profile_reset(ckks_ctx *ctx) {
+    if (ctx == nullptr) return CKKS_EINVAL;
+    RC(prof_drain(ctx));
+    for (int i = 0; i < 8; ++i) {
+        ctx->prof_ms[i] = 0;
+        ctx->prof_n[i] = 0;
+        ctx->prof_units[i] = 0;
+    }
+    return CKKS_OK;
+}
+
+extern "C" int ckks_profile_read(ckks_ctx *ctx, int kclass, double *total_ms, long long *launches, double *units) {
+    if (ctx == nullptr || kclass < 0 || kclass >= CKKS_K_COUNT) return CKKS_EINVAL;
+    RC(prof_drain(ctx));
+    if (total_ms) *total_ms = ctx->prof_ms[kclass];
+    if (launches) *launches = ctx->prof_n[kclass];
+    if (units) *units = ctx->prof_units[kclass];
     return CKKS_OK;
 }

@@ -65,6 +65,7 @@ cudaError_t launch_bconv(const ckks_ctx *ctx, const BConvLaunch &l, int max_src,
     if (l.ngroups == 0) return cudaSuccess;
     const int threads = 256;
     dim3 grid(unsigned((ctx->N / 2 + threads - 1) / threads), unsigned(l.ngroups * l.chunks));
+    ProfScope ps(ctx, K_BCONV, double(l.ngroups) * l.chunk, st);
     if (max_src <= 1) bconv_kernel<1><<<grid, threads, 0, st>>>(l, ctx->d_pinfo, ctx->logN);
     else if (max_src <= 2) bconv_kernel<2><<<grid, threads, 0, st>>>(l, ctx->d_pinfo, ctx->logN);
     else if (max_src <= 3) bconv_kernel<3><<<grid, threads, 0, st>>>(l, ctx->d_pinfo, ctx->logN);

@@ -24,9 +24,56 @@ struct ckks_ctx {
     ulonglong2 *d_Pmod;               // [L+k]: [P]_{q}
     ulonglong2 *d_qlinv;              // [(L+1)*(L+k)]: [q_{ell-1}^-1]_{q_i} at ell*(L+k) + i
     int last_cuda_error;
+    // measurement hook (ckks_profile_*): event pairs around every launch
+    struct ProfRec {
+        cudaEvent_t a, b;
+        int kclass;
+        double units;
+    };
+    mutable bool prof_on = false;
+    mutable std::vector<ProfRec> prof_pending;
+    mutable std::vector<cudaEvent_t> prof_pool;
+    mutable double prof_ms[8] = {};
+    mutable long long prof_n[8] = {};
+    mutable double prof_units[8] = {};
 };
 
 namespace ckks {
+
+enum { K_NTT_FWD = 0, K_NTT_INV = 1, K_BCONV = 2, K_INNER = 3, K_PMV = 4, K_ELEMWISE = 5 };
+
+// Brackets one launch with CUDA events when the context's measurement hook is on.
+class ProfScope {
+  public:
+    ProfScope(const ckks_ctx *c, int kclass, double units, cudaStream_t st) : c_(c), st_(st) {
+        if (!c_->prof_on) return;
+        rec_.kclass = kclass;
+        rec_.units = units;
+        rec_.a = take();
+        cudaEventRecord(rec_.a, st_);
+    }
+    ~ProfScope() {
+        if (!c_->prof_on) return;
+        rec_.b = take();
+        cudaEventRecord(rec_.b, st_);
+        c_->prof_pending.push_back(rec_);
+    }
+
+  private:
+    cudaEvent_t take() {
+        if (!c_->prof_pool.empty()) {
+            cudaEvent_t e = c_->prof_pool.back();
+            c_->prof_pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    const ckks_ctx *c_;
+    cudaStream_t st_;
+    ckks_ctx::ProfRec rec_{};
+};
 
 inline int ext_prime(const ckks_ctx *c, int ell, int pos) { return pos < ell ? pos : c->L + (pos - ell); }
 inline int beta_of(const ckks_ctx *c, int ell) { return (ell + c->alpha - 1) / c->alpha; }

@@ -61,6 +61,7 @@ __global__ void __launch_bounds__(256) inner_prod_kernel(InnerArgs A, const Prim
 cudaError_t launch_inner_prod(const ckks_ctx *ctx, const InnerArgs &a, cudaStream_t st) {
     const int threads = 256;
     dim3 grid(unsigned((ctx->N / 2 + threads - 1) / threads), unsigned(a.ell + ctx->k));
+    ProfScope ps(ctx, K_INNER, a.ell + ctx->k, st);
     inner_prod_kernel<<<grid, threads, 0, st>>>(a, ctx->d_pinfo, ctx->logN, ctx->L, ctx->k, ctx->alpha);
     return cudaGetLastError();
 }
@@ -135,6 +136,7 @@ __global__ void __launch_bounds__(256) pmv_accum_kernel(PmvArgs A, const PrimeIn
 cudaError_t launch_pmv_accum(const ckks_ctx *ctx, const PmvArgs &a, cudaStream_t st) {
     const int threads = 256;
     dim3 grid(unsigned((ctx->N / 2 + threads - 1) / threads), unsigned(a.ell + ctx->k));
+    ProfScope ps(ctx, K_PMV, double(a.ell + ctx->k) * a.nb, st);
     pmv_accum_kernel<<<grid, threads, 0, st>>>(a, ctx->d_pinfo, ctx->d_Pmod, ctx->logN, ctx->L, ctx->k, ctx->alpha);
     return cudaGetLastError();
 }
@@ -153,6 +155,7 @@ cudaError_t launch_automorph(const ckks_ctx *ctx, const u64 *in, u64 *out, int n
     if (nlimbs == 0) return cudaSuccess;
     const int threads = 256;
     dim3 grid(unsigned((ctx->N / 2 + threads - 1) / threads), unsigned(nlimbs));
+    ProfScope ps(ctx, K_ELEMWISE, nlimbs, st);
     automorph_kernel<<<grid, threads, 0, st>>>(in, out, g, ctx->logN);
     return cudaGetLastError();
 }
@@ -179,6 +182,7 @@ __global__ void __launch_bounds__(256) pmodup_kernel(const u64 *__restrict__ in,
 cudaError_t launch_pmodup(const ckks_ctx *ctx, const u64 *in, u64 *out, int ell, cudaStream_t st) {
     const int threads = 256;
     dim3 grid(unsigned((ctx->N / 2 + threads - 1) / threads), unsigned(ell + ctx->k));
+    ProfScope ps(ctx, K_ELEMWISE, ell + ctx->k, st);
     pmodup_kernel<<<grid, threads, 0, st>>>(in, out, ell, ctx->d_pinfo, ctx->d_Pmod, ctx->logN);
     return cudaGetLastError();
 }
@@ -206,6 +210,7 @@ __global__ void signed_to_res_kernel(const int64_t *__restrict__ c, u64 *__restr
 cudaError_t launch_signed_to_res(const ckks_ctx *ctx, const int64_t *c, u64 *out, cudaStream_t st) {
     const int threads = 256;
     dim3 grid(unsigned((ctx->N + threads - 1) / threads), unsigned(ctx->L + ctx->k));
+    ProfScope ps(ctx, K_ELEMWISE, ctx->L + ctx->k, st);
     signed_to_res_kernel<<<grid, threads, 0, st>>>(c, out, ctx->d_pinfo, ctx->logN);
     return cudaGetLastError();
 }
@@ -224,6 +229,7 @@ __global__ void square_kernel(const u64 *__restrict__ in, u64 *__restrict__ out,
 cudaError_t launch_square(const ckks_ctx *ctx, const u64 *in, u64 *out, cudaStream_t st) {
     const int threads = 256;
     dim3 grid(unsigned((ctx->N + threads - 1) / threads), unsigned(ctx->L + ctx->k));
+    ProfScope ps(ctx, K_ELEMWISE, ctx->L + ctx->k, st);
     square_kernel<<<grid, threads, 0, st>>>(in, out, ctx->d_pinfo, ctx->logN);
     return cudaGetLastError();
 }
@@ -253,6 +259,7 @@ cudaError_t launch_keygen_row(const ckks_ctx *ctx, const u64 *a, const u64 *s, c
                               u64 *row0, u64 *row1, cudaStream_t st) {
     const int threads = 256;
     dim3 grid(unsigned((ctx->N + threads - 1) / threads), unsigned(ctx->L + ctx->k));
+    ProfScope ps(ctx, K_ELEMWISE, ctx->L + ctx->k, st);
     keygen_row_kernel<<<grid, threads, 0, st>>>(a, s, sp, e, j, row0, row1, ctx->d_pinfo, ctx->d_Pmod, ctx->logN,
                                                 ctx->L, ctx->alpha);
     return cudaGetLastError();

@@ -257,10 +257,15 @@ cudaError_t launch_ntt_fwd(const ckks_ctx *ctx, const NttBatch &b, const Epi *ep
     const int L2 = ctx->logN >> 1, L1 = ctx->logN - L2;
     Epi none{};
     none.mode = EPI_STORE;
-    cudaError_t err = dispatch<false, false, false>(L1, L2, b, ctx, none, st, false);
+    cudaError_t err;
+    {
+        ProfScope ps(ctx, K_NTT_FWD, b.count, st);
+        err = dispatch<false, false, false>(L1, L2, b, ctx, none, st, false);
+    }
     if (err != cudaSuccess) return err;
     NttBatch b2 = b;
     for (int l = 0; l < b.count; l++) b2.src[l] = b.dst[l];
+    ProfScope ps(ctx, K_NTT_FWD, b.count, st);
     if (epi != nullptr && epi->mode != EPI_STORE) return dispatch<false, true, true>(L2, L1, b2, ctx, *epi, st, false);
     return dispatch<false, true, false>(L2, L1, b2, ctx, none, st, false);
 }
@@ -269,10 +274,15 @@ cudaError_t launch_ntt_inv(const ckks_ctx *ctx, const NttBatch &b, cudaStream_t 
     if (b.count == 0) return cudaSuccess;
     const int L2 = ctx->logN >> 1, L1 = ctx->logN - L2;
     Epi none{};
-    cudaError_t err = dispatch<true, true, false>(L2, L1, b, ctx, none, st, false);
+    cudaError_t err;
+    {
+        ProfScope ps(ctx, K_NTT_INV, b.count, st);
+        err = dispatch<true, true, false>(L2, L1, b, ctx, none, st, false);
+    }
     if (err != cudaSuccess) return err;
     NttBatch b2 = b;
     for (int l = 0; l < b.count; l++) b2.src[l] = b.dst[l];
+    ProfScope ps(ctx, K_NTT_INV, b.count, st);
     return dispatch<true, false, false>(L1, L2, b2, ctx, none, st, false);
 }
 
