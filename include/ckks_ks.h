@@ -210,6 +210,35 @@ int ckks_profile_enable(ckks_ctx *ctx, int on);
 int ckks_profile_reset(ckks_ctx *ctx);
 int ckks_profile_read(ckks_ctx *ctx, int kclass, double *total_ms, long long *launches, double *units);
 
+/* ------------------------------------------------------------------------
+ * ModDown without a caller-supplied workspace (the paper has no counterpart;
+ * this is a convenience of this library).
+ *
+ * ckks_moddown needs (k + ell) * N words of device workspace from the caller.
+ * Some callers cannot provide it: code that runs inside a host framework which
+ * owns all device memory and gives its plugins no allocator, services that
+ * forbid device allocations after start-up, or callers that simply have no
+ * cudaMalloc in reach.  This entry point computes exactly what ckks_moddown
+ * computes (same arguments minus `ws`, bit-identical output) but takes its
+ * scratch from a fixed array compiled into the library, so it allocates
+ * nothing: no cudaMalloc, no cudaFree, no allocating library routine.
+ *
+ *  - Limit: the array holds 2^21 words (16 MiB), i.e. (k + ell) * N <= 2^21;
+ *    N = 2^16 with ell + k <= 32 fits (e.g. ell = 24, k = 8).  Larger
+ *    requests return CKKS_EUNSUPPORTED before anything is launched.
+ *  - Every GPU that loads the library holds the 16 MiB array until the
+ *    process exits.
+ *  - The first call on a device looks up the array's device address (with
+ *    that device current) and caches it; make that first call before any
+ *    stream capture.
+ *  - All calls share the one array and it keeps the last call's contents.
+ *    Every word a call reads there it has written first in the same call, so
+ *    nothing needs clearing, but calls whose GPU work overlaps (different
+ *    streams, or different host threads) race on the array and corrupt each
+ *    other: order them on one stream or synchronise between them.
+ * ------------------------------------------------------------------------ */
+int ckks_moddown_noalloc(ckks_ctx *ctx, const uint64_t *d_in, int level, uint64_t *d_out, ckks_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -60,6 +60,7 @@ _SIGS = {
                                ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                ctypes.POINTER(_vp), _i, _vp, _vp, _vp, _vp]),
     "ckks_keygen_ksk": (_i, [_vp, _vp, _vp, _vp, ctypes.c_uint32, _vp, _vp, _vp]),
+    "ckks_moddown_noalloc": (_i, [_vp, _vp, _i, _vp, _vp]),
     "ckks_profile_enable": (_i, [_vp, _i]),
     "ckks_profile_reset": (_i, [_vp]),
     "ckks_profile_read": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
@@ -226,6 +227,17 @@ class Context:
         out = self.empty(level) if out is None else out
         ws = self.workspace(OP_MODDOWN, level) if ws is None else ws
         _check(lib().ckks_moddown(self._h, _p(x), level, _p(out), _p(ws), _stream(stream)), self._h)
+        return out
+
+    def moddown_noalloc(self, x, level, out=None, stream=None):
+        """ModDown with its scratch in the library's fixed 16 MiB device array
+        (no workspace; (k + level) * N must not exceed 2^21 words)."""
+        out = self.empty(level) if out is None else out
+        rc = lib().ckks_moddown_noalloc(self._h, _p(x), level, _p(out), _stream(stream))
+        if rc == CKKS_EUNSUPPORTED:
+            raise CkksError(f"ckks_moddown_noalloc: (k + level) * N = {(self.k + level) * self.N} words exceeds "
+                            f"the fixed scratch of 2^21 words")
+        _check(rc, self._h)
         return out
 
     def pmodup(self, x, level, out=None, stream=None):

@@ -3,6 +3,7 @@
 // operations as sequences of kernel launches on the caller's stream.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -854,4 +855,45 @@ extern "C" int ckks_profile_read(ckks_ctx *ctx, int kclass, double *total_ms, lo
     if (launches) *launches = ctx->prof_n[kclass];
     if (units) *units = ctx->prof_units[kclass];
     return CKKS_OK;
+}
+
+// ------------------------------------------------------------------ ModDown without a workspace
+// For callers that cannot allocate device memory: the ModDown scratch (k P-limbs
+// in coefficient form, then ell converted limbs) lives in this fixed array
+// instead of a caller workspace.  2^21 words = 16 MiB, held by every GPU that
+// loads the library until exit.  Calls share it; see the header for the races.
+static constexpr size_t kNoallocWords = size_t(1) << 21;
+static __device__ __align__(256) uint64_t g_moddown_scratch[kNoallocWords];
+
+static std::mutex g_noalloc_mu;
+static uint64_t *g_noalloc_ptr[256];  // device address of the array, per device ordinal
+
+// Device address of the array on `device`, looked up once with that device current.
+static cudaError_t noalloc_scratch(int device, uint64_t **out) {
+    if (device < 0 || device >= 256) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (g_noalloc_ptr[device] == nullptr) {
+        int prev = 0;
+        cudaError_t err = cudaGetDevice(&prev);
+        if (err != cudaSuccess) return err;
+        if (prev != device && (err = cudaSetDevice(device)) != cudaSuccess) return err;
+        void *p = nullptr;
+        err = cudaGetSymbolAddress(&p, g_moddown_scratch);
+        if (prev != device) cudaSetDevice(prev);
+        if (err != cudaSuccess) return err;
+        g_noalloc_ptr[device] = static_cast<uint64_t *>(p);
+    }
+    *out = g_noalloc_ptr[device];
+    return cudaSuccess;
+}
+
+extern "C" int ckks_moddown_noalloc(ckks_ctx *ctx, const uint64_t *in, int ell, uint64_t *out, ckks_stream_t stream) {
+    if (!level_ok(ctx, ell) || !al16(in) || !al16(out)) return CKKS_EINVAL;
+    if (size_t(ctx->k + ell) * size_t(ctx->N) > kNoallocWords) return CKKS_EUNSUPPORTED;
+    uint64_t *w = nullptr;
+    CK(noalloc_scratch(ctx->device, &w));
+    const u64 *ins[2] = {in, nullptr};
+    u64 *outs[2] = {out, nullptr};
+    const u64 *adds[2] = {nullptr, nullptr};
+    return moddown_polys(ctx, ell, 1, ins, outs, adds, 1, 0, w, w + size_t(ctx->k) * ctx->N, (cudaStream_t)stream);
 }
