@@ -36,6 +36,7 @@ LOGN, L, K_SP, DNUM, BITS = 16, 24, 8, 3, 54
 METRIC = "KeySwitch ops/s at N=2^16, ell=24, dnum=3"
 UNIT = "KeySwitch/s"
 WORKLOAD = "HRotate(5^r)+KeySwitch N=2^16 ell=24 k=8 dnum=3 54-bit primes"
+STREAMS = 4
 
 
 def load_peaks():
@@ -115,9 +116,33 @@ def make_workload(ctx, C, rank, torch):
     return items
 
 
-def step(ctx, items, ws):
-    for it in items:
-        ctx.hrotate(it["a"], it["b"], L, [it["g"]], [it["key"]], outs=[(it["oa"], it["ob"])], ws=ws)
+class Lanes:
+    """S CUDA streams, each with its own workspace: independent ciphertexts of a
+    step are spread round-robin so their kernels overlap on the GPU."""
+
+    def __init__(self, ctx, S, torch, ckks):
+        self.torch = torch
+        self.streams = [torch.cuda.Stream() for _ in range(S)]
+        self.ws = [ctx.workspace(ckks.OP_HROTATE, L, 1) for _ in range(S)]
+
+    def fork(self):
+        ev = self.torch.cuda.current_stream().record_event()
+        for s in self.streams:
+            s.wait_event(ev)
+
+    def join(self):
+        cur = self.torch.cuda.current_stream()
+        for s in self.streams:
+            cur.wait_stream(s)
+
+
+def step(ctx, items, lanes):
+    lanes.fork()
+    for i, it in enumerate(items):
+        j = i % len(lanes.streams)
+        ctx.hrotate(it["a"], it["b"], L, [it["g"]], [it["key"]], outs=[(it["oa"], it["ob"])], ws=lanes.ws[j],
+                    stream=lanes.streams[j])
+    lanes.join()
 
 
 def ntt_source_hash():
@@ -165,7 +190,7 @@ def oracle_keyswitch_seconds(reps=1):
 
 
 def base_config(C):
-    return {"workload": WORKLOAD, "ciphertexts_per_step": C, "rotations_per_ciphertext": 1, "N": 1 << LOGN,
+    return {"workload": WORKLOAD, "ciphertexts_per_step": C, "streams": STREAMS, "rotations_per_ciphertext": 1, "N": 1 << LOGN,
             "ell": L, "k": K_SP, "dnum": DNUM, "prime_bits": BITS, "keys": "one rotation key per ciphertext",
             "l2": "inputs larger than L2 (per-step working set > 1 GB), no flush"}
 
@@ -206,7 +231,7 @@ def run_gpu(args, rank, world, local_rank):
     ctx = ckks.Context(LOGN, primes[:L], primes[L:], DNUM, device=local_rank)
     C = args.batch
     items = make_workload(ctx, C, rank, torch)
-    ws = ctx.workspace(ckks.OP_HROTATE, L, 1)
+    lanes = Lanes(ctx, args.streams, torch, ckks)
     N = 1 << LOGN
 
     def barrier():
@@ -214,7 +239,7 @@ def run_gpu(args, rank, world, local_rank):
             dist.barrier()
 
     for _ in range(args.warmup):
-        step(ctx, items, ws)
+        step(ctx, items, lanes)
     torch.cuda.synchronize()
 
     # ---- timed region
@@ -227,7 +252,7 @@ def run_gpu(args, rank, world, local_rank):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.steps):
-        step(ctx, items, ws)
+        step(ctx, items, lanes)
     e1.record()
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
@@ -241,12 +266,14 @@ def run_gpu(args, rank, world, local_rank):
     ms_per_step = ms / args.steps
     value = world * C * args.steps / (ms / 1e3)
 
-    # ---- per-kernel-class device time on the launch stream (measurement hook)
+    # ---- per-kernel-class device time on the launch stream (measurement hook),
+    # one stream so that every bracketed launch runs alone
+    lane1 = Lanes(ctx, 1, torch, ckks)
     ctx.profile(True)
     ctx.profile_reset()
     prof_steps = max(1, min(args.steps, 10))
     for _ in range(prof_steps):
-        step(ctx, items, ws)
+        step(ctx, items, lane1)
     torch.cuda.synchronize()
     prof = ctx.profile_read()
     ctx.profile(False)
@@ -264,12 +291,16 @@ def run_gpu(args, rank, world, local_rank):
     dev_in = [(ctx.empty(L), ctx.empty(L)) for _ in range(C)]
 
     def e2e_step():
-        for (ha, hb), (da, db), it, (oa, ob) in zip(pin_in, dev_in, items, pin_out):
-            da.copy_(ha, non_blocking=True)
-            db.copy_(hb, non_blocking=True)
-            ctx.hrotate(da, db, L, [it["g"]], [it["key"]], outs=[(it["oa"], it["ob"])], ws=ws)
-            oa.copy_(it["oa"], non_blocking=True)
-            ob.copy_(it["ob"], non_blocking=True)
+        lanes.fork()
+        for i, ((ha, hb), (da, db), it, (oa, ob)) in enumerate(zip(pin_in, dev_in, items, pin_out)):
+            j = i % len(lanes.streams)
+            with torch.cuda.stream(lanes.streams[j]):
+                da.copy_(ha, non_blocking=True)
+                db.copy_(hb, non_blocking=True)
+                ctx.hrotate(da, db, L, [it["g"]], [it["key"]], outs=[(it["oa"], it["ob"])], ws=lanes.ws[j])
+                oa.copy_(it["oa"], non_blocking=True)
+                ob.copy_(it["ob"], non_blocking=True)
+        lanes.join()
 
     e2e_steps = max(1, min(args.steps, 10))
     e2e_step()
@@ -345,9 +376,12 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--batch", type=int, default=8, help="ciphertexts (each with its own key) per step")
+    ap.add_argument("--streams", type=int, default=4, help="CUDA streams the independent ciphertexts are spread over")
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    global STREAMS
+    STREAMS = args.streams
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.impl == "reference" else 1)))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -138,6 +138,15 @@ extern "C" int ckks_ctx_create(const ckks_params *prm, int device, ckks_ctx **ou
     c->alpha = alpha;
     c->primes = primes;
     c->last_cuda_error = 0;
+    c->small_primes = *std::max_element(primes.begin(), primes.end()) < (u64(1) << 57);
+    {
+        int maxbits = 0;
+        for (u64 q : primes) maxbits = std::max(maxbits, 64 - __builtin_clzll(q));
+        const int W = (maxbits + 1) / 2;
+        // sources in [0, 3q) split at W bits give products below 2^(2W+2); 2*kMaxSrc
+        // of them must sum below 2^62, so W <= 27 (primes of at most 54 bits)
+        c->split_bits = W <= 27 ? W : 0;
+    }
     const int LK = L + k;
 
     // ---- host tables
@@ -242,6 +251,25 @@ extern "C" int ckks_ctx_create(const ckks_params *prm, int device, ckks_ctx **ou
                 rs.mat[t][0] = 1;
             }
         }
+    }
+    // split form of every plan's matrix for the 32-bit multiply-add basis conversion
+    if (c->split_bits) {
+        const int W = c->split_bits;
+        const u64 mask = (u64(1) << W) - 1;
+        auto split = [&](BConvPlan &pl) {
+            for (int d = 0; d < pl.n_dst; ++d) {
+                const u64 t = primes[pl.dst_prime[d]];
+                for (int i = 0; i < pl.n_src; ++i) {
+                    const u64 C = pl.mat[d][i], D = hmul(C, u64((u128(1) << W) % t), t);
+                    pl.matw[d][i] = make_uint4(uint32_t(D >> W), uint32_t(C >> W), uint32_t(D & mask), uint32_t(C & mask));
+                }
+                pl.dst_rw[d] = u64(((u128)1 << W) % t);
+                pl.dst_rw_s[d] = shoup_of(pl.dst_rw[d], t);
+            }
+        };
+        for (auto &pl : modup) split(pl);
+        for (auto &pl : mdown) split(pl);
+        for (auto &pl : resc) split(pl);
     }
     std::vector<ulonglong2> Pinv(LK), Pmod(LK), qlinv(size_t(L + 1) * LK);
     for (int i = 0; i < LK; ++i) {

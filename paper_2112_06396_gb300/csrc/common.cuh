@@ -42,9 +42,62 @@ __device__ __forceinline__ u64 shoup_lazy(u64 x, u64 w, u64 ws, u64 p) {
     return x * w - q * p;
 }
 __device__ __forceinline__ u64 csub(u64 x, u64 m) { return x >= m ? x - m : x; }
+
+// Shoup multiplication with an approximate quotient.  With x = x1*2^32 + x0,
+// w' = s1*2^32 + s0, T = x1*s0 and U = x0*s1 + lo(T) (< 2^64, no overflow):
+//   x*w' = (x1*s1 + hi(T) + hi(U)) * 2^64 + lo(U)*2^32 + x0*s0,
+// and the last two terms sum to less than 2^65, so q_hat = x1*s1 + hi(T) +
+// hi(U) is in [q - 1, q] for q = floor(x*w'/2^64), and x*w - q_hat*p lies in
+// [0, 3p) (within [0, 4p)) for every 64-bit x.  np = 2^64 - p; the low words
+// of x*w and q_hat*np are accumulated on 32-bit halves.  Only full-rate
+// 32-bit multiply-adds (no high-half multiply) and two adds, against a full
+// 64x64 high product plus two 64-bit low products.
+__device__ __forceinline__ u64 shoup_approx(u64 x, u64 w, u64 ws, u64 np) {
+    u64 r;
+    asm("{\n\t"
+        ".reg .u32 x0, x1, w0, w1, s0, s1, n0, n1, h1, h2, q0, q1, r0, r1, m1, m2;\n\t"
+        ".reg .u64 q, acc, t;\n\t"
+        "mov.b64 {x0, x1}, %1;\n\t"
+        "mov.b64 {w0, w1}, %2;\n\t"
+        "mov.b64 {s0, s1}, %3;\n\t"
+        "mov.b64 {n0, n1}, %4;\n\t"
+        // T = x1*s0; U = x0*s1 + lo(T) (middle word, exact carry);
+        // q_hat = x1*s1 + hi(T) + hi(U): three wide multiply-adds and one add
+        // (mul.hi.u32 issues at half the rate of mad.wide.u32)
+        "mul.wide.u32 t, x1, s0;\n\t"
+        "mov.b64 {h1, h2}, t;\n\t"
+        "cvt.u64.u32 acc, h1;\n\t"
+        "mad.wide.u32 acc, x0, s1, acc;\n\t"
+        "cvt.u64.u32 t, h2;\n\t"
+        "mad.wide.u32 q, x1, s1, t;\n\t"
+        "mov.b64 {h1, h2}, acc;\n\t"
+        "cvt.u64.u32 t, h2;\n\t"
+        "add.u64 q, q, t;\n\t"
+        // low word of x*w, independent of the quotient
+        "mul.wide.u32 acc, x0, w0;\n\t"
+        "mul.lo.u32 m1, x0, w1;\n\t"
+        "mad.lo.u32 m1, x1, w0, m1;\n\t"
+        "mov.b64 {q0, q1}, q;\n\t"
+        // + q * (2^64 - p), low word
+        "mad.wide.u32 acc, q0, n0, acc;\n\t"
+        "mad.lo.u32 m2, q0, n1, m1;\n\t"
+        "mad.lo.u32 m2, q1, n0, m2;\n\t"
+        "mov.b64 {r0, r1}, acc;\n\t"
+        "add.u32 r1, r1, m2;\n\t"
+        "mov.b64 %0, {r0, r1};\n\t"
+        "}"
+        : "=l"(r)
+        : "l"(x), "l"(w), "l"(ws), "l"(np));
+    return r;
+}
 __device__ __forceinline__ u64 shoup_mul(u64 x, u64 w, u64 ws, u64 p) { return csub(shoup_lazy(x, w, ws, p), p); }
 __device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 p) { return csub(a + b, p); }
 __device__ __forceinline__ u64 sub_mod(u64 a, u64 b, u64 p) { return a >= b ? a - b : a + p - b; }
+
+// acc += a*b for 32-bit a, b: one wide multiply-add with the 64-bit addend
+__device__ __forceinline__ void mad_wide(u64 &acc, uint32_t a, uint32_t b) {
+    asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
+}
 
 // (hi:lo) += a*b, exact
 __device__ __forceinline__ void mac128(u64 &lo, u64 &hi, u64 a, u64 b) {
@@ -65,6 +118,26 @@ __device__ __forceinline__ u64 mul_mod(u64 a, u64 b, const PrimeInfo &P) {
     u64 lo = 0, hi = 0;
     mac128(lo, hi, a, b);
     return reduce128(lo, hi, P);
+}
+
+// 16-byte load that asks L2 to keep the line (twiddle tables, reused by every
+// limb of the same prime) ahead of streamed data such as key-switching keys.
+__device__ __forceinline__ ulonglong2 ld_keep(const ulonglong2 *p) {
+    ulonglong2 v;
+    asm("{\n\t"
+        ".reg .b64 pol;\n\t"
+        "createpolicy.fractional.L2::evict_last.b64 pol, 1.0;\n\t"
+        "ld.global.nc.L2::cache_hint.v2.u64 {%0, %1}, [%2], pol;\n\t"
+        "}"
+        : "=l"(v.x), "=l"(v.y)
+        : "l"(p));
+    return v;
+}
+
+// Bulk prefetch of `bytes` (a multiple of 16, 16-byte aligned) into L2 by the
+// TMA unit; no register or shared-memory destination, nothing to wait for.
+__device__ __forceinline__ void l2_prefetch(const void *p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
 // Slot permutation of Automorph in bit-reversed evaluation order: output
@@ -114,6 +187,11 @@ struct BConvPlan {
     uint16_t dst_prime[kMaxDst];
     u64 dst_sub[kMaxDst];
     u64 mat[kMaxDst][kMaxSrc];
+    // Split form for the 32-bit multiply-add path (primes below 2^57), with
+    // W = ceil(bits(max prime) / 2), C = mat = Ch*2^W + Cl, D = [C*2^W]_t =
+    // Dh*2^W + Dl: matw = (Dh, Ch, Dl, Cl).
+    uint4 matw[kMaxDst][kMaxSrc];
+    u64 dst_rw[kMaxDst], dst_rw_s[kMaxDst];  // [2^W]_t, Shoup companion
 };
 
 struct BConvGroup {

@@ -10,6 +10,8 @@
 struct ckks_ctx {
     int device;
     int logN, N, L, k, dnum, alpha;
+    bool small_primes;                // every prime < 2^57: lazy NTT without conditional subtractions
+    int split_bits;                   // W of the split basis conversion, 0 if primes are too large for it
     std::vector<u64> primes;          // L + k: q_0..q_{L-1}, p_0..p_{k-1}
     // device tables (one allocation)
     void *d_block;

@@ -14,6 +14,8 @@ namespace ckks {
 
 __device__ __forceinline__ ulonglong2 ld2(const u64 *p) { return *reinterpret_cast<const ulonglong2 *>(p); }
 __device__ __forceinline__ void st2(u64 *p, ulonglong2 v) { *reinterpret_cast<ulonglong2 *>(p) = v; }
+// Key-switching keys are read once per operation: stream them past L1 and L2.
+__device__ __forceinline__ ulonglong2 ld2_stream(const u64 *p) { return __ldcs(reinterpret_cast<const ulonglong2 *>(p)); }
 
 // Load the automorphed pair (out slots n0, n0+1) of one limb.
 __device__ __forceinline__ ulonglong2 ld2_perm(const u64 *limb, uint32_t n0, uint32_t g, int logN) {
@@ -32,8 +34,41 @@ __device__ __forceinline__ ulonglong2 ld2_perm(const u64 *limb, uint32_t n0, uin
 // u_t = sum_{j<beta} d_j[t] * key[j][0][t'], v_t = sum_j d_j[t] * key[j][1][t']
 // (t' = key row of position t), with d_j read through Automorph_g.  The
 // digit's own limbs come from `own` when given (ModUp copies them unchanged).
+template <int BETA>
 __global__ void __launch_bounds__(256) inner_prod_kernel(InnerArgs A, const PrimeInfo *__restrict__ pinfo, int logN,
                                                          int L, int k, int alpha) {
+    const size_t N = size_t(1) << logN;
+    const uint32_t n0 = (blockIdx.x * blockDim.x + threadIdx.x) * 2;
+    if (n0 >= N) return;
+    const int t = blockIdx.y;
+    const int ell = A.ell, ext = ell + k, LK = L + k;
+    const int prime = t < ell ? t : L + (t - ell);
+    // all 3*BETA loads are issued before the first multiply
+    ulonglong2 dv[BETA], ka[BETA], kb[BETA];
+#pragma unroll
+    for (int j = 0; j < BETA; j++) {
+        const bool own = (A.own != nullptr) && t < ell && (t / alpha) == j;
+        const u64 *d = own ? A.own + size_t(t) * N : A.ext + (size_t(j) * ext + t) * N;
+        dv[j] = ld2_perm(d, n0, A.galois, logN);
+        ka[j] = ld2_stream(A.key + ((size_t(j) * 2 + 0) * LK + prime) * N + n0);
+        kb[j] = ld2_stream(A.key + ((size_t(j) * 2 + 1) * LK + prime) * N + n0);
+    }
+    const PrimeInfo P = pinfo[prime];
+    u64 ul0 = 0, uh0 = 0, ul1 = 0, uh1 = 0, vl0 = 0, vh0 = 0, vl1 = 0, vh1 = 0;
+#pragma unroll
+    for (int j = 0; j < BETA; j++) {
+        mac128(ul0, uh0, dv[j].x, ka[j].x);
+        mac128(ul1, uh1, dv[j].y, ka[j].y);
+        mac128(vl0, vh0, dv[j].x, kb[j].x);
+        mac128(vl1, vh1, dv[j].y, kb[j].y);
+    }
+    st2(A.u + size_t(t) * N + n0, make_ulonglong2(reduce128(ul0, uh0, P), reduce128(ul1, uh1, P)));
+    st2(A.v + size_t(t) * N + n0, make_ulonglong2(reduce128(vl0, vh0, P), reduce128(vl1, vh1, P)));
+}
+
+// beta > 4: loop over digits
+__global__ void __launch_bounds__(256) inner_prod_kernel_any(InnerArgs A, const PrimeInfo *__restrict__ pinfo, int logN,
+                                                             int L, int k, int alpha) {
     const size_t N = size_t(1) << logN;
     const uint32_t n0 = (blockIdx.x * blockDim.x + threadIdx.x) * 2;
     if (n0 >= N) return;
@@ -47,8 +82,8 @@ __global__ void __launch_bounds__(256) inner_prod_kernel(InnerArgs A, const Prim
         const bool own = (A.own != nullptr) && t < ell && (t / alpha) == j;
         const u64 *d = own ? A.own + size_t(t) * N : A.ext + (size_t(j) * ext + t) * N;
         const ulonglong2 dv = ld2_perm(d, n0, A.galois, logN);
-        const ulonglong2 ka = ld2(A.key + ((size_t(j) * 2 + 0) * LK + prime) * N + n0);
-        const ulonglong2 kb = ld2(A.key + ((size_t(j) * 2 + 1) * LK + prime) * N + n0);
+        const ulonglong2 ka = ld2_stream(A.key + ((size_t(j) * 2 + 0) * LK + prime) * N + n0);
+        const ulonglong2 kb = ld2_stream(A.key + ((size_t(j) * 2 + 1) * LK + prime) * N + n0);
         mac128(ul0, uh0, dv.x, ka.x);
         mac128(ul1, uh1, dv.y, ka.y);
         mac128(vl0, vh0, dv.x, kb.x);
@@ -62,7 +97,15 @@ cudaError_t launch_inner_prod(const ckks_ctx *ctx, const InnerArgs &a, cudaStrea
     const int threads = 256;
     dim3 grid(unsigned((ctx->N / 2 + threads - 1) / threads), unsigned(a.ell + ctx->k));
     ProfScope ps(ctx, K_INNER, a.ell + ctx->k, st);
-    inner_prod_kernel<<<grid, threads, 0, st>>>(a, ctx->d_pinfo, ctx->logN, ctx->L, ctx->k, ctx->alpha);
+    const int beta = beta_of(ctx, a.ell);
+    switch (beta) {
+    case 1: inner_prod_kernel<1><<<grid, threads, 0, st>>>(a, ctx->d_pinfo, ctx->logN, ctx->L, ctx->k, ctx->alpha); break;
+    case 2: inner_prod_kernel<2><<<grid, threads, 0, st>>>(a, ctx->d_pinfo, ctx->logN, ctx->L, ctx->k, ctx->alpha); break;
+    case 3: inner_prod_kernel<3><<<grid, threads, 0, st>>>(a, ctx->d_pinfo, ctx->logN, ctx->L, ctx->k, ctx->alpha); break;
+    case 4: inner_prod_kernel<4><<<grid, threads, 0, st>>>(a, ctx->d_pinfo, ctx->logN, ctx->L, ctx->k, ctx->alpha); break;
+    default:
+        inner_prod_kernel_any<<<grid, threads, 0, st>>>(a, ctx->d_pinfo, ctx->logN, ctx->L, ctx->k, ctx->alpha);
+    }
     return cudaGetLastError();
 }
 
@@ -107,8 +150,8 @@ __global__ void __launch_bounds__(256) pmv_accum_kernel(PmvArgs A, const PrimeIn
                 const bool own = t < ell && (t / alpha) == j;
                 const u64 *d = own ? A.a + size_t(t) * N : A.ext + (size_t(j) * ext + t) * N;
                 const ulonglong2 dv = ld2_perm(d, n0, g, logN);
-                const ulonglong2 ka = ld2(key + ((size_t(j) * 2 + 0) * LK + prime) * N + n0);
-                const ulonglong2 kb = ld2(key + ((size_t(j) * 2 + 1) * LK + prime) * N + n0);
+                const ulonglong2 ka = ld2_stream(key + ((size_t(j) * 2 + 0) * LK + prime) * N + n0);
+                const ulonglong2 kb = ld2_stream(key + ((size_t(j) * 2 + 1) * LK + prime) * N + n0);
                 mac128(ul0, uh0, dv.x, ka.x);
                 mac128(ul1, uh1, dv.y, ka.y);
                 mac128(vl0, vh0, dv.x, kb.x);

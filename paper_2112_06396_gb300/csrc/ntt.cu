@@ -22,56 +22,116 @@
 
 namespace ckks {
 
-// Cooley-Tukey butterfly, X, Y in [0, 4p) -> [0, 4p)
-__device__ __forceinline__ void ct_bfly(u64 &X, u64 &Y, ulonglong2 w, u64 p, u64 two_p) {
-    X = csub(X, two_p);
-    u64 T = shoup_lazy(Y, w.x, w.y, p);
-    Y = X + two_p - T;
-    X = X + T;
+// Butterflies.  SMALLP (every prime < 2^57) uses the approximate-quotient
+// Shoup product (result in [0, 3p)):
+//  * forward (Cooley-Tukey): X' = X + T, Y' = X + 4p - T with T = W*Y in
+//    [0, 3p), no conditional subtraction: a value below M*p before a stage is
+//    below (M+4)*p after it.  Inputs may be lazy up to 8p (the basis
+//    conversions leave their outputs below 4p, the ModDown offset adds at
+//    most 4p more), so after all logN <= 17 stages every value is below
+//    (8 + 68)p < 2^64 and one reduction at the very end suffices;
+//  * inverse (Gentleman-Sande): X' = (X + Y) mod' 4p, Y' = W*(X - Y + 4p),
+//    keeping every value in [0, 4p).
+// Otherwise (primes up to 2^60) Harvey's exact-quotient butterflies keep
+// [0, 4p) forward and [0, 2p) inverse.
+template <bool SMALLP>
+__device__ __forceinline__ void ct_bfly(u64 &X, u64 &Y, ulonglong2 w, u64 p, u64 np) {
+    if (SMALLP) {
+        const u64 T = shoup_approx(Y, w.x, w.y, np);
+        Y = X + 4 * p - T;
+        X = X + T;
+    } else {
+        X = csub(X, 2 * p);
+        const u64 T = shoup_lazy(Y, w.x, w.y, p);
+        Y = X + 2 * p - T;
+        X = X + T;
+    }
 }
-// Gentleman-Sande butterfly, X, Y in [0, 2p) -> [0, 2p)
-__device__ __forceinline__ void gs_bfly(u64 &X, u64 &Y, ulonglong2 w, u64 p, u64 two_p) {
-    u64 T = X + two_p - Y;
-    X = csub(X + Y, two_p);
-    Y = shoup_lazy(T, w.x, w.y, p);
+template <bool SMALLP>
+__device__ __forceinline__ void gs_bfly(u64 &X, u64 &Y, ulonglong2 w, u64 p, u64 np) {
+    if (SMALLP) {
+        const u64 T = X + 4 * p - Y;
+        X = csub(X + Y, 4 * p);
+        Y = shoup_approx(T, w.x, w.y, np);
+    } else {
+        const u64 T = X + 2 * p - Y;
+        X = csub(X + Y, 2 * p);
+        Y = shoup_lazy(T, w.x, w.y, p);
+    }
 }
 
-template <int LOGR, int A, int C, bool INV, bool CONTIG, bool EPI>
-__global__ void __launch_bounds__((1 << (LOGR - A)) * C)
-ntt_pass_kernel(NttBatch batch, const PrimeInfo *__restrict__ pinfo, const ulonglong2 *__restrict__ tw_all,
-                int logN, Epi epi) {
+template <int LOGN, int LOGR, int A, int C, bool INV, bool CONTIG, bool EPI, bool SMALLP>
+__global__ void __launch_bounds__((1 << (LOGR - A)) * C, A <= 4 ? 4 : 2)
+ntt_pass_kernel(NttBatch batch, const PrimeInfo *__restrict__ pinfo, const ulonglong2 *__restrict__ tw_all, Epi epi) {
     constexpr int B = LOGR - A;
     constexpr int TPC = 1 << B;   // threads per column
     constexpr int E = 1 << A;     // words per thread
     constexpr int R = 1 << LOGR;  // rows per column
     constexpr int RS = R + TPC;   // pass-C smem row stride (one pad word per E rows)
+    constexpr int NT = TPC * C;
+    constexpr int TILE = CONTIG ? C * RS : R * C;
     extern __shared__ u64 sm[];
 
-    const int L2 = logN >> 1;
-    const int L1 = logN - L2;
-    const size_t N = size_t(1) << logN;
+    // every shift is a compile-time constant and every index fits 32 bits
+    constexpr int L2 = LOGN >> 1;
+    constexpr int L1 = LOGN - L2;
+    constexpr uint32_t N = 1u << LOGN;
+    constexpr int logN = LOGN;
     const int limb = blockIdx.y;
     const int prime = batch.prime[limb];
     const u64 *__restrict__ src = batch.src[limb];
     u64 *dst = batch.dst[limb];
     const ulonglong2 *__restrict__ tw = tw_all + size_t(prime) * N;
     const u64 p = pinfo[prime].p;
-    const u64 two_p = 2 * p;
+    const u64 np = u64(0) - p;
 
     const int tid = threadIdx.x;
     const int g = CONTIG ? (tid % TPC) : (tid / C);
     const int cl = CONTIG ? (tid / TPC) : (tid % C);
-    const int col = blockIdx.x * C + cl;
-    const int s0 = CONTIG ? L1 : 0;
-    const u64 prefix = CONTIG ? u64(col) : 0;
+    const uint32_t col = blockIdx.x * C + cl;
+    constexpr int s0 = CONTIG ? L1 : 0;
+    const uint32_t prefix = CONTIG ? col : 0;
 
-    auto gidx = [&](int r) -> size_t {
-        return CONTIG ? ((size_t(col) << L2) + r) : ((size_t(r) << L2) + col);
-    };
+    auto gidx = [&](int r) -> uint32_t { return CONTIG ? ((col << L2) + r) : ((uint32_t(r) << L2) + col); };
     auto sidx = [&](int r) -> int { return CONTIG ? (cl * RS + r + (r >> A)) : (r * C + cl); };
-    auto twi = [&](int sigma, int r) -> size_t {
-        return (size_t(1) << (s0 + sigma)) + (prefix << sigma) + (size_t(r) >> (LOGR - sigma));
+    auto twi = [&](int sigma, int r) -> uint32_t {
+        return (1u << (s0 + sigma)) + (prefix << sigma) + (uint32_t(r) >> (LOGR - sigma));
     };
+    // Pass S uses only the twiddles 1 .. R-1 of this prime: stage them in shared memory.
+    ulonglong2 *stw = reinterpret_cast<ulonglong2 *>(sm + TILE);
+    if (!CONTIG) {
+        for (int i = tid; i < R; i += NT) stw[i] = ld_keep(&tw[i]);
+        __syncthreads();
+    }
+    auto TW = [&](int sigma, int r) -> ulonglong2 {
+        const size_t i = twi(sigma, r);
+        return CONTIG ? ld_keep(&tw[i]) : stw[i];
+    };
+    // Pass C: one thread asks the TMA unit to pull this CTA's twiddle ranges
+    // (stage sigma uses C * 2^sigma consecutive entries) and, for the ModDown
+    // epilogue, the x and add tiles into L2 while the data loads run.
+    if (CONTIG && tid == 0) {
+        const size_t col0 = size_t(blockIdx.x) * C;
+#pragma unroll
+        for (int sg = 0; sg < LOGR; sg++) {
+            const ulonglong2 *t0 = tw + (size_t(1) << (s0 + sg)) + (col0 << sg);
+            l2_prefetch(t0, uint32_t(C * sizeof(ulonglong2)) << sg);
+        }
+        if (EPI && epi.mode == EPI_SCALE) {
+            const int poly = limb / epi.nper;
+            const size_t base = size_t(limb % epi.nper) * N + (col0 << L2);
+            l2_prefetch(epi.x[poly] + base, uint32_t(C * sizeof(u64)) << L2);
+            if (epi.accumulate) l2_prefetch(epi.out[poly] + base, uint32_t(C * sizeof(u64)) << L2);
+            if (epi.add[poly] != nullptr) {
+                for (int b = 0; b < C; b++) {
+                    const uint32_t first = uint32_t((col0 + b) << L2);
+                    const uint32_t sblk = (epi.galois == 1 ? first : automorph_src(first, epi.galois, logN)) >> L2;
+                    l2_prefetch(epi.add[poly] + size_t(limb % epi.nper) * N + (size_t(sblk) << L2),
+                                uint32_t(sizeof(u64)) << L2);
+                }
+            }
+        }
+    }
 
     u64 x[E];
     if (!INV) {
@@ -85,8 +145,7 @@ ntt_pass_kernel(NttBatch batch, const PrimeInfo *__restrict__ pinfo, const ulong
 #pragma unroll
             for (int k = 0; k < E; k++) {
                 if (k & half) continue;
-                ulonglong2 w = __ldg(&tw[twi(sg, g + (k << B))]);
-                ct_bfly(x[k], x[k + half], w, p, two_p);
+                ct_bfly<SMALLP>(x[k], x[k + half], TW(sg, g + (k << B)), p, np);
             }
         }
 #pragma unroll
@@ -101,8 +160,7 @@ ntt_pass_kernel(NttBatch batch, const PrimeInfo *__restrict__ pinfo, const ulong
 #pragma unroll
             for (int e = 0; e < E; e++) {
                 if (e & half) continue;
-                ulonglong2 w = __ldg(&tw[twi(sg, (g << A) + e)]);
-                ct_bfly(x[e], x[e + half], w, p, two_p);
+                ct_bfly<SMALLP>(x[e], x[e + half], TW(sg, (g << A) + e), p, np);
             }
         }
         if (!CONTIG) {
@@ -116,23 +174,52 @@ ntt_pass_kernel(NttBatch batch, const PrimeInfo *__restrict__ pinfo, const ulong
             __syncthreads();
 #pragma unroll
             for (int k = 0; k < E; k++) x[k] = sm[sidx(g + (k << B))];
+            const u64 one_s = pinfo[prime].one_s;
+            ulonglong2 c = make_ulonglong2(0, 0);
+            int poly = 0;
+            size_t base = 0;
+            if (EPI) {
+                poly = limb / epi.nper;
+                base = size_t(limb % epi.nper) * N;
+                c = epi.cmul[prime];
+            }
 #pragma unroll
             for (int k = 0; k < E; k++) {
-                const size_t i = gidx(g + (k << B));
-                u64 v = csub(csub(x[k], two_p), p);
-                if (!EPI || epi.mode == EPI_STORE) {
-                    dst[i] = v;
-                } else {
-                    const int poly = limb / epi.nper;
-                    const size_t base = size_t(limb % epi.nper) * N;
-                    const ulonglong2 c = epi.cmul[prime];
-                    u64 r = shoup_mul(sub_mod(epi.x[poly][base + i], v, p), c.x, c.y, p);
-                    if (epi.add[poly] != nullptr) {
-                        const uint32_t si = epi.galois == 1 ? uint32_t(i) : automorph_src(uint32_t(i), epi.galois, logN);
-                        r = add_mod(r, epi.add[poly][base + si], p);
+                u64 v = SMALLP ? shoup_approx(x[k], 1, one_s, np) : x[k];
+                x[k] = csub(csub(v, 2 * p), p);
+            }
+            if (!EPI || epi.mode == EPI_STORE) {
+#pragma unroll
+                for (int k = 0; k < E; k++) dst[gidx(g + (k << B))] = x[k];
+            } else {
+                // Epilogue operands are read-only for this launch: load a group of
+                // them through the non-coherent path before any store, so the
+                // loads overlap instead of waiting behind each store.
+                const u64 *__restrict__ xp = epi.x[poly] + base;
+                const u64 *__restrict__ ap = epi.add[poly] == nullptr ? nullptr : epi.add[poly] + base;
+                u64 *op = epi.out[poly] + base;
+                constexpr int GRP = E < 8 ? E : 8;
+#pragma unroll
+                for (int k0 = 0; k0 < E; k0 += GRP) {
+                    u64 xv[GRP], av[GRP], ov[GRP];
+#pragma unroll
+                    for (int k = 0; k < GRP; k++) {
+                        const uint32_t i = uint32_t(gidx(g + ((k0 + k) << B)));
+                        xv[k] = __ldg(xp + i);
+                        av[k] = 0;
+                        ov[k] = 0;
+                        if (ap != nullptr)
+                            av[k] = __ldg(ap + (epi.galois == 1 ? i : automorph_src(i, epi.galois, logN)));
+                        if (epi.accumulate) ov[k] = op[i];
                     }
-                    if (epi.accumulate) r = add_mod(r, epi.out[poly][base + i], p);
-                    epi.out[poly][base + i] = r;
+#pragma unroll
+                    for (int k = 0; k < GRP; k++) {
+                        const uint32_t i = uint32_t(gidx(g + ((k0 + k) << B)));
+                        u64 r = shoup_mul(sub_mod(xv[k], x[k0 + k], p), c.x, c.y, p);
+                        r = add_mod(r, av[k], p);
+                        r = add_mod(r, ov[k], p);
+                        op[i] = r;
+                    }
                 }
             }
         }
@@ -157,8 +244,7 @@ ntt_pass_kernel(NttBatch batch, const PrimeInfo *__restrict__ pinfo, const ulong
 #pragma unroll
             for (int e = 0; e < E; e++) {
                 if (e & half) continue;
-                ulonglong2 w = __ldg(&tw[twi(sg, (g << A) + e)]);
-                gs_bfly(x[e], x[e + half], w, p, two_p);
+                gs_bfly<SMALLP>(x[e], x[e + half], TW(sg, (g << A) + e), p, np);
             }
         }
 #pragma unroll
@@ -176,24 +262,29 @@ ntt_pass_kernel(NttBatch batch, const PrimeInfo *__restrict__ pinfo, const ulong
 #pragma unroll
                 for (int k = 0; k < E; k++) {
                     if (k & half) continue;
-                    u64 X = x[k], Y = x[k + half];
-                    u64 T = X + two_p - Y;
-                    x[k] = shoup_lazy(X + Y, P.ninv, P.ninv_s, p);
-                    x[k + half] = shoup_lazy(T, P.ninv_w, P.ninv_w_s, p);
+                    const u64 X = x[k], Y = x[k + half];
+                    if (SMALLP) {
+                        const u64 T = X + 4 * p - Y;
+                        x[k] = shoup_approx(X + Y, P.ninv, P.ninv_s, np);
+                        x[k + half] = shoup_approx(T, P.ninv_w, P.ninv_w_s, np);
+                    } else {
+                        const u64 T = X + 2 * p - Y;
+                        x[k] = shoup_lazy(X + Y, P.ninv, P.ninv_s, p);
+                        x[k + half] = shoup_lazy(T, P.ninv_w, P.ninv_w_s, p);
+                    }
                 }
             } else {
 #pragma unroll
                 for (int k = 0; k < E; k++) {
                     if (k & half) continue;
-                    ulonglong2 w = __ldg(&tw[twi(sg, g + (k << B))]);
-                    gs_bfly(x[k], x[k + half], w, p, two_p);
+                    gs_bfly<SMALLP>(x[k], x[k + half], TW(sg, g + (k << B)), p, np);
                 }
             }
         }
 #pragma unroll
         for (int k = 0; k < E; k++) {
             u64 v = x[k];
-            if (!CONTIG) v = csub(v, p);  // last pass: fully reduce
+            if (!CONTIG) v = SMALLP ? csub(csub(v, 2 * p), p) : csub(v, p);  // last pass: fully reduce
             dst[gidx(g + (k << B))] = v;
         }
     }
@@ -202,35 +293,49 @@ ntt_pass_kernel(NttBatch batch, const PrimeInfo *__restrict__ pinfo, const ulong
 // ------------------------------------------------------------------ host side
 namespace {
 
-template <int LOGR, int C, bool INV, bool CONTIG, bool EPI>
-cudaError_t launch_one(const NttBatch &b, const ckks_ctx *ctx, const Epi &epi, int tiles, cudaStream_t st,
-                       bool set_attr) {
+template <int LOGN, bool INV, bool CONTIG, bool EPI, bool SMALLP>
+cudaError_t launch_one_p(const NttBatch &b, const ckks_ctx *ctx, const Epi &epi, cudaStream_t st, bool set_attr) {
+    // pass S transforms columns of 2^L1 rows, pass C blocks of 2^L2 words
+    constexpr int L2 = LOGN >> 1, L1 = LOGN - L2;
+    constexpr int LOGR = CONTIG ? L2 : L1;
+    constexpr int OTHER = CONTIG ? L1 : L2;
     constexpr int A = (LOGR + 1) / 2;
     constexpr int B = LOGR - A;
     constexpr int TPC = 1 << B;
     constexpr int R = 1 << LOGR;
-    const size_t smem = CONTIG ? size_t(C) * (R + TPC) * 8 : size_t(R) * C * 8;
-    auto kern = ntt_pass_kernel<LOGR, A, C, INV, CONTIG, EPI>;
+    // C = columns (pass S) or blocks (pass C) per CTA: 256 threads, clamped to
+    // the number of columns / blocks of the matrix view
+    constexpr int C = (256 / TPC) < (1 << OTHER) ? (256 / TPC) : (1 << OTHER);
+    const size_t smem = CONTIG ? size_t(C) * (R + TPC) * 8 : size_t(R) * C * 8 + size_t(R) * 16;
+    auto kern = ntt_pass_kernel<LOGN, LOGR, A, C, INV, CONTIG, EPI, SMALLP>;
     if (set_attr) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    dim3 grid(tiles, b.count);
-    kern<<<grid, TPC * C, smem, st>>>(b, ctx->d_pinfo, INV ? ctx->d_tw_inv : ctx->d_tw_fwd, ctx->logN, epi);
+    dim3 grid((1 << OTHER) / C, b.count);
+    kern<<<grid, TPC * C, smem, st>>>(b, ctx->d_pinfo, INV ? ctx->d_tw_inv : ctx->d_tw_fwd, epi);
     return cudaGetLastError();
 }
 
-// C = columns (pass S) or blocks (pass C) per CTA: 256 threads, clamped to the
-// number of columns/blocks of the matrix view.
+template <int LOGN, bool INV, bool CONTIG, bool EPI>
+cudaError_t launch_one(const NttBatch &b, const ckks_ctx *ctx, const Epi &epi, cudaStream_t st, bool set_attr) {
+    if (set_attr) {
+        cudaError_t e = launch_one_p<LOGN, INV, CONTIG, EPI, true>(b, ctx, epi, st, true);
+        if (e != cudaSuccess) return e;
+        return launch_one_p<LOGN, INV, CONTIG, EPI, false>(b, ctx, epi, st, true);
+    }
+    if (ctx->small_primes) return launch_one_p<LOGN, INV, CONTIG, EPI, true>(b, ctx, epi, st, false);
+    return launch_one_p<LOGN, INV, CONTIG, EPI, false>(b, ctx, epi, st, false);
+}
+
 template <bool INV, bool CONTIG, bool EPI>
-cudaError_t dispatch(int LOGR, int other, const NttBatch &b, const ckks_ctx *ctx, const Epi &epi, cudaStream_t st,
-                     bool set_attr) {
-    const int ncols = 1 << other;
-    switch (LOGR) {
-    case 5:
-        if (ncols >= 64) return launch_one<5, 64, INV, CONTIG, EPI>(b, ctx, epi, ncols / 64, st, set_attr);
-        return launch_one<5, 32, INV, CONTIG, EPI>(b, ctx, epi, ncols / 32, st, set_attr);
-    case 6: return launch_one<6, 32, INV, CONTIG, EPI>(b, ctx, epi, ncols / 32, st, set_attr);
-    case 7: return launch_one<7, 32, INV, CONTIG, EPI>(b, ctx, epi, ncols / 32, st, set_attr);
-    case 8: return launch_one<8, 16, INV, CONTIG, EPI>(b, ctx, epi, ncols / 16, st, set_attr);
-    case 9: return launch_one<9, 16, INV, CONTIG, EPI>(b, ctx, epi, ncols / 16, st, set_attr);
+cudaError_t dispatch(const NttBatch &b, const ckks_ctx *ctx, const Epi &epi, cudaStream_t st, bool set_attr) {
+    switch (ctx->logN) {
+    case 10: return launch_one<10, INV, CONTIG, EPI>(b, ctx, epi, st, set_attr);
+    case 11: return launch_one<11, INV, CONTIG, EPI>(b, ctx, epi, st, set_attr);
+    case 12: return launch_one<12, INV, CONTIG, EPI>(b, ctx, epi, st, set_attr);
+    case 13: return launch_one<13, INV, CONTIG, EPI>(b, ctx, epi, st, set_attr);
+    case 14: return launch_one<14, INV, CONTIG, EPI>(b, ctx, epi, st, set_attr);
+    case 15: return launch_one<15, INV, CONTIG, EPI>(b, ctx, epi, st, set_attr);
+    case 16: return launch_one<16, INV, CONTIG, EPI>(b, ctx, epi, st, set_attr);
+    case 17: return launch_one<17, INV, CONTIG, EPI>(b, ctx, epi, st, set_attr);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -238,15 +343,14 @@ cudaError_t dispatch(int LOGR, int other, const NttBatch &b, const ckks_ctx *ctx
 }  // namespace
 
 cudaError_t ntt_set_attributes(const ckks_ctx *ctx) {
-    const int L2 = ctx->logN >> 1, L1 = ctx->logN - L2;
     NttBatch b{};
     Epi e{};
     cudaError_t err;
-    if ((err = dispatch<false, false, false>(L1, L2, b, ctx, e, nullptr, true)) != cudaSuccess) return err;
-    if ((err = dispatch<false, true, false>(L2, L1, b, ctx, e, nullptr, true)) != cudaSuccess) return err;
-    if ((err = dispatch<false, true, true>(L2, L1, b, ctx, e, nullptr, true)) != cudaSuccess) return err;
-    if ((err = dispatch<true, true, false>(L2, L1, b, ctx, e, nullptr, true)) != cudaSuccess) return err;
-    if ((err = dispatch<true, false, false>(L1, L2, b, ctx, e, nullptr, true)) != cudaSuccess) return err;
+    if ((err = dispatch<false, false, false>(b, ctx, e, nullptr, true)) != cudaSuccess) return err;
+    if ((err = dispatch<false, true, false>(b, ctx, e, nullptr, true)) != cudaSuccess) return err;
+    if ((err = dispatch<false, true, true>(b, ctx, e, nullptr, true)) != cudaSuccess) return err;
+    if ((err = dispatch<true, true, false>(b, ctx, e, nullptr, true)) != cudaSuccess) return err;
+    if ((err = dispatch<true, false, false>(b, ctx, e, nullptr, true)) != cudaSuccess) return err;
     return cudaSuccess;
 }
 
@@ -254,36 +358,34 @@ cudaError_t ntt_set_attributes(const ckks_ctx *ctx) {
 // epilogue replaces the store of the last pass.
 cudaError_t launch_ntt_fwd(const ckks_ctx *ctx, const NttBatch &b, const Epi *epi, cudaStream_t st) {
     if (b.count == 0) return cudaSuccess;
-    const int L2 = ctx->logN >> 1, L1 = ctx->logN - L2;
     Epi none{};
     none.mode = EPI_STORE;
     cudaError_t err;
     {
         ProfScope ps(ctx, K_NTT_FWD, b.count, st);
-        err = dispatch<false, false, false>(L1, L2, b, ctx, none, st, false);
+        err = dispatch<false, false, false>(b, ctx, none, st, false);
     }
     if (err != cudaSuccess) return err;
     NttBatch b2 = b;
     for (int l = 0; l < b.count; l++) b2.src[l] = b.dst[l];
     ProfScope ps(ctx, K_NTT_FWD, b.count, st);
-    if (epi != nullptr && epi->mode != EPI_STORE) return dispatch<false, true, true>(L2, L1, b2, ctx, *epi, st, false);
-    return dispatch<false, true, false>(L2, L1, b2, ctx, none, st, false);
+    if (epi != nullptr && epi->mode != EPI_STORE) return dispatch<false, true, true>(b2, ctx, *epi, st, false);
+    return dispatch<false, true, false>(b2, ctx, none, st, false);
 }
 
 cudaError_t launch_ntt_inv(const ckks_ctx *ctx, const NttBatch &b, cudaStream_t st) {
     if (b.count == 0) return cudaSuccess;
-    const int L2 = ctx->logN >> 1, L1 = ctx->logN - L2;
     Epi none{};
     cudaError_t err;
     {
         ProfScope ps(ctx, K_NTT_INV, b.count, st);
-        err = dispatch<true, true, false>(L2, L1, b, ctx, none, st, false);
+        err = dispatch<true, true, false>(b, ctx, none, st, false);
     }
     if (err != cudaSuccess) return err;
     NttBatch b2 = b;
     for (int l = 0; l < b.count; l++) b2.src[l] = b.dst[l];
     ProfScope ps(ctx, K_NTT_INV, b.count, st);
-    return dispatch<true, false, false>(L1, L2, b2, ctx, none, st, false);
+    return dispatch<true, false, false>(b2, ctx, none, st, false);
 }
 
 }  // namespace ckks
