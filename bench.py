@@ -145,6 +145,64 @@ def step(ctx, items, lanes):
     lanes.join()
 
 
+def measure_other_rows(ctx, ckks, torch, reps=5):
+    """Rescale (Alg. 1's ModDown_{B,1}) of one ciphertext and one CoeffToSlot-shaped
+    PtMatVecMult level (Alg. 8 with 8 baby x 4 giant steps of stride 1, 32 seeded
+    diagonals over the extended basis, 7 baby + 3 giant rotation keys) at N=2^16,
+    ell=24, timed with CUDA events outside the KeySwitch timed region."""
+    N = 1 << LOGN
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(ctx.device)
+    primes = ctx.q + ctx.p
+    a = dev(synth.uniform_residues(ctx.q, N, "bench/rows/a"))
+    b = dev(synth.uniform_residues(ctx.q, N, "bench/rows/b"))
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ws_r = ctx.workspace(ckks.OP_RESCALE, L)
+    oa, ob = ctx.empty(L - 1), ctx.empty(L - 1)
+    rescale_ms = timed(lambda: (ctx.rescale(a, L, oa, ws_r), ctx.rescale(b, L, ob, ws_r)))
+
+    nb, ng = 8, 4
+    twoN = 2 * N
+    g_baby = [1] + [pow(5, i, twoN) for i in range(1, nb)]
+    g_giant = [1] + [pow(5, t * nb, twoN) for t in range(1, ng)]
+    s = dev(synth.ternary(N, "bench/rows/s"))
+
+    def key(g, tag):
+        a_key = np.stack([synth.uniform_residues(primes, N, f"bench/rows/{tag}/a{j}") for j in range(DNUM)])
+        e_key = np.stack([synth.gaussian(N, f"bench/rows/{tag}/e{j}") for j in range(DNUM)])
+        return ctx.keygen_ksk(s, dev(e_key), dev(a_key), g)
+
+    kb = [None] + [key(g, f"kb{i}") for i, g in enumerate(g_baby) if i > 0]
+    kg = [None] + [key(g, f"kg{t}") for t, g in enumerate(g_giant) if t > 0]
+    diags = [dev(synth.uniform_residues(ctx.ext_primes(L), N, f"bench/rows/M{d}")) for d in range(nb * ng)]
+    ws_p = ctx.workspace(ckks.OP_PTMATVEC, L, ng)
+    pa, pb = ctx.empty(L - 1), ctx.empty(L - 1)
+    pmv_ms = timed(lambda: ctx.ptmatvecmult(a, b, L, nb, ng, g_baby, g_giant, kb, kg, diags, True, pa, pb, ws_p))
+    pmv_bytes = (2 * L + (nb - 1 + ng - 1) * traffic.key_limbs(L, K_SP, L, DNUM) + nb * ng * (L + K_SP)
+                 + 2 * (L - 1)) * traffic.limb_bytes(N)
+    del kb, kg, diags
+    torch.cuda.empty_cache()
+    return {
+        "rescale": {"ms_per_ciphertext": rescale_ms, "ciphertexts_per_s": 1e3 / rescale_ms,
+                    "shape": "2 polys, ell 24 -> 23"},
+        "ptmatvecmult": {"ms_per_level": pmv_ms, "levels_per_s": 1e3 / pmv_ms,
+                         "shape": "ell=24, 8 baby x 4 giant steps, 32 diagonals, 10 keys, rescaled",
+                         "compulsory_bytes": pmv_bytes,
+                         "hbm_frac_of_measured": pmv_bytes / (pmv_ms * 1e-3) / 1e9 / load_peaks()["hbm_gbs"]},
+    }
+
+
 def ntt_source_hash():
     h = hashlib.sha256()
     for f in ("ntt.cu", "common.cuh"):
@@ -354,11 +412,16 @@ def run_gpu(args, rank, world, local_rank):
                          "traffic": None if tr is None else tr * limb_transforms / ntt_launch,
                          "algorithmic_bytes_per_launch": bytes_per_launch, "hbm_gbs_achieved": hbm_achieved,
                          "hbm_frac_of_measured": hbm_achieved / peaks["hbm_gbs"], "peak_src": peaks["src"],
-                         "avg_launch_us": avg_launch_ms * 1e3, "share_of_step": ntt_ms / prof_steps / ms_per_step},
+                         "avg_launch_us": avg_launch_ms * 1e3,
+                         "share_of_kernel_time": ntt_ms / sum(v[0] for v in prof.values())},
             "kernels": by_class,
             "e2e": {"value": world * C * e2e_steps / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": bytes_io,
                     "d2h_bytes_per_step": bytes_io, "matches_device_result": ok},
         }
+        if not args.no_rows:
+            del items, lanes, lane1
+            torch.cuda.empty_cache()
+            line["other_rows"] = measure_other_rows(ctx, ckks, torch)
         if world == 1 and not args.no_cpu_baseline:
             times = oracle_keyswitch_seconds(1)
             line["cpu_baseline"] = {"value": 1.0 / times[0], "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -379,6 +442,7 @@ def main():
     ap.add_argument("--streams", type=int, default=4, help="CUDA streams the independent ciphertexts are spread over")
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-rows", action="store_true", help="skip the Rescale / PtMatVecMult side measurements")
     args = ap.parse_args()
     global STREAMS
     STREAMS = args.streams
