@@ -438,15 +438,16 @@ static int modup_all(ckks_ctx *ctx, const u64 *a, int ell, u64 *ext, u64 *acoeff
         }
         CK(launch_bconv(ctx, l, std::min(ctx->alpha, ell), st));
     }
+    // position-major order: the new limbs of one prime (one per digit) are
+    // adjacent, so the CTAs transforming them run together and share twiddles
     LimbList fw;
-    for (int j = 0; j < beta; ++j) {
-        const int lo = j * ctx->alpha, hi = std::min(lo + ctx->alpha, ell);
-        for (int t = 0; t < ext_n; ++t) {
+    for (int t = 0; t < ext_n; ++t)
+        for (int j = 0; j < beta; ++j) {
+            const int lo = j * ctx->alpha, hi = std::min(lo + ctx->alpha, ell);
             if (t >= lo && t < hi) continue;
             u64 *p = ext + (size_t(j) * ext_n + t) * N;
             fw.add(p, p, ext_prime(ctx, ell, t));
         }
-    }
     return run_ntt(ctx, fw, false, st);
 }
 
@@ -458,9 +459,9 @@ static int moddown_polys(ckks_ctx *ctx, int ell, int npolys, const u64 *const in
                          const u64 *const add[2], uint32_t g, int accumulate, u64 *pcoeff, u64 *w, cudaStream_t st) {
     const size_t N = ctx->N;
     const int k = ctx->k;
-    LimbList inv;
-    for (int p = 0; p < npolys; ++p)
-        for (int m = 0; m < k; ++m) inv.add(in[p] + size_t(ell + m) * N, pcoeff + size_t(p * k + m) * N, ctx->L + m);
+    LimbList inv;  // prime-major: both polynomials' limbs of one prime are adjacent
+    for (int m = 0; m < k; ++m)
+        for (int p = 0; p < npolys; ++p) inv.add(in[p] + size_t(ell + m) * N, pcoeff + size_t(p * k + m) * N, ctx->L + m);
     RC(run_ntt(ctx, inv, true, st));
     BConvLaunch l{};
     l.ngroups = npolys;
@@ -474,16 +475,16 @@ static int moddown_polys(ckks_ctx *ctx, int ell, int npolys, const u64 *const in
     CK(launch_bconv(ctx, l, k, st));
     NttBatch b;
     b.count = npolys * ell;
-    for (int p = 0; p < npolys; ++p)
-        for (int t = 0; t < ell; ++t) {
+    for (int t = 0; t < ell; ++t)
+        for (int p = 0; p < npolys; ++p) {
             u64 *q = w + (size_t(p) * ell + t) * N;
-            b.src[p * ell + t] = q;
-            b.dst[p * ell + t] = q;
-            b.prime[p * ell + t] = uint16_t(t);
+            b.src[t * npolys + p] = q;
+            b.dst[t * npolys + p] = q;
+            b.prime[t * npolys + p] = uint16_t(t);
         }
     Epi e{};
     e.mode = EPI_SCALE;
-    e.nper = ell;
+    e.npolys = npolys;
     for (int p = 0; p < 2; ++p) {
         e.x[p] = p < npolys ? in[p] : nullptr;
         e.out[p] = p < npolys ? out[p] : nullptr;
@@ -516,16 +517,16 @@ static int rescale_polys(ckks_ctx *ctx, int ell, int npolys, const u64 *const in
     CK(launch_bconv(ctx, l, 1, st));
     NttBatch b;
     b.count = npolys * (ell - 1);
-    for (int p = 0; p < npolys; ++p)
-        for (int t = 0; t < ell - 1; ++t) {
+    for (int t = 0; t < ell - 1; ++t)
+        for (int p = 0; p < npolys; ++p) {
             u64 *q = w + (size_t(p) * (ell - 1) + t) * N;
-            b.src[p * (ell - 1) + t] = q;
-            b.dst[p * (ell - 1) + t] = q;
-            b.prime[p * (ell - 1) + t] = uint16_t(t);
+            b.src[t * npolys + p] = q;
+            b.dst[t * npolys + p] = q;
+            b.prime[t * npolys + p] = uint16_t(t);
         }
     Epi e{};
     e.mode = EPI_SCALE;
-    e.nper = ell - 1;
+    e.npolys = npolys;
     for (int p = 0; p < 2; ++p) {
         e.x[p] = p < npolys ? in[p] : nullptr;
         e.out[p] = p < npolys ? out[p] : nullptr;

@@ -159,14 +159,15 @@ struct NttBatch {
 };
 
 // Epilogue of the last forward pass.  EPI_STORE writes the transform.
-// EPI_SCALE treats batch limb l as limb (l % nper) of polynomial (l / nper):
+// EPI_SCALE treats batch limb l as limb (l / npolys) of polynomial (l % npolys)
+// (the polynomials' limbs of one prime are adjacent in the batch):
 //   out = (x - ntt) * c  [+ add[perm_g(n)]]  [+ out if accumulate]
 // with c = cmul[prime] (value, Shoup companion).  This is the last step of
 // ModDown (c = P^-1) and Rescale (c = q_{ell-1}^-1).
 enum { EPI_STORE = 0, EPI_SCALE = 1 };
 struct Epi {
     int mode;
-    int nper;
+    int npolys;
     const u64 *x[2];
     u64 *out[2];
     const u64 *add[2];

@@ -61,7 +61,7 @@ __device__ __forceinline__ void gs_bfly(u64 &X, u64 &Y, ulonglong2 w, u64 p, u64
 }
 
 template <int LOGN, int LOGR, int A, int C, bool INV, bool CONTIG, bool EPI, bool SMALLP>
-__global__ void __launch_bounds__((1 << (LOGR - A)) * C, A <= 4 ? 4 : 2)
+__global__ void __launch_bounds__((1 << (LOGR - A)) * C, (A <= 4 ? 1024 : 512) / ((1 << (LOGR - A)) * C))
 ntt_pass_kernel(NttBatch batch, const PrimeInfo *__restrict__ pinfo, const ulonglong2 *__restrict__ tw_all, Epi epi) {
     constexpr int B = LOGR - A;
     constexpr int TPC = 1 << B;   // threads per column
@@ -77,7 +77,7 @@ ntt_pass_kernel(NttBatch batch, const PrimeInfo *__restrict__ pinfo, const ulong
     constexpr int L1 = LOGN - L2;
     constexpr uint32_t N = 1u << LOGN;
     constexpr int logN = LOGN;
-    const int limb = blockIdx.y;
+    const int limb = blockIdx.x;  // limbs sharing a prime are adjacent: co-resident CTAs reuse twiddles
     const int prime = batch.prime[limb];
     const u64 *__restrict__ src = batch.src[limb];
     u64 *dst = batch.dst[limb];
@@ -88,7 +88,7 @@ ntt_pass_kernel(NttBatch batch, const PrimeInfo *__restrict__ pinfo, const ulong
     const int tid = threadIdx.x;
     const int g = CONTIG ? (tid % TPC) : (tid / C);
     const int cl = CONTIG ? (tid / TPC) : (tid % C);
-    const uint32_t col = blockIdx.x * C + cl;
+    const uint32_t col = blockIdx.y * C + cl;
     constexpr int s0 = CONTIG ? L1 : 0;
     const uint32_t prefix = CONTIG ? col : 0;
 
@@ -111,22 +111,22 @@ ntt_pass_kernel(NttBatch batch, const PrimeInfo *__restrict__ pinfo, const ulong
     // (stage sigma uses C * 2^sigma consecutive entries) and, for the ModDown
     // epilogue, the x and add tiles into L2 while the data loads run.
     if (CONTIG && tid == 0) {
-        const size_t col0 = size_t(blockIdx.x) * C;
+        const size_t col0 = size_t(blockIdx.y) * C;
 #pragma unroll
         for (int sg = 0; sg < LOGR; sg++) {
             const ulonglong2 *t0 = tw + (size_t(1) << (s0 + sg)) + (col0 << sg);
             l2_prefetch(t0, uint32_t(C * sizeof(ulonglong2)) << sg);
         }
         if (EPI && epi.mode == EPI_SCALE) {
-            const int poly = limb / epi.nper;
-            const size_t base = size_t(limb % epi.nper) * N + (col0 << L2);
+            const int poly = limb % epi.npolys;
+            const size_t base = size_t(limb / epi.npolys) * N + (col0 << L2);
             l2_prefetch(epi.x[poly] + base, uint32_t(C * sizeof(u64)) << L2);
             if (epi.accumulate) l2_prefetch(epi.out[poly] + base, uint32_t(C * sizeof(u64)) << L2);
             if (epi.add[poly] != nullptr) {
                 for (int b = 0; b < C; b++) {
                     const uint32_t first = uint32_t((col0 + b) << L2);
                     const uint32_t sblk = (epi.galois == 1 ? first : automorph_src(first, epi.galois, logN)) >> L2;
-                    l2_prefetch(epi.add[poly] + size_t(limb % epi.nper) * N + (size_t(sblk) << L2),
+                    l2_prefetch(epi.add[poly] + size_t(limb / epi.npolys) * N + (size_t(sblk) << L2),
                                 uint32_t(sizeof(u64)) << L2);
                 }
             }
@@ -179,8 +179,8 @@ ntt_pass_kernel(NttBatch batch, const PrimeInfo *__restrict__ pinfo, const ulong
             int poly = 0;
             size_t base = 0;
             if (EPI) {
-                poly = limb / epi.nper;
-                base = size_t(limb % epi.nper) * N;
+                poly = limb % epi.npolys;
+                base = size_t(limb / epi.npolys) * N;
                 c = epi.cmul[prime];
             }
 #pragma unroll
@@ -198,7 +198,7 @@ ntt_pass_kernel(NttBatch batch, const PrimeInfo *__restrict__ pinfo, const ulong
                 const u64 *__restrict__ xp = epi.x[poly] + base;
                 const u64 *__restrict__ ap = epi.add[poly] == nullptr ? nullptr : epi.add[poly] + base;
                 u64 *op = epi.out[poly] + base;
-                constexpr int GRP = E < 8 ? E : 8;
+                constexpr int GRP = E < 4 ? E : 4;
 #pragma unroll
                 for (int k0 = 0; k0 < E; k0 += GRP) {
                     u64 xv[GRP], av[GRP], ov[GRP];
@@ -303,13 +303,16 @@ cudaError_t launch_one_p(const NttBatch &b, const ckks_ctx *ctx, const Epi &epi,
     constexpr int B = LOGR - A;
     constexpr int TPC = 1 << B;
     constexpr int R = 1 << LOGR;
-    // C = columns (pass S) or blocks (pass C) per CTA: 256 threads, clamped to
-    // the number of columns / blocks of the matrix view
-    constexpr int C = (256 / TPC) < (1 << OTHER) ? (256 / TPC) : (1 << OTHER);
+    // C = columns (pass S) or blocks (pass C) per CTA: small CTAs (128 threads
+    // for pass S, 64 for pass C, measured best at N=2^16) keep barriers local and
+    // let many independent CTAs hide the load latency; clamped to the number of
+    // columns / blocks of the matrix view
+    constexpr int WANT = (CONTIG ? 64 : 128) / TPC > 0 ? (CONTIG ? 64 : 128) / TPC : 1;
+    constexpr int C = WANT < (1 << OTHER) ? WANT : (1 << OTHER);
     const size_t smem = CONTIG ? size_t(C) * (R + TPC) * 8 : size_t(R) * C * 8 + size_t(R) * 16;
     auto kern = ntt_pass_kernel<LOGN, LOGR, A, C, INV, CONTIG, EPI, SMALLP>;
     if (set_attr) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    dim3 grid((1 << OTHER) / C, b.count);
+    dim3 grid(b.count, (1 << OTHER) / C);
     kern<<<grid, TPC * C, smem, st>>>(b, ctx->d_pinfo, INV ? ctx->d_tw_inv : ctx->d_tw_fwd, epi);
     return cudaGetLastError();
 }
