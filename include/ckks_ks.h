@@ -165,6 +165,32 @@ int ckks_hrotate(ckks_ctx *ctx, const uint64_t *d_a, const uint64_t *d_b, int le
                  const uint32_t *galois, const uint64_t *const *d_keys, uint64_t *const *d_oa,
                  uint64_t *const *d_ob, void *ws, ckks_stream_t stream);
 
+/* Batched key switching: n independent ciphertexts, each at its own level
+ * levels[i] (1..L) and with its own key, processed together so that every
+ * step of the pipeline is one kernel launch over the whole batch (iNTT of the
+ * inputs, ModUp's basis conversion, NTT of the new limbs, KSKInnerProd, iNTT
+ * of the P-limbs, ModDown's basis conversion, NTT + scale), in batches of 64.
+ * The arithmetic per ciphertext is that of the single-ciphertext calls, and
+ * so are the bits of every result:
+ *   d_b == NULL or d_b[i] == NULL: KeySwitch of d_a[i] with d_keys[i]
+ *     (as ckks_keyswitch; galois[i] is ignored, galois may be NULL);
+ *   otherwise: HRotate of (d_a[i], d_b[i]) by the one Galois element
+ *     galois[i] with its rotation key d_keys[i] (Algorithm 4 with r = 1, as
+ *     ckks_hrotate).
+ * Every array is a host array of length n; the pointers in it are device
+ * pointers.  Inputs are [levels[i]][N] (evaluation form); d_oa[i], d_ob[i]
+ * receive [levels[i]][N] and must not overlap any input or each other.  Keys
+ * are [dnum][2][L+k][N] and may be shared between entries.  The workspace
+ * holds every ciphertext's intermediates at once: its size comes from
+ * ckks_batch_workspace_bytes with the same levels.  Contexts whose primes are
+ * too wide for the split basis conversion run the entries one after another.
+ * Returns CKKS_EINVAL for n < 0, a level out of range, a null or misaligned
+ * pointer, or an invalid Galois element of a rotation entry. */
+int ckks_batch_workspace_bytes(const ckks_ctx *ctx, int n, const int *levels, size_t *bytes);
+int ckks_keyswitch_batch(ckks_ctx *ctx, int n, const uint64_t *const *d_a, const uint64_t *const *d_b,
+                         const int *levels, const uint32_t *galois, const uint64_t *const *d_keys,
+                         uint64_t *const *d_oa, uint64_t *const *d_ob, void *ws, ckks_stream_t stream);
+
 /* PtMatVecMult with hoisted ModUp and ModDown (Algorithm 8) in baby-step /
  * giant-step form (Sec. 5.2): nb baby steps, ng giant steps, diagonal (t, i) =
  * d_diag[t*nb + i], an [ell+k][N] evaluation-form plaintext over the extended

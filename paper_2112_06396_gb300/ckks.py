@@ -60,6 +60,10 @@ _SIGS = {
                                ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                ctypes.POINTER(_vp), _i, _vp, _vp, _vp, _vp]),
     "ckks_keygen_ksk": (_i, [_vp, _vp, _vp, _vp, ctypes.c_uint32, _vp, _vp, _vp]),
+    "ckks_batch_workspace_bytes": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_size_t)]),
+    "ckks_keyswitch_batch": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_i),
+                                  ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                  ctypes.POINTER(_vp), _vp, _vp]),
     "ckks_moddown_noalloc": (_i, [_vp, _vp, _i, _vp, _vp]),
     "ckks_profile_enable": (_i, [_vp, _i]),
     "ckks_profile_reset": (_i, [_vp]),
@@ -276,6 +280,32 @@ class Context:
         oa = (_vp * r)(*[o[0].data_ptr() for o in outs])
         ob = (_vp * r)(*[o[1].data_ptr() for o in outs])
         _check(lib().ckks_hrotate(self._h, _p(a), _p(b), level, r, g, kp, oa, ob, _p(ws), _stream(stream)), self._h)
+        return outs
+
+    def batch_workspace(self, levels):
+        n = len(levels)
+        lv = (_i * max(n, 1))(*[int(x) for x in levels])
+        nbytes = ctypes.c_size_t()
+        _check(lib().ckks_batch_workspace_bytes(self._h, n, lv, ctypes.byref(nbytes)))
+        return torch.empty(max(nbytes.value // 8, 2), dtype=torch.uint64, device=self.device)
+
+    def keyswitch_batch(self, a, b, levels, galois, keys, outs=None, ws=None, stream=None):
+        """Batched key switching.  a, keys: lists of tensors; b: None or a list
+        whose None entries make KeySwitch entries (others are one-rotation
+        HRotates by galois[i]); levels: list of ints.  Returns [(oa, ob)]."""
+        n = len(a)
+        if outs is None:
+            outs = [(self.empty(levels[i]), self.empty(levels[i])) for i in range(n)]
+        ws = self.batch_workspace(levels) if ws is None else ws
+        m = max(n, 1)
+        ap = (_vp * m)(*[x.data_ptr() for x in a])
+        bp = None if b is None else (_vp * m)(*[None if x is None else x.data_ptr() for x in b])
+        lv = (_i * m)(*[int(x) for x in levels])
+        gp = None if galois is None else (ctypes.c_uint32 * m)(*[int(x) for x in galois])
+        kp = (_vp * m)(*[x.data_ptr() for x in keys])
+        oa = (_vp * m)(*[o[0].data_ptr() for o in outs])
+        ob = (_vp * m)(*[o[1].data_ptr() for o in outs])
+        _check(lib().ckks_keyswitch_batch(self._h, n, ap, bp, lv, gp, kp, oa, ob, _p(ws), _stream(stream)), self._h)
         return outs
 
     def ptmatvecmult(self, a, b, level, nb, ng, g_baby, g_giant, key_baby, key_giant, diags, rescale=True,

@@ -428,7 +428,9 @@ static int modup_all(ckks_ctx *ctx, const u64 *a, int ell, u64 *ext, u64 *acoeff
     for (int j0 = 0; j0 < beta; j0 += kMaxGroups) {
         BConvLaunch l{};
         l.ngroups = std::min(beta - j0, kMaxGroups);
-        l.chunk = ext_n;
+        // targets per digit: every position outside the digit (the smallest,
+        // last digit has the most)
+        l.chunk = ext_n - std::min(ctx->alpha, ell - (beta - 1) * ctx->alpha);
         l.chunks = 1;
         for (int g = 0; g < l.ngroups; ++g) {
             const int j = j0 + g;
@@ -674,7 +676,7 @@ extern "C" int ckks_modup(ckks_ctx *ctx, const uint64_t *a, int ell, int digit, 
     RC(run_ntt(ctx, inv, true, st));
     BConvLaunch l{};
     l.ngroups = 1;
-    l.chunk = ext_n;
+    l.chunk = ext_n - (hi - lo);
     l.chunks = 1;
     l.g[0].plan = ctx->d_modup + size_t(ell) * ctx->dnum + digit;
     l.g[0].src = acoeff;
@@ -756,6 +758,89 @@ extern "C" int ckks_hrotate(ckks_ctx *ctx, const uint64_t *a, const uint64_t *b,
         u64 *out[2] = {oa[i], ob[i]};
         const u64 *add[2] = {nullptr, b};
         RC(moddown_polys(ctx, ell, 2, in, out, add, galois[i], 0, w + lo.tmp, w + lo.tmp + size_t(2) * ctx->k * N, st));
+    }
+    return CKKS_OK;
+}
+
+// ---- batched key switching
+// Per-ciphertext workspace: the HRotate layout of its level, packed in batch order.
+static size_t batch_ws_words(const ckks_ctx *c, int n, const int *levels) {
+    size_t w = 0;
+    for (int i = 0; i < n; ++i) w += hr_layout(c, levels[i]).total;
+    return w;
+}
+
+extern "C" int ckks_batch_workspace_bytes(const ckks_ctx *ctx, int n, const int *levels, size_t *bytes) {
+    if (ctx == nullptr || bytes == nullptr || n < 0 || (n > 0 && levels == nullptr)) return CKKS_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (!level_ok(ctx, levels[i])) return CKKS_EINVAL;
+    *bytes = batch_ws_words(ctx, n, levels) * sizeof(u64);
+    return CKKS_OK;
+}
+
+// One ciphertext of a batch on its own (contexts without the split conversion).
+static int batch_one(ckks_ctx *ctx, const CtDesc &c, cudaStream_t st) {
+    const size_t N = ctx->N;
+    const HrLayout lo = hr_layout(ctx, c.ell);
+    RC(modup_all(ctx, c.a, c.ell, c.ws + lo.ext, c.ws + lo.tmp, st));
+    u64 *u = c.ws + lo.uv, *v = u + size_t(c.ell + ctx->k) * N;
+    InnerArgs ia{c.ws + lo.ext, c.a, c.key, u, v, c.ell, c.galois};
+    CK(launch_inner_prod(ctx, ia, st));
+    const u64 *in[2] = {u, v};
+    u64 *out[2] = {c.oa, c.ob};
+    const u64 *add[2] = {nullptr, c.b};
+    return moddown_polys(ctx, c.ell, 2, in, out, add, c.galois, 0, c.ws + lo.tmp,
+                         c.ws + lo.tmp + size_t(2) * ctx->k * N, st);
+}
+
+extern "C" int ckks_keyswitch_batch(ckks_ctx *ctx, int n, const uint64_t *const *a, const uint64_t *const *b,
+                                    const int *levels, const uint32_t *galois, const uint64_t *const *keys,
+                                    uint64_t *const *oa, uint64_t *const *ob, void *ws, ckks_stream_t stream) {
+    if (ctx == nullptr || n < 0) return CKKS_EINVAL;
+    if (n == 0) return CKKS_OK;
+    if (!a || !levels || !keys || !oa || !ob || !al16(ws)) return CKKS_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        const bool rot = b != nullptr && b[i] != nullptr;
+        if (!level_ok(ctx, levels[i]) || !al16(a[i]) || !al16(keys[i]) || !al16(oa[i]) || !al16(ob[i]))
+            return CKKS_EINVAL;
+        if (rot && (!al16(b[i]) || galois == nullptr || !galois_ok(ctx, galois[i]))) return CKKS_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    u64 *w = static_cast<u64 *>(ws);
+    for (int c0 = 0; c0 < n; c0 += kMaxCts) {
+        KsBatchDesc d{};
+        d.n = std::min(n - c0, kMaxCts);
+        d.L = ctx->L;
+        d.k = ctx->k;
+        d.alpha = ctx->alpha;
+        d.dnum = ctx->dnum;
+        d.logN = ctx->logN;
+        for (int c = 0; c < d.n; ++c) {
+            const int i = c0 + c;
+            const bool rot = b != nullptr && b[i] != nullptr;
+            CtDesc &x = d.ct[c];
+            x.a = a[i];
+            x.b = rot ? b[i] : nullptr;
+            x.key = keys[i];
+            x.oa = oa[i];
+            x.ob = ob[i];
+            x.ws = w;
+            x.ell = levels[i];
+            x.galois = rot ? galois[i] : 1u;
+            w += hr_layout(ctx, levels[i]).total;
+        }
+        if (!ctx->split_bits) {
+            for (int c = 0; c < d.n; ++c) RC(batch_one(ctx, d.ct[c], st));
+            continue;
+        }
+        // one launch per phase over the whole batch
+        CK(launch_ntt_batch(ctx, d, PH_INTT_A, st));
+        CK(launch_bconv_batch(ctx, d, 0, st));
+        CK(launch_ntt_batch(ctx, d, PH_NTT_UP, st));
+        CK(launch_inner_prod_batch(ctx, d, st));
+        CK(launch_ntt_batch(ctx, d, PH_INTT_P, st));
+        CK(launch_bconv_batch(ctx, d, 1, st));
+        CK(launch_ntt_batch(ctx, d, PH_NTT_DOWN, st));
     }
     return CKKS_OK;
 }

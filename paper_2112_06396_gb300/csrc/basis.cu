@@ -8,6 +8,7 @@
 // A thread owns two adjacent coefficients (16-byte loads and stores), keeps its
 // y_i in registers and produces every target limb of its chunk, so each source
 // word is read once per chunk and each target word is written once.
+#include "batch.cuh"
 #include "common.cuh"
 #include "internal.h"
 
@@ -72,16 +73,16 @@ __global__ void __launch_bounds__(256) bconv_kernel(BConvLaunch L, const PrimeIn
 // Shoup fold of A by [2^W]_t and one final reduction.  A CTA converts all
 // targets of its group for 256 coefficients; the constants of the group sit
 // in shared memory and every source word is read and scaled exactly once.
-template <int NS>
-__global__ void __launch_bounds__(128) bconv_split_kernel(BConvLaunch L, const PrimeInfo *__restrict__ pinfo, int logN,
-                                                          int W) {
+template <int NS, class GMAP>
+__global__ void __launch_bounds__(128) bconv_split_kernel(const __grid_constant__ GMAP gm, int chunks, int chunk,
+                                                          const PrimeInfo *__restrict__ pinfo, int logN, int W) {
     extern __shared__ uint4 smat[];  // [n_dst][NS] then the per-target constants
-    const BConvGroup G = L.g[blockIdx.y / L.chunks];
+    const BConvGroup G = gm.get(blockIdx.y / chunks);
     const BConvPlan *__restrict__ plan = G.plan;
     const size_t N = size_t(1) << logN;
     const int n_src = plan->n_src;
-    const int t0 = (blockIdx.y % L.chunks) * L.chunk;  // this CTA's targets: t0 .. t0+n_dst-1
-    const int n_dst = min(plan->n_dst - t0, L.chunk);
+    const int t0 = (blockIdx.y % chunks) * chunk;  // this CTA's targets: t0 .. t0+n_dst-1
+    const int n_dst = min(plan->n_dst - t0, chunk);
     if (n_dst <= 0) return;
     struct Dst {
         u64 p, one_s, rw, rw_s, sub, pos;
@@ -154,41 +155,67 @@ __global__ void __launch_bounds__(128) bconv_split_kernel(BConvLaunch L, const P
     }
 }
 
+// Split conversion over `ngroups` groups of up to n_all targets each: targets
+// in chunks of at most 12 per CTA row (enough CTAs to fill the SMs while each
+// source word is still scaled once per 12 targets).
+template <class GMAP>
+static cudaError_t launch_split(const ckks_ctx *ctx, const GMAP &gm, int ngroups, int n_all, int max_src,
+                                cudaStream_t st) {
+    const int chunks = (n_all + 11) / 12;
+    const int chunk = (n_all + chunks - 1) / chunks;
+    const int tpb = 128;
+    dim3 grid(unsigned((ctx->N / 2 + tpb - 1) / tpb), unsigned(ngroups * chunks));
+    ProfScope ps(ctx, K_BCONV, double(ngroups) * n_all, st);
+    const int W = ctx->split_bits;
+    auto smem = [&](int ns) { return size_t(chunk) * ns * sizeof(uint4) + size_t(chunk) * 48; };
+#define CKKS_BCONV_SPLIT(NSV)                                                                                      \
+    do {                                                                                                           \
+        auto kern = bconv_split_kernel<NSV, GMAP>;                                                                 \
+        if (smem(NSV) > 48 * 1024)                                                                                 \
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem(NSV)));               \
+        kern<<<grid, tpb, smem(NSV), st>>>(gm, chunks, chunk, ctx->d_pinfo, ctx->logN, W);                         \
+    } while (0)
+    if (max_src <= 1) CKKS_BCONV_SPLIT(1);
+    else if (max_src <= 2) CKKS_BCONV_SPLIT(2);
+    else if (max_src <= 3) CKKS_BCONV_SPLIT(3);
+    else if (max_src <= 4) CKKS_BCONV_SPLIT(4);
+    else if (max_src <= 6) CKKS_BCONV_SPLIT(6);
+    else if (max_src <= 8) CKKS_BCONV_SPLIT(8);
+    else if (max_src <= 12) CKKS_BCONV_SPLIT(12);
+    else if (max_src <= 16) CKKS_BCONV_SPLIT(16);
+    else if (max_src <= 24) CKKS_BCONV_SPLIT(24);
+    else CKKS_BCONV_SPLIT(32);
+#undef CKKS_BCONV_SPLIT
+    return cudaGetLastError();
+}
+
+// The basis conversions of one batched key-switching phase (ModUp digits or
+// ModDown polynomials of every ciphertext).  Needs the split conversion.
+cudaError_t launch_bconv_batch(const ckks_ctx *ctx, const KsBatchDesc &d, int down, cudaStream_t st) {
+    GroupMapBatch gm;
+    gm.d = d;
+    gm.down = down;
+    gm.modup = ctx->d_modup;
+    gm.moddown = ctx->d_moddown;
+    int groups = 0, n_all = 0;
+    for (int c = 0; c < d.n; ++c) {
+        const int ell = d.ct[c].ell, beta = (ell + d.alpha - 1) / d.alpha;
+        gm.d.pre[c] = groups;
+        groups += down ? 2 : beta;
+        n_all = std::max(n_all, down ? ell : ell + d.k - std::min(d.alpha, ell - (beta - 1) * d.alpha));
+    }
+    gm.d.pre[d.n] = groups;
+    if (groups == 0) return cudaSuccess;
+    return launch_split(ctx, gm, groups, n_all, down ? d.k : d.alpha, st);
+}
+
 cudaError_t launch_bconv(const ckks_ctx *ctx, const BConvLaunch &l, int max_src, cudaStream_t st) {
     if (l.ngroups == 0) return cudaSuccess;
     const int threads = 256;
     if (ctx->split_bits && max_src <= kMaxSrc) {
-        // targets in chunks of at most 12 per CTA row: enough CTAs to fill the
-        // SMs while each source word is still scaled once per 12 targets
-        BConvLaunch s = l;
-        const int n_all = l.chunk * l.chunks;
-        s.chunks = (n_all + 11) / 12;
-        s.chunk = (n_all + s.chunks - 1) / s.chunks;
-        const int n_dst = s.chunk;
-        const int tpb = 128;
-        dim3 grid(unsigned((ctx->N / 2 + tpb - 1) / tpb), unsigned(s.ngroups * s.chunks));
-        ProfScope ps(ctx, K_BCONV, double(l.ngroups) * n_all, st);
-        const int W = ctx->split_bits;
-        auto smem = [&](int ns) { return size_t(n_dst) * ns * sizeof(uint4) + size_t(n_dst) * 48; };
-#define CKKS_BCONV_SPLIT(NSV)                                                                                      \
-    do {                                                                                                           \
-        auto kern = bconv_split_kernel<NSV>;                                                                       \
-        if (smem(NSV) > 48 * 1024)                                                                                 \
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem(NSV)));               \
-        kern<<<grid, tpb, smem(NSV), st>>>(s, ctx->d_pinfo, ctx->logN, W);                                         \
-    } while (0)
-        if (max_src <= 1) CKKS_BCONV_SPLIT(1);
-        else if (max_src <= 2) CKKS_BCONV_SPLIT(2);
-        else if (max_src <= 3) CKKS_BCONV_SPLIT(3);
-        else if (max_src <= 4) CKKS_BCONV_SPLIT(4);
-        else if (max_src <= 6) CKKS_BCONV_SPLIT(6);
-        else if (max_src <= 8) CKKS_BCONV_SPLIT(8);
-        else if (max_src <= 12) CKKS_BCONV_SPLIT(12);
-        else if (max_src <= 16) CKKS_BCONV_SPLIT(16);
-        else if (max_src <= 24) CKKS_BCONV_SPLIT(24);
-        else CKKS_BCONV_SPLIT(32);
-#undef CKKS_BCONV_SPLIT
-        return cudaGetLastError();
+        GroupMapList gm;
+        gm.l = l;
+        return launch_split(ctx, gm, l.ngroups, l.chunk * l.chunks, max_src, st);
     }
     dim3 grid(unsigned((ctx->N / 2 + threads - 1) / threads), unsigned(l.ngroups * l.chunks));
     ProfScope ps(ctx, K_BCONV, double(l.ngroups) * l.chunk, st);

@@ -1,0 +1,216 @@
+// batch.cuh -- where each limb (NTT launches), group (basis conversions) and
+// position (inner products) of a launch reads and writes.
+//
+// Single operations describe their limbs with explicit pointer lists in the
+// launch parameters (MapList).  Batched key switching (many ciphertexts at
+// their own levels, each with its own key and Galois element, in one launch
+// per phase) describes only the ciphertexts (KsBatchDesc) and every kernel
+// derives its limb's pointers on the device from a prefix sum over the
+// per-ciphertext counts of its phase.
+#pragma once
+
+#include "common.cuh"
+
+namespace ckks {
+
+// One limb of an NTT launch.  The epilogue operands are used by launches with
+// the ModDown/Rescale epilogue: out = (x - ntt) * cmul[prime] [+ add at the
+// Automorph_galois slot] [+ out].
+struct LimbIO {
+    const u64 *src;
+    u64 *dst;
+    int prime;
+    const u64 *ex;
+    u64 *eout;
+    const u64 *eadd;
+    uint32_t galois;
+    int accumulate;
+};
+
+// Explicit limb list (single operations).
+struct MapList {
+    NttBatch b;
+    Epi e;
+    int second;  // second pass of a transform: read the first pass's output in place
+    __device__ __forceinline__ LimbIO get(int l, uint32_t N) const {
+        LimbIO io;
+        io.src = second ? b.dst[l] : b.src[l];
+        io.dst = b.dst[l];
+        io.prime = b.prime[l];
+        io.ex = nullptr;
+        io.eout = nullptr;
+        io.eadd = nullptr;
+        io.galois = 1;
+        io.accumulate = 0;
+        if (e.mode == EPI_SCALE) {
+            const int poly = l % e.npolys;
+            const size_t base = size_t(l / e.npolys) * N;
+            io.ex = e.x[poly] + base;
+            io.eout = e.out[poly] + base;
+            io.eadd = e.add[poly] == nullptr ? nullptr : e.add[poly] + base;
+            io.galois = e.galois;
+            io.accumulate = e.accumulate;
+        }
+        return io;
+    }
+    __device__ __forceinline__ const ulonglong2 *cmul() const { return e.cmul; }
+};
+
+// ---------------------------------------------------------------- batched key switching
+constexpr int kMaxCts = 64;
+
+// One ciphertext of a batch.  b == nullptr: KeySwitch of a (outputs u, v);
+// otherwise HRotate with one rotation (Algorithm 4): (u, v + Automorph_g(b)).
+// ws: this ciphertext's workspace, laid out for its level:
+//   ext [beta][ell+k][N] | uv [2][ell+k][N] | tmp (acoeff [ell][N], later
+//   pcoeff [2][k][N] and w [2][ell][N]).
+struct CtDesc {
+    const u64 *a, *b, *key;
+    u64 *oa, *ob, *ws;
+    int ell;
+    uint32_t galois;
+};
+
+struct KsBatchDesc {
+    int n;
+    int L, k, alpha, dnum, logN;
+    CtDesc ct[kMaxCts];
+    int pre[kMaxCts + 1];  // prefix sums of this launch's per-ciphertext counts
+};
+
+struct CtLayout {
+    int beta, ext;
+    u64 *extp, *uv, *acoeff, *pcoeff, *w;
+};
+
+__host__ __device__ __forceinline__ CtLayout ct_layout(const KsBatchDesc &d, const CtDesc &c) {
+    CtLayout o;
+    const size_t N = size_t(1) << d.logN;
+    o.beta = (c.ell + d.alpha - 1) / d.alpha;
+    o.ext = c.ell + d.k;
+    o.extp = c.ws;
+    o.uv = c.ws + size_t(o.beta) * o.ext * N;
+    o.acoeff = o.uv + size_t(2) * o.ext * N;
+    o.pcoeff = o.acoeff;
+    o.w = o.pcoeff + size_t(2) * d.k * N;
+    return o;
+}
+
+// index l of a phase -> (ciphertext, index within it)
+__device__ __forceinline__ int batch_find(const KsBatchDesc &d, int l, int &i) {
+    int lo = 0, hi = d.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (d.pre[mid] <= l) lo = mid;
+        else hi = mid - 1;
+    }
+    i = l - d.pre[lo];
+    return lo;
+}
+
+// Per-ciphertext counts of the batched phases.
+enum { PH_INTT_A = 0, PH_NTT_UP = 1, PH_INTT_P = 2, PH_NTT_DOWN = 3 };
+__host__ __device__ __forceinline__ int phase_count(const KsBatchDesc &d, int ell, int phase) {
+    const int beta = (ell + d.alpha - 1) / d.alpha;
+    switch (phase) {
+    case PH_INTT_A: return ell;
+    case PH_NTT_UP: return beta * (ell + d.k) - ell;
+    case PH_INTT_P: return 2 * d.k;
+    default: return 2 * ell;
+    }
+}
+
+struct MapBatch {
+    KsBatchDesc d;
+    int phase;
+    int second;            // second pass: in place on the first pass's output
+    const ulonglong2 *cm;  // [P^-1]_q per prime (ModDown epilogue)
+    __device__ __forceinline__ LimbIO get(int l, uint32_t N) const {
+        int i;
+        const int c = batch_find(d, l, i);
+        const CtDesc &ct = d.ct[c];
+        const CtLayout lo = ct_layout(d, ct);
+        const int ell = ct.ell;
+        LimbIO io;
+        io.ex = nullptr;
+        io.eout = nullptr;
+        io.eadd = nullptr;
+        io.galois = 1;
+        io.accumulate = 0;
+        if (phase == PH_INTT_A) {
+            io.src = ct.a + size_t(i) * N;
+            io.dst = lo.acoeff + size_t(i) * N;
+            io.prime = i;
+        } else if (phase == PH_NTT_UP) {
+            // new ModUp limbs in position-major order: a chain position t < ell
+            // appears for the beta-1 digits that do not hold it, a special
+            // position for every digit
+            int t, j;
+            const int bm1 = lo.beta - 1;
+            if (i < ell * bm1) {
+                t = i / bm1;
+                const int r = i % bm1;
+                j = r < t / d.alpha ? r : r + 1;
+            } else {
+                const int i2 = i - ell * bm1;
+                t = ell + i2 / lo.beta;
+                j = i2 % lo.beta;
+            }
+            u64 *p = lo.extp + (size_t(j) * lo.ext + t) * N;
+            io.src = p;
+            io.dst = p;
+            io.prime = t < ell ? t : d.L + (t - ell);
+        } else if (phase == PH_INTT_P) {
+            const int m = i >> 1, poly = i & 1;
+            io.src = lo.uv + (size_t(poly) * lo.ext + ell + m) * N;
+            io.dst = lo.pcoeff + (size_t(poly) * d.k + m) * N;
+            io.prime = d.L + m;
+        } else {
+            const int t = i >> 1, poly = i & 1;
+            u64 *p = lo.w + (size_t(poly) * ell + t) * N;
+            io.src = p;
+            io.dst = p;
+            io.prime = t;
+            io.ex = lo.uv + (size_t(poly) * lo.ext + t) * N;
+            io.eout = (poly ? ct.ob : ct.oa) + size_t(t) * N;
+            io.eadd = (poly && ct.b != nullptr) ? ct.b + size_t(t) * N : nullptr;
+            io.galois = ct.galois;
+        }
+        if (second) io.src = io.dst;
+        return io;
+    }
+    __device__ __forceinline__ const ulonglong2 *cmul() const { return cm; }
+};
+
+// Basis-conversion groups.
+struct GroupMapList {
+    BConvLaunch l;
+    __device__ __forceinline__ BConvGroup get(int gi) const { return l.g[gi]; }
+};
+
+struct GroupMapBatch {
+    KsBatchDesc d;
+    int down;                   // 0: ModUp digits, 1: ModDown polynomials
+    const BConvPlan *modup;     // [(L+1)*dnum]
+    const BConvPlan *moddown;   // [L+1]
+    __device__ __forceinline__ BConvGroup get(int gi) const {
+        int i;
+        const int c = batch_find(d, gi, i);
+        const CtDesc &ct = d.ct[c];
+        const CtLayout lo = ct_layout(d, ct);
+        const size_t N = size_t(1) << d.logN;
+        BConvGroup g;
+        if (!down) {
+            g.plan = modup + size_t(ct.ell) * d.dnum + i;
+            g.src = lo.acoeff + size_t(i) * d.alpha * N;
+            g.dst = lo.extp + size_t(i) * lo.ext * N;
+        } else {
+            g.plan = moddown + ct.ell;
+            g.src = lo.pcoeff + size_t(i) * d.k * N;
+            g.dst = lo.w + size_t(i) * ct.ell * N;
+        }
+        return g;
+    }
+};
+
+}  // namespace ckks

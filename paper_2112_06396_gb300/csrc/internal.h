@@ -5,6 +5,7 @@
 #include <cstddef>
 #include <vector>
 
+#include "batch.cuh"
 #include "common.cuh"
 
 struct ckks_ctx {
@@ -83,7 +84,9 @@ inline int beta_of(const ckks_ctx *c, int ell) { return (ell + c->alpha - 1) / c
 cudaError_t ntt_set_attributes(const ckks_ctx *ctx);
 cudaError_t launch_ntt_fwd(const ckks_ctx *ctx, const NttBatch &b, const Epi *epi, cudaStream_t st);
 cudaError_t launch_ntt_inv(const ckks_ctx *ctx, const NttBatch &b, cudaStream_t st);
+cudaError_t launch_ntt_batch(const ckks_ctx *ctx, const KsBatchDesc &d, int phase, cudaStream_t st);
 cudaError_t launch_bconv(const ckks_ctx *ctx, const BConvLaunch &l, int max_src, cudaStream_t st);
+cudaError_t launch_bconv_batch(const ckks_ctx *ctx, const KsBatchDesc &d, int down, cudaStream_t st);
 
 // keyswitch.cu
 struct InnerArgs {
@@ -95,6 +98,7 @@ struct InnerArgs {
     uint32_t galois;     // 1 = no automorphism
 };
 cudaError_t launch_inner_prod(const ckks_ctx *ctx, const InnerArgs &a, cudaStream_t st);
+cudaError_t launch_inner_prod_batch(const ckks_ctx *ctx, const KsBatchDesc &d, cudaStream_t st);
 
 struct PmvArgs {
     const u64 *ext;      // hoisted ModUp outputs [beta][ell+k][N]

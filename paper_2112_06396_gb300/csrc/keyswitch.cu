@@ -7,6 +7,7 @@
 // slot pair (2n, 2n+1) reads one aligned source pair, swapped when the image
 // of 2n is odd.  Gathers therefore stay 16-byte vector loads and every warp
 // touches whole 256-byte segments.
+#include "batch.cuh"
 #include "common.cuh"
 #include "internal.h"
 
@@ -105,6 +106,88 @@ cudaError_t launch_inner_prod(const ckks_ctx *ctx, const InnerArgs &a, cudaStrea
     case 4: inner_prod_kernel<4><<<grid, threads, 0, st>>>(a, ctx->d_pinfo, ctx->logN, ctx->L, ctx->k, ctx->alpha); break;
     default:
         inner_prod_kernel_any<<<grid, threads, 0, st>>>(a, ctx->d_pinfo, ctx->logN, ctx->L, ctx->k, ctx->alpha);
+    }
+    return cudaGetLastError();
+}
+
+// Batched KSKInnerProd: grid.y runs over the extended positions of every
+// ciphertext of the batch (ell_c + k each).  Each ciphertext reads its own
+// digits (its workspace), its own key and its own Galois element; its u, v land
+// in its workspace.  BMAX > 0: the digit loop is unrolled to BMAX with every
+// load issued up front; BMAX == 0: plain loop.
+template <int BMAX>
+__global__ void __launch_bounds__(256) inner_prod_batch_kernel(const __grid_constant__ KsBatchDesc d,
+                                                               const PrimeInfo *__restrict__ pinfo) {
+    const int logN = d.logN;
+    const size_t N = size_t(1) << logN;
+    const uint32_t n0 = (blockIdx.x * blockDim.x + threadIdx.x) * 2;
+    if (n0 >= N) return;
+    int t;
+    const int c = batch_find(d, blockIdx.y, t);
+    const CtDesc &ct = d.ct[c];
+    const CtLayout lo = ct_layout(d, ct);
+    const int ell = ct.ell, LK = d.L + d.k, alpha = d.alpha, beta = lo.beta;
+    const int prime = t < ell ? t : d.L + (t - ell);
+    const uint32_t g = ct.galois;
+    const u64 *key = ct.key;
+    u64 ul0 = 0, uh0 = 0, ul1 = 0, uh1 = 0, vl0 = 0, vh0 = 0, vl1 = 0, vh1 = 0;
+    if constexpr (BMAX > 0) {
+        ulonglong2 dv[BMAX], ka[BMAX], kb[BMAX];
+#pragma unroll
+        for (int j = 0; j < BMAX; j++) {
+            if (j < beta) {
+                const bool own = t < ell && (t / alpha) == j;
+                const u64 *src = own ? ct.a + size_t(t) * N : lo.extp + (size_t(j) * lo.ext + t) * N;
+                dv[j] = ld2_perm(src, n0, g, logN);
+                ka[j] = ld2_stream(key + ((size_t(j) * 2 + 0) * LK + prime) * N + n0);
+                kb[j] = ld2_stream(key + ((size_t(j) * 2 + 1) * LK + prime) * N + n0);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < BMAX; j++) {
+            if (j < beta) {
+                mac128(ul0, uh0, dv[j].x, ka[j].x);
+                mac128(ul1, uh1, dv[j].y, ka[j].y);
+                mac128(vl0, vh0, dv[j].x, kb[j].x);
+                mac128(vl1, vh1, dv[j].y, kb[j].y);
+            }
+        }
+    } else {
+        for (int j = 0; j < beta; j++) {
+            const bool own = t < ell && (t / alpha) == j;
+            const u64 *src = own ? ct.a + size_t(t) * N : lo.extp + (size_t(j) * lo.ext + t) * N;
+            const ulonglong2 dv = ld2_perm(src, n0, g, logN);
+            const ulonglong2 ka = ld2_stream(key + ((size_t(j) * 2 + 0) * LK + prime) * N + n0);
+            const ulonglong2 kb = ld2_stream(key + ((size_t(j) * 2 + 1) * LK + prime) * N + n0);
+            mac128(ul0, uh0, dv.x, ka.x);
+            mac128(ul1, uh1, dv.y, ka.y);
+            mac128(vl0, vh0, dv.x, kb.x);
+            mac128(vl1, vh1, dv.y, kb.y);
+        }
+    }
+    const PrimeInfo P = pinfo[prime];
+    st2(lo.uv + size_t(t) * N + n0, make_ulonglong2(reduce128(ul0, uh0, P), reduce128(ul1, uh1, P)));
+    st2(lo.uv + (size_t(lo.ext) + t) * N + n0, make_ulonglong2(reduce128(vl0, vh0, P), reduce128(vl1, vh1, P)));
+}
+
+cudaError_t launch_inner_prod_batch(const ckks_ctx *ctx, const KsBatchDesc &d, cudaStream_t st) {
+    KsBatchDesc m = d;
+    int count = 0;
+    for (int c = 0; c < d.n; ++c) {
+        m.pre[c] = count;
+        count += d.ct[c].ell + d.k;
+    }
+    m.pre[d.n] = count;
+    if (count == 0) return cudaSuccess;
+    const int threads = 256;
+    dim3 grid(unsigned((ctx->N / 2 + threads - 1) / threads), unsigned(count));
+    ProfScope ps(ctx, K_INNER, count, st);
+    switch (ctx->dnum) {
+    case 1: inner_prod_batch_kernel<1><<<grid, threads, 0, st>>>(m, ctx->d_pinfo); break;
+    case 2: inner_prod_batch_kernel<2><<<grid, threads, 0, st>>>(m, ctx->d_pinfo); break;
+    case 3: inner_prod_batch_kernel<3><<<grid, threads, 0, st>>>(m, ctx->d_pinfo); break;
+    case 4: inner_prod_batch_kernel<4><<<grid, threads, 0, st>>>(m, ctx->d_pinfo); break;
+    default: inner_prod_batch_kernel<0><<<grid, threads, 0, st>>>(m, ctx->d_pinfo);
     }
     return cudaGetLastError();
 }

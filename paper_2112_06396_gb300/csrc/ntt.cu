@@ -17,6 +17,7 @@
 // contiguous-pass output is re-staged through shared memory).  Values stay in
 // [0, 4p) between stages (Harvey's lazy butterflies) and are fully reduced
 // only when the transform ends.
+#include "batch.cuh"
 #include "common.cuh"
 #include "internal.h"
 
@@ -60,9 +61,10 @@ __device__ __forceinline__ void gs_bfly(u64 &X, u64 &Y, ulonglong2 w, u64 p, u64
     }
 }
 
-template <int LOGN, int LOGR, int A, int C, bool INV, bool CONTIG, bool EPI, bool SMALLP>
+template <int LOGN, int LOGR, int A, int C, bool INV, bool CONTIG, bool EPI, bool SMALLP, class MAP>
 __global__ void __launch_bounds__((1 << (LOGR - A)) * C, (A <= 4 ? 1024 : 512) / ((1 << (LOGR - A)) * C))
-ntt_pass_kernel(NttBatch batch, const PrimeInfo *__restrict__ pinfo, const ulonglong2 *__restrict__ tw_all, Epi epi) {
+ntt_pass_kernel(const __grid_constant__ MAP map, const PrimeInfo *__restrict__ pinfo,
+                const ulonglong2 *__restrict__ tw_all) {
     constexpr int B = LOGR - A;
     constexpr int TPC = 1 << B;   // threads per column
     constexpr int E = 1 << A;     // words per thread
@@ -77,10 +79,11 @@ ntt_pass_kernel(NttBatch batch, const PrimeInfo *__restrict__ pinfo, const ulong
     constexpr int L1 = LOGN - L2;
     constexpr uint32_t N = 1u << LOGN;
     constexpr int logN = LOGN;
-    const int limb = blockIdx.x;  // limbs sharing a prime are adjacent: co-resident CTAs reuse twiddles
-    const int prime = batch.prime[limb];
-    const u64 *__restrict__ src = batch.src[limb];
-    u64 *dst = batch.dst[limb];
+    // limbs sharing a prime are adjacent: co-resident CTAs reuse twiddles
+    const LimbIO io = map.get(blockIdx.x, N);
+    const int prime = io.prime;
+    const u64 *__restrict__ src = io.src;
+    u64 *dst = io.dst;
     const ulonglong2 *__restrict__ tw = tw_all + size_t(prime) * N;
     const u64 p = pinfo[prime].p;
     const u64 np = u64(0) - p;
@@ -117,17 +120,14 @@ ntt_pass_kernel(NttBatch batch, const PrimeInfo *__restrict__ pinfo, const ulong
             const ulonglong2 *t0 = tw + (size_t(1) << (s0 + sg)) + (col0 << sg);
             l2_prefetch(t0, uint32_t(C * sizeof(ulonglong2)) << sg);
         }
-        if (EPI && epi.mode == EPI_SCALE) {
-            const int poly = limb % epi.npolys;
-            const size_t base = size_t(limb / epi.npolys) * N + (col0 << L2);
-            l2_prefetch(epi.x[poly] + base, uint32_t(C * sizeof(u64)) << L2);
-            if (epi.accumulate) l2_prefetch(epi.out[poly] + base, uint32_t(C * sizeof(u64)) << L2);
-            if (epi.add[poly] != nullptr) {
+        if (EPI) {
+            l2_prefetch(io.ex + (col0 << L2), uint32_t(C * sizeof(u64)) << L2);
+            if (io.accumulate) l2_prefetch(io.eout + (col0 << L2), uint32_t(C * sizeof(u64)) << L2);
+            if (io.eadd != nullptr) {
                 for (int b = 0; b < C; b++) {
                     const uint32_t first = uint32_t((col0 + b) << L2);
-                    const uint32_t sblk = (epi.galois == 1 ? first : automorph_src(first, epi.galois, logN)) >> L2;
-                    l2_prefetch(epi.add[poly] + size_t(limb / epi.npolys) * N + (size_t(sblk) << L2),
-                                uint32_t(sizeof(u64)) << L2);
+                    const uint32_t sblk = (io.galois == 1 ? first : automorph_src(first, io.galois, logN)) >> L2;
+                    l2_prefetch(io.eadd + (size_t(sblk) << L2), uint32_t(sizeof(u64)) << L2);
                 }
             }
         }
@@ -175,29 +175,22 @@ ntt_pass_kernel(NttBatch batch, const PrimeInfo *__restrict__ pinfo, const ulong
 #pragma unroll
             for (int k = 0; k < E; k++) x[k] = sm[sidx(g + (k << B))];
             const u64 one_s = pinfo[prime].one_s;
-            ulonglong2 c = make_ulonglong2(0, 0);
-            int poly = 0;
-            size_t base = 0;
-            if (EPI) {
-                poly = limb % epi.npolys;
-                base = size_t(limb / epi.npolys) * N;
-                c = epi.cmul[prime];
-            }
 #pragma unroll
             for (int k = 0; k < E; k++) {
                 u64 v = SMALLP ? shoup_approx(x[k], 1, one_s, np) : x[k];
                 x[k] = csub(csub(v, 2 * p), p);
             }
-            if (!EPI || epi.mode == EPI_STORE) {
+            if (!EPI) {
 #pragma unroll
                 for (int k = 0; k < E; k++) dst[gidx(g + (k << B))] = x[k];
             } else {
                 // Epilogue operands are read-only for this launch: load a group of
                 // them through the non-coherent path before any store, so the
                 // loads overlap instead of waiting behind each store.
-                const u64 *__restrict__ xp = epi.x[poly] + base;
-                const u64 *__restrict__ ap = epi.add[poly] == nullptr ? nullptr : epi.add[poly] + base;
-                u64 *op = epi.out[poly] + base;
+                const ulonglong2 c = map.cmul()[prime];
+                const u64 *__restrict__ xp = io.ex;
+                const u64 *__restrict__ ap = io.eadd;
+                u64 *op = io.eout;
                 constexpr int GRP = E < 4 ? E : 4;
 #pragma unroll
                 for (int k0 = 0; k0 < E; k0 += GRP) {
@@ -209,8 +202,8 @@ ntt_pass_kernel(NttBatch batch, const PrimeInfo *__restrict__ pinfo, const ulong
                         av[k] = 0;
                         ov[k] = 0;
                         if (ap != nullptr)
-                            av[k] = __ldg(ap + (epi.galois == 1 ? i : automorph_src(i, epi.galois, logN)));
-                        if (epi.accumulate) ov[k] = op[i];
+                            av[k] = __ldg(ap + (io.galois == 1 ? i : automorph_src(i, io.galois, logN)));
+                        if (io.accumulate) ov[k] = op[i];
                     }
 #pragma unroll
                     for (int k = 0; k < GRP; k++) {
@@ -293,8 +286,8 @@ ntt_pass_kernel(NttBatch batch, const PrimeInfo *__restrict__ pinfo, const ulong
 // ------------------------------------------------------------------ host side
 namespace {
 
-template <int LOGN, bool INV, bool CONTIG, bool EPI, bool SMALLP>
-cudaError_t launch_one_p(const NttBatch &b, const ckks_ctx *ctx, const Epi &epi, cudaStream_t st, bool set_attr) {
+template <int LOGN, bool INV, bool CONTIG, bool EPI, bool SMALLP, class MAP>
+cudaError_t launch_one_p(const MAP &m, int count, const ckks_ctx *ctx, cudaStream_t st, bool set_attr) {
     // pass S transforms columns of 2^L1 rows, pass C blocks of 2^L2 words
     constexpr int L2 = LOGN >> 1, L1 = LOGN - L2;
     constexpr int LOGR = CONTIG ? L2 : L1;
@@ -310,85 +303,127 @@ cudaError_t launch_one_p(const NttBatch &b, const ckks_ctx *ctx, const Epi &epi,
     constexpr int WANT = (CONTIG ? 64 : 128) / TPC > 0 ? (CONTIG ? 64 : 128) / TPC : 1;
     constexpr int C = WANT < (1 << OTHER) ? WANT : (1 << OTHER);
     const size_t smem = CONTIG ? size_t(C) * (R + TPC) * 8 : size_t(R) * C * 8 + size_t(R) * 16;
-    auto kern = ntt_pass_kernel<LOGN, LOGR, A, C, INV, CONTIG, EPI, SMALLP>;
+    auto kern = ntt_pass_kernel<LOGN, LOGR, A, C, INV, CONTIG, EPI, SMALLP, MAP>;
     if (set_attr) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    dim3 grid(b.count, (1 << OTHER) / C);
-    kern<<<grid, TPC * C, smem, st>>>(b, ctx->d_pinfo, INV ? ctx->d_tw_inv : ctx->d_tw_fwd, epi);
+    dim3 grid(count, (1 << OTHER) / C);
+    kern<<<grid, TPC * C, smem, st>>>(m, ctx->d_pinfo, INV ? ctx->d_tw_inv : ctx->d_tw_fwd);
     return cudaGetLastError();
 }
 
-template <int LOGN, bool INV, bool CONTIG, bool EPI>
-cudaError_t launch_one(const NttBatch &b, const ckks_ctx *ctx, const Epi &epi, cudaStream_t st, bool set_attr) {
+template <int LOGN, bool INV, bool CONTIG, bool EPI, class MAP>
+cudaError_t launch_one(const MAP &m, int count, const ckks_ctx *ctx, cudaStream_t st, bool set_attr) {
     if (set_attr) {
-        cudaError_t e = launch_one_p<LOGN, INV, CONTIG, EPI, true>(b, ctx, epi, st, true);
+        cudaError_t e = launch_one_p<LOGN, INV, CONTIG, EPI, true>(m, count, ctx, st, true);
         if (e != cudaSuccess) return e;
-        return launch_one_p<LOGN, INV, CONTIG, EPI, false>(b, ctx, epi, st, true);
+        return launch_one_p<LOGN, INV, CONTIG, EPI, false>(m, count, ctx, st, true);
     }
-    if (ctx->small_primes) return launch_one_p<LOGN, INV, CONTIG, EPI, true>(b, ctx, epi, st, false);
-    return launch_one_p<LOGN, INV, CONTIG, EPI, false>(b, ctx, epi, st, false);
+    if (ctx->small_primes) return launch_one_p<LOGN, INV, CONTIG, EPI, true>(m, count, ctx, st, false);
+    return launch_one_p<LOGN, INV, CONTIG, EPI, false>(m, count, ctx, st, false);
 }
 
-template <bool INV, bool CONTIG, bool EPI>
-cudaError_t dispatch(const NttBatch &b, const ckks_ctx *ctx, const Epi &epi, cudaStream_t st, bool set_attr) {
+template <bool INV, bool CONTIG, bool EPI, class MAP>
+cudaError_t dispatch(const MAP &m, int count, const ckks_ctx *ctx, cudaStream_t st, bool set_attr) {
     switch (ctx->logN) {
-    case 10: return launch_one<10, INV, CONTIG, EPI>(b, ctx, epi, st, set_attr);
-    case 11: return launch_one<11, INV, CONTIG, EPI>(b, ctx, epi, st, set_attr);
-    case 12: return launch_one<12, INV, CONTIG, EPI>(b, ctx, epi, st, set_attr);
-    case 13: return launch_one<13, INV, CONTIG, EPI>(b, ctx, epi, st, set_attr);
-    case 14: return launch_one<14, INV, CONTIG, EPI>(b, ctx, epi, st, set_attr);
-    case 15: return launch_one<15, INV, CONTIG, EPI>(b, ctx, epi, st, set_attr);
-    case 16: return launch_one<16, INV, CONTIG, EPI>(b, ctx, epi, st, set_attr);
-    case 17: return launch_one<17, INV, CONTIG, EPI>(b, ctx, epi, st, set_attr);
+    case 10: return launch_one<10, INV, CONTIG, EPI>(m, count, ctx, st, set_attr);
+    case 11: return launch_one<11, INV, CONTIG, EPI>(m, count, ctx, st, set_attr);
+    case 12: return launch_one<12, INV, CONTIG, EPI>(m, count, ctx, st, set_attr);
+    case 13: return launch_one<13, INV, CONTIG, EPI>(m, count, ctx, st, set_attr);
+    case 14: return launch_one<14, INV, CONTIG, EPI>(m, count, ctx, st, set_attr);
+    case 15: return launch_one<15, INV, CONTIG, EPI>(m, count, ctx, st, set_attr);
+    case 16: return launch_one<16, INV, CONTIG, EPI>(m, count, ctx, st, set_attr);
+    case 17: return launch_one<17, INV, CONTIG, EPI>(m, count, ctx, st, set_attr);
     default: return cudaErrorInvalidValue;
     }
+}
+
+template <class MAP>
+cudaError_t set_attributes_for(const ckks_ctx *ctx) {
+    MAP m{};
+    cudaError_t err;
+    if ((err = dispatch<false, false, false>(m, 0, ctx, nullptr, true)) != cudaSuccess) return err;
+    if ((err = dispatch<false, true, false>(m, 0, ctx, nullptr, true)) != cudaSuccess) return err;
+    if ((err = dispatch<false, true, true>(m, 0, ctx, nullptr, true)) != cudaSuccess) return err;
+    if ((err = dispatch<true, true, false>(m, 0, ctx, nullptr, true)) != cudaSuccess) return err;
+    return dispatch<true, false, false>(m, 0, ctx, nullptr, true);
+}
+
+// Two passes of one transform: the second runs in place on the first's output.
+template <class MAP>
+cudaError_t run_fwd(MAP m, int count, bool epi, const ckks_ctx *ctx, cudaStream_t st) {
+    cudaError_t err;
+    m.second = 0;
+    {
+        ProfScope ps(ctx, K_NTT_FWD, count, st);
+        err = dispatch<false, false, false>(m, count, ctx, st, false);
+    }
+    if (err != cudaSuccess) return err;
+    m.second = 1;
+    ProfScope ps(ctx, K_NTT_FWD, count, st);
+    if (epi) return dispatch<false, true, true>(m, count, ctx, st, false);
+    return dispatch<false, true, false>(m, count, ctx, st, false);
+}
+
+template <class MAP>
+cudaError_t run_inv(MAP m, int count, const ckks_ctx *ctx, cudaStream_t st) {
+    cudaError_t err;
+    m.second = 0;
+    {
+        ProfScope ps(ctx, K_NTT_INV, count, st);
+        err = dispatch<true, true, false>(m, count, ctx, st, false);
+    }
+    if (err != cudaSuccess) return err;
+    m.second = 1;
+    ProfScope ps(ctx, K_NTT_INV, count, st);
+    return dispatch<true, false, false>(m, count, ctx, st, false);
 }
 
 }  // namespace
 
 cudaError_t ntt_set_attributes(const ckks_ctx *ctx) {
-    NttBatch b{};
-    Epi e{};
-    cudaError_t err;
-    if ((err = dispatch<false, false, false>(b, ctx, e, nullptr, true)) != cudaSuccess) return err;
-    if ((err = dispatch<false, true, false>(b, ctx, e, nullptr, true)) != cudaSuccess) return err;
-    if ((err = dispatch<false, true, true>(b, ctx, e, nullptr, true)) != cudaSuccess) return err;
-    if ((err = dispatch<true, true, false>(b, ctx, e, nullptr, true)) != cudaSuccess) return err;
-    if ((err = dispatch<true, false, false>(b, ctx, e, nullptr, true)) != cudaSuccess) return err;
-    return cudaSuccess;
+    cudaError_t err = set_attributes_for<MapList>(ctx);
+    if (err != cudaSuccess) return err;
+    return set_attributes_for<MapBatch>(ctx);
 }
 
-// Forward transform of a batch (src -> dst, then in place); the optional
-// epilogue replaces the store of the last pass.
+// Forward transform of a limb list (src -> dst, then in place); the optional
+// ModDown/Rescale epilogue replaces the store of the last pass.
 cudaError_t launch_ntt_fwd(const ckks_ctx *ctx, const NttBatch &b, const Epi *epi, cudaStream_t st) {
     if (b.count == 0) return cudaSuccess;
-    Epi none{};
-    none.mode = EPI_STORE;
-    cudaError_t err;
-    {
-        ProfScope ps(ctx, K_NTT_FWD, b.count, st);
-        err = dispatch<false, false, false>(b, ctx, none, st, false);
+    MapList m;
+    m.b = b;
+    const bool scale = epi != nullptr && epi->mode == EPI_SCALE;
+    if (scale) m.e = *epi;
+    else {
+        m.e = Epi{};
+        m.e.mode = EPI_STORE;
     }
-    if (err != cudaSuccess) return err;
-    NttBatch b2 = b;
-    for (int l = 0; l < b.count; l++) b2.src[l] = b.dst[l];
-    ProfScope ps(ctx, K_NTT_FWD, b.count, st);
-    if (epi != nullptr && epi->mode != EPI_STORE) return dispatch<false, true, true>(b2, ctx, *epi, st, false);
-    return dispatch<false, true, false>(b2, ctx, none, st, false);
+    return run_fwd(m, b.count, scale, ctx, st);
 }
 
 cudaError_t launch_ntt_inv(const ckks_ctx *ctx, const NttBatch &b, cudaStream_t st) {
     if (b.count == 0) return cudaSuccess;
-    Epi none{};
-    cudaError_t err;
-    {
-        ProfScope ps(ctx, K_NTT_INV, b.count, st);
-        err = dispatch<true, true, false>(b, ctx, none, st, false);
+    MapList m;
+    m.b = b;
+    m.e = Epi{};
+    m.e.mode = EPI_STORE;
+    return run_inv(m, b.count, ctx, st);
+}
+
+// One phase of batched key switching over every ciphertext of the batch.
+cudaError_t launch_ntt_batch(const ckks_ctx *ctx, const KsBatchDesc &d, int phase, cudaStream_t st) {
+    MapBatch m;
+    m.d = d;
+    m.phase = phase;
+    m.cm = ctx->d_Pinv;
+    int count = 0;
+    for (int c = 0; c < d.n; ++c) {
+        m.d.pre[c] = count;
+        count += phase_count(d, d.ct[c].ell, phase);
     }
-    if (err != cudaSuccess) return err;
-    NttBatch b2 = b;
-    for (int l = 0; l < b.count; l++) b2.src[l] = b.dst[l];
-    ProfScope ps(ctx, K_NTT_INV, b.count, st);
-    return dispatch<true, false, false>(b2, ctx, none, st, false);
+    m.d.pre[d.n] = count;
+    if (count == 0) return cudaSuccess;
+    if (phase == PH_INTT_A || phase == PH_INTT_P) return run_inv(m, count, ctx, st);
+    return run_fwd(m, count, phase == PH_NTT_DOWN, ctx, st);
 }
 
 }  // namespace ckks

@@ -119,3 +119,13 @@ def small_uniform(N: int, name: str, bound: int, master: int = MASTER_SEED) -> n
     shift = np.uint64(64 - bits)
     v = _accept(seed, N, lambda d: d >> shift, lambda x: x < np.uint64(span))
     return v.astype(np.int64) - bound
+
+
+def uniform_ints(n: int, lo: int, hi: int, name: str, master: int = MASTER_SEED) -> list[int]:
+    """n integers uniform in [lo, hi] (e.g. the levels of a batch), by rejection."""
+    seed = stream_seed(name, 0, master)
+    span = hi - lo + 1
+    bits = max(1, (span - 1).bit_length())
+    shift = np.uint64(64 - bits)
+    v = _accept(seed, n, lambda d: d >> shift, lambda x: x < np.uint64(span))
+    return [int(x) + lo for x in v]

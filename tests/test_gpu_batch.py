@@ -1,0 +1,146 @@
+"""Batched key switching through the C ABI: many ciphertexts at uneven levels,
+each with its own key and Galois element, one launch per pipeline step.
+
+Every entry of a batch must carry the bits of the single-ciphertext call
+(KeySwitch, or HRotate with one rotation, Algorithm 4) and of the oracle.
+Exact modular arithmetic: tolerance 0.
+"""
+import numpy as np
+import pytest
+
+import synth
+from tests.test_gpu_parity import Setup, _gpu, dev, host
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _entries(S, levels, rot_every, tag):
+    """Inputs of a mixed batch: entry i is an HRotate when i % rot_every == 1
+    (Galois elements 5, 5^7, 2N-1 in turn), else a KeySwitch.  Keys are
+    shared between entries of the same Galois element."""
+    P = S.P
+    twoN = 2 * P.N
+    gs_cycle = [5, pow(5, 7, twoN), twoN - 1]
+    keys = {}
+    a, b, g, kh = [], [], [], []
+    for i, ell in enumerate(levels):
+        ai, bi = S.ct(ell, f"{tag}/ct{i}")
+        rot = rot_every > 0 and i % rot_every == 1
+        gi = gs_cycle[(i // max(rot_every, 1)) % 3] if rot else 0
+        if gi not in keys:
+            keys[gi] = S.key(gi, f"{tag}/key{gi}")[0]
+        a.append(ai)
+        b.append(bi if rot else None)
+        g.append(gi if rot else 1)
+        kh.append(gi)
+    return a, b, g, kh, keys
+
+
+def _run_and_check(S, levels, rot_every, tag, oracle_every=1):
+    P, ctx = S.P, S.ctx
+    a, b, g, kh, keys = _entries(S, levels, rot_every, tag)
+    dkeys = {gi: dev(k) for gi, k in keys.items()}
+    da = [dev(x) for x in a]
+    db = [None if x is None else dev(x) for x in b]
+    outs = ctx.keyswitch_batch(da, db, levels, g, [dkeys[gi] for gi in kh])
+    for i, ell in enumerate(levels):
+        if db[i] is None:
+            su, sv = ctx.keyswitch(da[i], ell, dkeys[kh[i]])
+        else:
+            ((su, sv),) = ctx.hrotate(da[i], db[i], ell, [g[i]], [dkeys[kh[i]]])
+        np.testing.assert_array_equal(host(outs[i][0]), host(su), err_msg=f"entry {i} ell={ell}")
+        np.testing.assert_array_equal(host(outs[i][1]), host(sv), err_msg=f"entry {i} ell={ell}")
+        if i % oracle_every == 0:
+            if b[i] is None:
+                ru, rv = S.o.keyswitch(P, ell, a[i], keys[kh[i]])
+            else:
+                ((ru, rv),) = S.o.hrotate(P, ell, a[i], b[i], [g[i]], [keys[kh[i]]])
+            np.testing.assert_array_equal(host(outs[i][0]), ru, err_msg=f"oracle entry {i}")
+            np.testing.assert_array_equal(host(outs[i][1]), rv, err_msg=f"oracle entry {i}")
+    return outs
+
+
+@pytest.fixture(scope="module")
+def cfg1(oracle_lib):
+    return Setup(oracle_lib, 12, 6, 3, 2, 50)
+
+
+@pytest.fixture(scope="module")
+def cfg_odd(oracle_lib):
+    return Setup(oracle_lib, 11, 7, 3, 3, 50)
+
+
+def test_batch_mixed_levels_keyswitch_and_hrotate(cfg1):
+    """Every level 1..L, KeySwitch and HRotate entries interleaved."""
+    _run_and_check(cfg1, [6, 1, 3, 5, 2, 6, 4, 1, 3, 6], 2, "gpu/batch/c1")
+
+
+def test_batch_partial_digits(cfg_odd):
+    """alpha = 3, L = 7: last digits of 1 or 2 limbs at most levels."""
+    _run_and_check(cfg_odd, [7, 5, 1, 4, 2, 6, 3, 7], 3, "gpu/batch/odd")
+
+
+def test_batch_more_than_64_entries(oracle_lib):
+    """70 entries: two internal batches, the second of 6."""
+    S = Setup(oracle_lib, 10, 4, 2, 2, 50)
+    levels = synth.uniform_ints(70, 1, 4, "gpu/batch/70/levels")
+    _run_and_check(S, levels, 4, "gpu/batch/70", oracle_every=9)
+
+
+def test_batch_wide_primes_run_one_by_one(oracle_lib):
+    """58-bit primes: no split conversion, entries run one after another."""
+    S = Setup(oracle_lib, 11, 4, 2, 2, 58)
+    _run_and_check(S, [4, 2, 3, 1], 2, "gpu/batch/wide")
+
+
+def test_batch_edge_arguments(cfg1):
+    ckks = _gpu()
+    ctx, P = cfg1.ctx, cfg1.P
+    assert ctx.keyswitch_batch([], None, [], None, []) == []
+    a, _ = cfg1.ct(2, "gpu/batch/edge")
+    key = dev(cfg1.key(0, "gpu/batch/edge/key")[0])
+    da = dev(a)
+    with pytest.raises(ckks.CkksError):
+        ctx.keyswitch_batch([da], None, [P.L + 1], None, [key])      # level above L
+    with pytest.raises(ckks.CkksError):
+        ctx.keyswitch_batch([da], None, [0], None, [key])            # level 0
+    with pytest.raises(ckks.CkksError):
+        ctx.keyswitch_batch([da], [da], [2], [4], [key])             # even Galois element
+    # the Galois element of a KeySwitch entry is ignored
+    (u, v), = ctx.keyswitch_batch([da], [None], [2], [4], [key])
+    su, sv = ctx.keyswitch(da, 2, key)
+    np.testing.assert_array_equal(host(u), host(su))
+    np.testing.assert_array_equal(host(v), host(sv))
+
+
+@pytest.fixture(scope="module")
+def cfgB(oracle_lib):
+    return Setup(oracle_lib, 16, 24, 8, 3, 54)
+
+
+def test_batch_64_uneven_levels_headline_shape(cfgB):
+    """64 KeySwitches at levels uniform in {4..24}, N=2^16, k=8, dnum=3, one
+    shared key: every entry against the single call, the lowest- and
+    highest-level entries against the oracle."""
+    S = cfgB
+    P, ctx = S.P, S.ctx
+    levels = synth.uniform_ints(64, 4, 24, "batch/levels")
+    key = S.key(0, "gpu/B/relin")[0]
+    dkey = dev(key)
+    a = [S.ct(ell, f"gpu/B/batch/ct{i}")[0] for i, ell in enumerate(levels)]
+    da = [dev(x) for x in a]
+    outs = ctx.keyswitch_batch(da, None, levels, None, [dkey] * 64)
+    ws = S.ctx.workspace(3, P.L)
+    for i, ell in enumerate(levels):
+        su, sv = ctx.keyswitch(da[i], ell, dkey, ws=ws)
+        np.testing.assert_array_equal(host(outs[i][0]), host(su), err_msg=f"entry {i} ell={ell}")
+        np.testing.assert_array_equal(host(outs[i][1]), host(sv), err_msg=f"entry {i} ell={ell}")
+    for i in (levels.index(min(levels)), levels.index(max(levels))):
+        ru, rv = S.o.keyswitch(P, levels[i], a[i], key)
+        np.testing.assert_array_equal(host(outs[i][0]), ru)
+        np.testing.assert_array_equal(host(outs[i][1]), rv)
+    # a second run over the same workspace gives the same bits
+    outs2 = ctx.keyswitch_batch(da, None, levels, None, [dkey] * 64)
+    for (u1, v1), (u2, v2) in zip(outs, outs2):
+        assert torch.equal(u1, u2) and torch.equal(v1, v2)
