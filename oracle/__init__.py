@@ -82,6 +82,7 @@ def _load():
                 "or_pmodup": (ctypes.c_int, [P, ctypes.c_int, u64p, u64p]),
                 "or_keyswitch": (ctypes.c_int, [P, ctypes.c_int, u64p, u64p, u64p, u64p]),
                 "or_rotate": (ctypes.c_int, [P, ctypes.c_int, u64p, u64p, ctypes.c_uint64, u64p, u64p, u64p]),
+                "or_mult": (ctypes.c_int, [P, ctypes.c_int, u64p, u64p, u64p, u64p, u64p, u64p, u64p]),
                 "or_hrotate": (ctypes.c_int, [P, ctypes.c_int, u64p, u64p, ctypes.c_int, u64p,
                                               ctypes.POINTER(u64p), ctypes.POINTER(u64p), ctypes.POINTER(u64p)]),
                 "or_ptmatvec": (ctypes.c_int, [P, ctypes.c_int, u64p, u64p, ctypes.c_int, ctypes.c_int,
@@ -261,6 +262,16 @@ def keyswitch(P: Params, ell, a, key):
     v = np.zeros_like(u)
     _load().or_keyswitch(P.c, ell, _u(a), _u(key), _u(u), _u(v))
     return u, v
+
+
+def mult(P: Params, ell, a1, b1, a2, b2, key):
+    """Algorithm 2 (Mult + relinearisation + Rescale): outputs at level ell-1."""
+    c = [np.ascontiguousarray(x, dtype=np.uint64) for x in (a1, b1, a2, b2, key)]
+    oa = np.zeros((ell - 1, P.N), dtype=np.uint64)
+    ob = np.zeros_like(oa)
+    if _load().or_mult(P.c, ell, *[_u(x) for x in c], _u(oa), _u(ob)) != 0:
+        raise ValueError("mult needs ell >= 2")
+    return oa, ob
 
 
 def rotate(P: Params, ell, a, b, g, key):

@@ -444,6 +444,41 @@ int or_keyswitch(const or_params *P, int ell, const u64 *a, const u64 *key, u64 
     return 0;
 }
 
+/* Algorithm 2: Mult with relinearisation and Rescale.  Slot-wise (evaluation
+ * form) products (a3, b3, c3) = (a1*a2, a1*b2 + a2*b1, b1*b2); KeySwitch of a3
+ * with the key for s^2 gives (u, v); (a', b') = (b3 + u, c3 + v); the result
+ * is (Rescale(a'), Rescale(b')) at level ell-1.  Needs ell >= 2. */
+int or_mult(const or_params *P, int ell, const u64 *a1, const u64 *b1, const u64 *a2, const u64 *b2,
+            const u64 *key, u64 *oa, u64 *ob) {
+    if (ell < 2) return -1;
+    size_t N = N_of(P), sz = (size_t)ell * N;
+    u64 *a3 = (u64 *)malloc(sizeof(u64) * sz), *b3 = (u64 *)malloc(sizeof(u64) * sz);
+    u64 *c3 = (u64 *)malloc(sizeof(u64) * sz);
+    for (int i = 0; i < ell; i++) {
+        u64 q = P->primes[i];
+        for (size_t n = 0; n < N; n++) {
+            size_t o = (size_t)i * N + n;
+            a3[o] = mulmod(a1[o], a2[o], q);
+            b3[o] = addmod(mulmod(a1[o], b2[o], q), mulmod(a2[o], b1[o], q), q);
+            c3[o] = mulmod(b1[o], b2[o], q);
+        }
+    }
+    u64 *u = (u64 *)malloc(sizeof(u64) * sz), *v = (u64 *)malloc(sizeof(u64) * sz);
+    or_keyswitch(P, ell, a3, key, u, v);
+    for (int i = 0; i < ell; i++) {
+        u64 q = P->primes[i];
+        for (size_t n = 0; n < N; n++) {
+            size_t o = (size_t)i * N + n;
+            u[o] = addmod(b3[o], u[o], q);
+            v[o] = addmod(c3[o], v[o], q);
+        }
+    }
+    or_rescale(P, ell, u, oa);
+    or_rescale(P, ell, v, ob);
+    free(a3); free(b3); free(c3); free(u); free(v);
+    return 0;
+}
+
 /* Algorithm 3: automorph (a, b) first, key-switch a_rot, return (u, v + b_rot). */
 int or_rotate(const or_params *P, int ell, const u64 *a, const u64 *b, u64 g, const u64 *key, u64 *oa, u64 *ob) {
     size_t N = N_of(P);

@@ -161,3 +161,38 @@ def test_ptmatvec_decrypts(oracle_lib, nb, ng, ell, rescale):
     else:
         got = decrypt_int(oracle_lib, P, ell, s, oa, ob)
         assert max(abs(x - y) for x, y in zip(got, expect)) <= bound
+
+
+@pytest.mark.parametrize("logN,L,k,dnum,ell", [(6, 6, 3, 2, 6), (6, 7, 3, 3, 4), (6, 6, 3, 2, 2), (12, 6, 3, 2, 6)])
+def test_mult_decrypts_to_rescaled_product(oracle_lib, logN, L, k, dnum, ell):
+    """Algorithm 2: Dec(Mult(ct1, ct2)) = (m1 * m2 + e_ks) / q_{ell-1} up to the
+    Rescale rounding, where m_i = Delta * x_i + e_i are the encrypted
+    polynomials and * is the negacyclic product.  With a the rescaled
+    ciphertext's rounding residues r_a, r_b (|r| <= q/2):
+      |Dec(out) - m1*m2 / q_{ell-1}| <= ks_bound / q_{ell-1} + (h_s + 1) / 2."""
+    P = params(oracle_lib, logN, L, k, dnum)
+    s = synth.ternary(P.N, "pin/mult/s")
+    rlk = make_key(oracle_lib, P, s, oracle_lib.sq_secret(P, s), "pin/mult/rlk")
+    ql = int(P.primes[ell - 1])
+    delta = 1 << (ql.bit_length() // 2 + 4)
+    cts, ms = [], []
+    for i in range(2):
+        x = synth.small_uniform(P.N, f"pin/mult/x{i}", 8)
+        m = delta * x + synth.gaussian(P.N, f"pin/mult/e{i}")
+        a = synth.uniform_residues(P.primes[:ell], P.N, f"pin/mult/a{i}")
+        cts.append((a, oracle_lib.encrypt(P, ell, s, m, a)))
+        ms.append([int(v) for v in m])
+    (a1, b1), (a2, b2) = cts
+    oa, ob = oracle_lib.mult(P, ell, a1, b1, a2, b2, rlk)
+    assert oa.shape == (ell - 1, P.N)
+    got = decrypt_int(oracle_lib, P, ell - 1, s, oa, ob)
+    prod_m = negacyclic_mul(ms[0], ms[1])
+    hs = int(np.count_nonzero(s))
+    bound = ks_bound(P, ell, s) / ql + (hs + 1) / 2
+    err = max(abs(g * ql - t) for g, t in zip(got, prod_m)) / ql
+    assert err <= bound
+    assert max(abs(t) for t in prod_m) / ql > 100 * bound  # the check is not vacuous
+    # both operand orders give the same bits (the tensor step is symmetric)
+    oa2, ob2 = oracle_lib.mult(P, ell, a2, b2, a1, b1, rlk)
+    np.testing.assert_array_equal(oa, oa2)
+    np.testing.assert_array_equal(ob, ob2)
