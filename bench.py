@@ -145,61 +145,158 @@ def step(ctx, items, lanes):
     lanes.join()
 
 
-def measure_other_rows(ctx, ckks, torch, reps=5):
-    """Rescale (Alg. 1's ModDown_{B,1}) of one ciphertext and one CoeffToSlot-shaped
-    PtMatVecMult level (Alg. 8 with 8 baby x 4 giant steps of stride 1, 32 seeded
-    diagonals over the extended basis, 7 baby + 3 giant rotation keys) at N=2^16,
-    ell=24, timed with CUDA events outside the KeySwitch timed region."""
-    N = 1 << LOGN
+def _timed(torch, fn, reps=5, warm=2):
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _keygen(ctx, torch, s, g, tag):
+    N = ctx.N
     dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(ctx.device)
     primes = ctx.q + ctx.p
+    a_key = np.stack([synth.uniform_residues(primes, N, f"{tag}/a{j}") for j in range(ctx.dnum)])
+    e_key = np.stack([synth.gaussian(N, f"{tag}/e{j}") for j in range(ctx.dnum)])
+    return ctx.keygen_ksk(s, dev(e_key), dev(a_key), g)
+
+
+def measure_small_keyswitch(ckks, torch, reps=50):
+    """Single KeySwitch at N=2^12, ell=6, k=3, dnum=2, 50-bit primes: latency."""
+    ctx = ckks.Context.from_bits(12, 6, 3, 2, 50)
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(ctx.device)
+    s = dev(synth.ternary(ctx.N, "bench/small/s"))
+    key = _keygen(ctx, torch, s, 0, "bench/small/key")
+    a = dev(synth.uniform_residues(ctx.q, ctx.N, "bench/small/a"))
+    u, v = ctx.empty(6), ctx.empty(6)
+    ws = ctx.workspace(ckks.OP_KEYSWITCH, 6)
+    ms = _timed(torch, lambda: ctx.keyswitch(a, 6, key, u, v, ws), reps)
+    out = {"shape": "KeySwitch N=2^12 ell=6 k=3 dnum=2 50-bit primes", "us_per_keyswitch": ms * 1e3,
+           "keyswitch_per_s": 1e3 / ms,
+           "compulsory_bytes": traffic.compulsory_keyswitch_bytes(ctx.N, 6, 3, 6, 2)}
+    ctx.close()
+    return out
+
+
+def measure_batched(ctx, ckks, torch, reps=5):
+    """64 KeySwitches at levels uniform in {4..24} sharing one key: one batched
+    call (one launch per pipeline step) against one-at-a-time calls on one
+    stream and the same calls spread over 4 streams."""
+    N = ctx.N
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(ctx.device)
+    levels = synth.uniform_ints(64, 4, 24, "batch/levels")
+    s = dev(synth.ternary(N, "bench/batch/s"))
+    key = _keygen(ctx, torch, s, 0, "bench/batch/key")
+    a = [dev(synth.uniform_residues(ctx.q[:ell], N, f"bench/batch/ct{i}")) for i, ell in enumerate(levels)]
+    outs = [(ctx.empty(ell), ctx.empty(ell)) for ell in levels]
+    ws = ctx.batch_workspace(levels)
+    keys = [key] * len(levels)
+    t_batch = _timed(torch, lambda: ctx.keyswitch_batch(a, None, levels, None, keys, outs=outs, ws=ws), reps)
+    ws1 = ctx.workspace(ckks.OP_KEYSWITCH, L)
+
+    def serial():
+        for i, ell in enumerate(levels):
+            ctx.keyswitch(a[i], ell, key, outs[i][0], outs[i][1], ws1)
+
+    t_serial = _timed(torch, serial, reps)
+    streams = [torch.cuda.Stream() for _ in range(4)]
+    ws4 = [ctx.workspace(ckks.OP_KEYSWITCH, L) for _ in range(4)]
+
+    def four():
+        ev = torch.cuda.current_stream().record_event()
+        for st in streams:
+            st.wait_event(ev)
+        for i, ell in enumerate(levels):
+            j = i % 4
+            ctx.keyswitch(a[i], ell, key, outs[i][0], outs[i][1], ws4[j], stream=streams[j])
+        for st in streams:
+            torch.cuda.current_stream().wait_stream(st)
+
+    t_four = _timed(torch, four, reps)
+    ctx.profile(True)
+    ctx.profile_reset()
+    ctx.keyswitch_batch(a, None, levels, None, keys, outs=outs, ws=ws)
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    comp = traffic.compulsory_batch_keyswitch_bytes(N, levels, [0] * len(levels), K_SP, L, DNUM)
+    n = len(levels)
+    del a, outs, ws, ws1, ws4
+    torch.cuda.empty_cache()
+    return {"shape": "64 KeySwitch, ell uniform in {4..24} (seeded), N=2^16, k=8, dnum=3, one shared key",
+            "levels_sum": sum(levels),
+            "batched": {"ms_per_batch": t_batch, "keyswitch_per_s": n / t_batch * 1e3,
+                        "launches": sum(v[1] for v in prof.values()),
+                        "kernel_ms": {k: v[0] for k, v in prof.items() if v[1]}},
+            "serial_one_stream": {"ms_per_batch": t_serial, "keyswitch_per_s": n / t_serial * 1e3},
+            "four_streams": {"ms_per_batch": t_four, "keyswitch_per_s": n / t_four * 1e3},
+            "speedup_vs_serial": t_serial / t_batch,
+            "compulsory_bytes": comp,
+            "hbm_frac_of_measured": comp / (t_batch * 1e-3) / 1e9 / load_peaks()["hbm_gbs"]}
+
+
+def measure_other_rows(ctx, ckks, torch, reps=5):
+    """Rescale (Alg. 1's ModDown_{B,1}) of one ciphertext, and a CoeffToSlot-shaped
+    PtMatVecMult: fftIter = 3 levels at ell = 24, 23, 22 (Alg. 8 with 8 baby x 4
+    giant steps per level, rotation offsets (t*8 + i) * 32^level, 32 seeded
+    diagonals over the extended basis per level, 7 baby + 3 giant rotation keys
+    per level = 30 keys resident, Rescale after each level), all at N=2^16,
+    timed with CUDA events outside the KeySwitch timed region."""
+    N = 1 << LOGN
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(ctx.device)
     a = dev(synth.uniform_residues(ctx.q, N, "bench/rows/a"))
     b = dev(synth.uniform_residues(ctx.q, N, "bench/rows/b"))
-
-    def timed(fn):
-        for _ in range(2):
-            fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            fn()
-        e1.record()
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / reps
-
     ws_r = ctx.workspace(ckks.OP_RESCALE, L)
     oa, ob = ctx.empty(L - 1), ctx.empty(L - 1)
-    rescale_ms = timed(lambda: (ctx.rescale(a, L, oa, ws_r), ctx.rescale(b, L, ob, ws_r)))
+    rescale_ms = _timed(torch, lambda: (ctx.rescale(a, L, oa, ws_r), ctx.rescale(b, L, ob, ws_r)), reps)
 
-    nb, ng = 8, 4
+    nb, ng, radix_log = 8, 4, 5
     twoN = 2 * N
-    g_baby = [1] + [pow(5, i, twoN) for i in range(1, nb)]
-    g_giant = [1] + [pow(5, t * nb, twoN) for t in range(1, ng)]
     s = dev(synth.ternary(N, "bench/rows/s"))
-
-    def key(g, tag):
-        a_key = np.stack([synth.uniform_residues(primes, N, f"bench/rows/{tag}/a{j}") for j in range(DNUM)])
-        e_key = np.stack([synth.gaussian(N, f"bench/rows/{tag}/e{j}") for j in range(DNUM)])
-        return ctx.keygen_ksk(s, dev(e_key), dev(a_key), g)
-
-    kb = [None] + [key(g, f"kb{i}") for i, g in enumerate(g_baby) if i > 0]
-    kg = [None] + [key(g, f"kg{t}") for t, g in enumerate(g_giant) if t > 0]
-    diags = [dev(synth.uniform_residues(ctx.ext_primes(L), N, f"bench/rows/M{d}")) for d in range(nb * ng)]
+    levels = []
+    for lv in range(3):
+        ell = L - lv
+        stride = 1 << (radix_log * lv)
+        g_baby = [1] + [pow(5, i * stride, twoN) for i in range(1, nb)]
+        g_giant = [1] + [pow(5, t * nb * stride, twoN) for t in range(1, ng)]
+        kb = [None] + [_keygen(ctx, torch, s, g, f"bench/rows/l{lv}/kb{i}") for i, g in enumerate(g_baby) if i > 0]
+        kg = [None] + [_keygen(ctx, torch, s, g, f"bench/rows/l{lv}/kg{t}") for t, g in enumerate(g_giant) if t > 0]
+        diags = [dev(synth.uniform_residues(ctx.ext_primes(ell), N, f"bench/rows/l{lv}/M{d}"))
+                 for d in range(nb * ng)]
+        levels.append((ell, g_baby, g_giant, kb, kg, diags))
     ws_p = ctx.workspace(ckks.OP_PTMATVEC, L, ng)
-    pa, pb = ctx.empty(L - 1), ctx.empty(L - 1)
-    pmv_ms = timed(lambda: ctx.ptmatvecmult(a, b, L, nb, ng, g_baby, g_giant, kb, kg, diags, True, pa, pb, ws_p))
-    pmv_bytes = (2 * L + (nb - 1 + ng - 1) * traffic.key_limbs(L, K_SP, L, DNUM) + nb * ng * (L + K_SP)
-                 + 2 * (L - 1)) * traffic.limb_bytes(N)
-    del kb, kg, diags
+    bufs = [(a, b)] + [(ctx.empty(L - 1 - i), ctx.empty(L - 1 - i)) for i in range(3)]
+
+    def level(i):
+        ell, g_baby, g_giant, kb, kg, diags = levels[i]
+        ia, ib = bufs[i]
+        pa, pb = bufs[i + 1]
+        ctx.ptmatvecmult(ia, ib, ell, nb, ng, g_baby, g_giant, kb, kg, diags, True, pa, pb, ws_p)
+
+    per_level = [_timed(torch, lambda i=i: level(i), reps) for i in range(3)]
+    c2s_ms = _timed(torch, lambda: [level(i) for i in range(3)], reps)
+    comp = []
+    for i, (ell, *_rest) in enumerate(levels):
+        comp.append((2 * ell + (nb - 1 + ng - 1) * traffic.key_limbs(ell, K_SP, L, DNUM) + nb * ng * (ell + K_SP)
+                     + 2 * (ell - 1)) * traffic.limb_bytes(N))
+    hbm = load_peaks()["hbm_gbs"]
+    del levels, bufs
     torch.cuda.empty_cache()
     return {
         "rescale": {"ms_per_ciphertext": rescale_ms, "ciphertexts_per_s": 1e3 / rescale_ms,
                     "shape": "2 polys, ell 24 -> 23"},
-        "ptmatvecmult": {"ms_per_level": pmv_ms, "levels_per_s": 1e3 / pmv_ms,
-                         "shape": "ell=24, 8 baby x 4 giant steps, 32 diagonals, 10 keys, rescaled",
-                         "compulsory_bytes": pmv_bytes,
-                         "hbm_frac_of_measured": pmv_bytes / (pmv_ms * 1e-3) / 1e9 / load_peaks()["hbm_gbs"]},
+        "ptmatvecmult": {"shape": "CoeffToSlot-shaped: 3 levels at ell 24, 23, 22; 8 baby x 4 giant steps, "
+                                  "stride 32^level, 32 diagonals and 10 keys per level (30 keys), rescaled",
+                         "ms_per_level": per_level, "ms_coeff_to_slot": c2s_ms,
+                         "coeff_to_slot_per_s": 1e3 / c2s_ms,
+                         "compulsory_bytes_per_level": comp,
+                         "hbm_frac_of_measured_per_level": [c / (t * 1e-3) / 1e9 / hbm for c, t in zip(comp, per_level)]},
     }
 
 
@@ -422,6 +519,8 @@ def run_gpu(args, rank, world, local_rank):
             del items, lanes, lane1
             torch.cuda.empty_cache()
             line["other_rows"] = measure_other_rows(ctx, ckks, torch)
+            line["other_rows"]["batched_keyswitch"] = measure_batched(ctx, ckks, torch)
+            line["other_rows"]["small_keyswitch"] = measure_small_keyswitch(ckks, torch)
         if world == 1 and not args.no_cpu_baseline:
             times = oracle_keyswitch_seconds(1)
             line["cpu_baseline"] = {"value": 1.0 / times[0], "unit": UNIT, "cores": 1, "kind": "oracle",

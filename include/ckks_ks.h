@@ -68,7 +68,8 @@ enum {
     CKKS_OP_HROTATE = 5,
     CKKS_OP_RESCALE = 6,
     CKKS_OP_PTMATVEC = 7,
-    CKKS_OP_KEYGEN = 8
+    CKKS_OP_KEYGEN = 8,
+    CKKS_OP_MULT = 9
 };
 
 typedef struct {
@@ -190,6 +191,25 @@ int ckks_batch_workspace_bytes(const ckks_ctx *ctx, int n, const int *levels, si
 int ckks_keyswitch_batch(ckks_ctx *ctx, int n, const uint64_t *const *d_a, const uint64_t *const *d_b,
                          const int *levels, const uint32_t *galois, const uint64_t *const *d_keys,
                          uint64_t *const *d_oa, uint64_t *const *d_ob, void *ws, ckks_stream_t stream);
+
+/* Mult with relinearisation and Rescale (Algorithm 2): for ciphertexts
+ * (d_a1, d_b1), (d_a2, d_b2) at level ell >= 2 (evaluation form, [ell][N]):
+ * (a3, b3, c3) = (a1 a2, a1 b2 + a2 b1, b1 b2) slot-wise, (u, v) = KeySwitch
+ * of a3 with the relinearisation key d_key (s^2 -> s), and the outputs
+ * d_oa, d_ob ([ell-1][N]) are Rescale(b3 + u), Rescale(c3 + v).  Workspace
+ * CKKS_OP_MULT.  The batched form runs n such products (each at its own level,
+ * with its own key) with one launch per pipeline step, with the same bits per
+ * entry; its workspace comes from ckks_mult_batch_workspace_bytes.  Outputs
+ * must not overlap inputs.  CKKS_EINVAL for a level < 2 or > L, or a null or
+ * misaligned pointer. */
+int ckks_mult(ckks_ctx *ctx, const uint64_t *d_a1, const uint64_t *d_b1, const uint64_t *d_a2,
+              const uint64_t *d_b2, int level, const uint64_t *d_key, uint64_t *d_oa, uint64_t *d_ob, void *ws,
+              ckks_stream_t stream);
+int ckks_mult_batch_workspace_bytes(const ckks_ctx *ctx, int n, const int *levels, size_t *bytes);
+int ckks_mult_batch(ckks_ctx *ctx, int n, const uint64_t *const *d_a1, const uint64_t *const *d_b1,
+                    const uint64_t *const *d_a2, const uint64_t *const *d_b2, const int *levels,
+                    const uint64_t *const *d_keys, uint64_t *const *d_oa, uint64_t *const *d_ob, void *ws,
+                    ckks_stream_t stream);
 
 /* PtMatVecMult with hoisted ModUp and ModDown (Algorithm 8) in baby-step /
  * giant-step form (Sec. 5.2): nb baby steps, ng giant steps, diagonal (t, i) =

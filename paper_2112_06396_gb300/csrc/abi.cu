@@ -634,6 +634,10 @@ extern "C" int ckks_workspace_bytes(const ckks_ctx *c, int op, int ell, int r, s
         w = pmv_layout(c, ell, r).total;
         break;
     case CKKS_OP_KEYGEN: w = size_t(3) * (c->L + c->k) * N; break;
+    case CKKS_OP_MULT:
+        if (ell < 2) return CKKS_EINVAL;
+        w = hr_layout(c, ell).total + size_t(5) * ell * N;
+        break;
     default: return CKKS_EINVAL;
     }
     *bytes = w * sizeof(u64);
@@ -762,11 +766,28 @@ extern "C" int ckks_hrotate(ckks_ctx *ctx, const uint64_t *a, const uint64_t *b,
     return CKKS_OK;
 }
 
-// ---- batched key switching
-// Per-ciphertext workspace: the HRotate layout of its level, packed in batch order.
-static size_t batch_ws_words(const ckks_ctx *c, int n, const int *levels) {
+// ---- batched key switching and Mult
+// One entry of a batch (host side).
+enum { BE_KEYSWITCH = 0, BE_HROTATE = 1, BE_MULT = 2 };
+struct BatchEntry {
+    int kind;
+    const u64 *a, *b;    // KeySwitch: a; HRotate: (a, b); Mult: first ciphertext (a1, b1)
+    const u64 *a2, *b2;  // Mult: second ciphertext
+    const u64 *key;
+    u64 *oa, *ob;
+    int ell;
+    uint32_t galois;
+};
+
+// Per-entry workspace: the HRotate layout of its level, then for Mult entries
+// a3, b3, c3 and the key switch's outputs (a', b') before the Rescale.
+static size_t entry_ws_words(const ckks_ctx *c, int kind, int ell) {
+    return hr_layout(c, ell).total + (kind == BE_MULT ? size_t(5) * ell * c->N : 0);
+}
+
+static size_t batch_ws_words(const ckks_ctx *c, int n, const int *levels, int kind) {
     size_t w = 0;
-    for (int i = 0; i < n; ++i) w += hr_layout(c, levels[i]).total;
+    for (int i = 0; i < n; ++i) w += entry_ws_words(c, kind, levels[i]);
     return w;
 }
 
@@ -774,13 +795,59 @@ extern "C" int ckks_batch_workspace_bytes(const ckks_ctx *ctx, int n, const int 
     if (ctx == nullptr || bytes == nullptr || n < 0 || (n > 0 && levels == nullptr)) return CKKS_EINVAL;
     for (int i = 0; i < n; ++i)
         if (!level_ok(ctx, levels[i])) return CKKS_EINVAL;
-    *bytes = batch_ws_words(ctx, n, levels) * sizeof(u64);
+    *bytes = batch_ws_words(ctx, n, levels, BE_HROTATE) * sizeof(u64);
     return CKKS_OK;
 }
 
-// One ciphertext of a batch on its own (contexts without the split conversion).
-static int batch_one(ckks_ctx *ctx, const CtDesc &c, cudaStream_t st) {
+extern "C" int ckks_mult_batch_workspace_bytes(const ckks_ctx *ctx, int n, const int *levels, size_t *bytes) {
+    if (ctx == nullptr || bytes == nullptr || n < 0 || (n > 0 && levels == nullptr)) return CKKS_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (!level_ok(ctx, levels[i]) || levels[i] < 2) return CKKS_EINVAL;
+    *bytes = batch_ws_words(ctx, n, levels, BE_MULT) * sizeof(u64);
+    return CKKS_OK;
+}
+
+// The device descriptor of one entry; ws is the entry's workspace.
+static CtDesc entry_desc(const ckks_ctx *ctx, const BatchEntry &e, u64 *ws, TensorEntry *te) {
+    const size_t N = ctx->N, lN = size_t(e.ell) * N;
+    CtDesc x{};
+    x.key = e.key;
+    x.ws = ws;
+    x.ell = e.ell;
+    x.galois = 1;
+    if (e.kind == BE_MULT) {
+        u64 *m = ws + hr_layout(ctx, e.ell).total;
+        *te = TensorEntry{e.a, e.b, e.a2, e.b2, m, m + lN, m + 2 * lN, e.ell};
+        x.a = m;
+        x.add[0] = m + lN;
+        x.add[1] = m + 2 * lN;
+        x.oa = m + 3 * lN;
+        x.ob = m + 4 * lN;
+        x.ra = e.oa;
+        x.rb = e.ob;
+    } else {
+        x.a = e.a;
+        x.oa = e.oa;
+        x.ob = e.ob;
+        if (e.kind == BE_HROTATE) {
+            x.add[1] = e.b;
+            x.galois = e.galois;
+        }
+    }
+    return x;
+}
+
+// One entry on its own, with the single-operation launches (contexts whose
+// primes are too wide for the split basis conversion).
+static int entry_one(ckks_ctx *ctx, const CtDesc &c, const TensorEntry *te, cudaStream_t st) {
     const size_t N = ctx->N;
+    if (te != nullptr) {
+        TensorBatch T;
+        T.n = 1;
+        T.logN = ctx->logN;
+        T.e[0] = *te;
+        CK(launch_tensor(ctx, T, st));
+    }
     const HrLayout lo = hr_layout(ctx, c.ell);
     RC(modup_all(ctx, c.a, c.ell, c.ws + lo.ext, c.ws + lo.tmp, st));
     u64 *u = c.ws + lo.uv, *v = u + size_t(c.ell + ctx->k) * N;
@@ -788,25 +855,20 @@ static int batch_one(ckks_ctx *ctx, const CtDesc &c, cudaStream_t st) {
     CK(launch_inner_prod(ctx, ia, st));
     const u64 *in[2] = {u, v};
     u64 *out[2] = {c.oa, c.ob};
-    const u64 *add[2] = {nullptr, c.b};
-    return moddown_polys(ctx, c.ell, 2, in, out, add, c.galois, 0, c.ws + lo.tmp,
-                         c.ws + lo.tmp + size_t(2) * ctx->k * N, st);
+    const u64 *add[2] = {c.add[0], c.add[1]};
+    RC(moddown_polys(ctx, c.ell, 2, in, out, add, c.galois, 0, c.ws + lo.tmp, c.ws + lo.tmp + size_t(2) * ctx->k * N,
+                     st));
+    if (c.ra != nullptr) {
+        const u64 *rin[2] = {c.oa, c.ob};
+        u64 *rout[2] = {c.ra, c.rb};
+        RC(rescale_polys(ctx, c.ell, 2, rin, rout, c.ws, c.ws + 2 * N, st));
+    }
+    return CKKS_OK;
 }
 
-extern "C" int ckks_keyswitch_batch(ckks_ctx *ctx, int n, const uint64_t *const *a, const uint64_t *const *b,
-                                    const int *levels, const uint32_t *galois, const uint64_t *const *keys,
-                                    uint64_t *const *oa, uint64_t *const *ob, void *ws, ckks_stream_t stream) {
-    if (ctx == nullptr || n < 0) return CKKS_EINVAL;
-    if (n == 0) return CKKS_OK;
-    if (!a || !levels || !keys || !oa || !ob || !al16(ws)) return CKKS_EINVAL;
-    for (int i = 0; i < n; ++i) {
-        const bool rot = b != nullptr && b[i] != nullptr;
-        if (!level_ok(ctx, levels[i]) || !al16(a[i]) || !al16(keys[i]) || !al16(oa[i]) || !al16(ob[i]))
-            return CKKS_EINVAL;
-        if (rot && (!al16(b[i]) || galois == nullptr || !galois_ok(ctx, galois[i]))) return CKKS_EINVAL;
-    }
-    cudaStream_t st = (cudaStream_t)stream;
-    u64 *w = static_cast<u64 *>(ws);
+// Runs a batch in groups of kMaxCts entries; the workspace holds every
+// entry's region (entry_ws_words) in batch order.
+static int run_batch(ckks_ctx *ctx, int n, const BatchEntry *e, u64 *w, cudaStream_t st) {
     for (int c0 = 0; c0 < n; c0 += kMaxCts) {
         KsBatchDesc d{};
         d.n = std::min(n - c0, kMaxCts);
@@ -815,34 +877,82 @@ extern "C" int ckks_keyswitch_batch(ckks_ctx *ctx, int n, const uint64_t *const 
         d.alpha = ctx->alpha;
         d.dnum = ctx->dnum;
         d.logN = ctx->logN;
+        TensorBatch T;
+        T.n = 0;
+        T.logN = ctx->logN;
+        int te_of[kMaxCts];
         for (int c = 0; c < d.n; ++c) {
-            const int i = c0 + c;
-            const bool rot = b != nullptr && b[i] != nullptr;
-            CtDesc &x = d.ct[c];
-            x.a = a[i];
-            x.b = rot ? b[i] : nullptr;
-            x.key = keys[i];
-            x.oa = oa[i];
-            x.ob = ob[i];
-            x.ws = w;
-            x.ell = levels[i];
-            x.galois = rot ? galois[i] : 1u;
-            w += hr_layout(ctx, levels[i]).total;
+            const BatchEntry &x = e[c0 + c];
+            te_of[c] = -1;
+            TensorEntry te{};
+            d.ct[c] = entry_desc(ctx, x, w, &te);
+            if (x.kind == BE_MULT) {
+                te_of[c] = T.n;
+                T.e[T.n++] = te;
+            }
+            w += entry_ws_words(ctx, x.kind, x.ell);
         }
         if (!ctx->split_bits) {
-            for (int c = 0; c < d.n; ++c) RC(batch_one(ctx, d.ct[c], st));
+            for (int c = 0; c < d.n; ++c) RC(entry_one(ctx, d.ct[c], te_of[c] >= 0 ? &T.e[te_of[c]] : nullptr, st));
             continue;
         }
-        // one launch per phase over the whole batch
+        // one launch per step over the whole batch
+        CK(launch_tensor(ctx, T, st));
         CK(launch_ntt_batch(ctx, d, PH_INTT_A, st));
-        CK(launch_bconv_batch(ctx, d, 0, st));
+        CK(launch_bconv_batch(ctx, d, GM_MODUP, st));
         CK(launch_ntt_batch(ctx, d, PH_NTT_UP, st));
         CK(launch_inner_prod_batch(ctx, d, st));
         CK(launch_ntt_batch(ctx, d, PH_INTT_P, st));
-        CK(launch_bconv_batch(ctx, d, 1, st));
+        CK(launch_bconv_batch(ctx, d, GM_MODDOWN, st));
         CK(launch_ntt_batch(ctx, d, PH_NTT_DOWN, st));
+        if (T.n > 0) {
+            CK(launch_ntt_batch(ctx, d, PH_RS_INTT, st));
+            CK(launch_bconv_batch(ctx, d, GM_RESCALE, st));
+            CK(launch_ntt_batch(ctx, d, PH_RS_NTT, st));
+        }
     }
     return CKKS_OK;
+}
+
+extern "C" int ckks_keyswitch_batch(ckks_ctx *ctx, int n, const uint64_t *const *a, const uint64_t *const *b,
+                                    const int *levels, const uint32_t *galois, const uint64_t *const *keys,
+                                    uint64_t *const *oa, uint64_t *const *ob, void *ws, ckks_stream_t stream) {
+    if (ctx == nullptr || n < 0) return CKKS_EINVAL;
+    if (n == 0) return CKKS_OK;
+    if (!a || !levels || !keys || !oa || !ob || !al16(ws)) return CKKS_EINVAL;
+    std::vector<BatchEntry> e(n);
+    for (int i = 0; i < n; ++i) {
+        const bool rot = b != nullptr && b[i] != nullptr;
+        if (!level_ok(ctx, levels[i]) || !al16(a[i]) || !al16(keys[i]) || !al16(oa[i]) || !al16(ob[i]))
+            return CKKS_EINVAL;
+        if (rot && (!al16(b[i]) || galois == nullptr || !galois_ok(ctx, galois[i]))) return CKKS_EINVAL;
+        e[i] = BatchEntry{rot ? BE_HROTATE : BE_KEYSWITCH, a[i], rot ? b[i] : nullptr, nullptr, nullptr, keys[i],
+                          oa[i], ob[i], levels[i], rot ? galois[i] : 1u};
+    }
+    return run_batch(ctx, n, e.data(), static_cast<u64 *>(ws), (cudaStream_t)stream);
+}
+
+extern "C" int ckks_mult_batch(ckks_ctx *ctx, int n, const uint64_t *const *a1, const uint64_t *const *b1,
+                               const uint64_t *const *a2, const uint64_t *const *b2, const int *levels,
+                               const uint64_t *const *keys, uint64_t *const *oa, uint64_t *const *ob, void *ws,
+                               ckks_stream_t stream) {
+    if (ctx == nullptr || n < 0) return CKKS_EINVAL;
+    if (n == 0) return CKKS_OK;
+    if (!a1 || !b1 || !a2 || !b2 || !levels || !keys || !oa || !ob || !al16(ws)) return CKKS_EINVAL;
+    std::vector<BatchEntry> e(n);
+    for (int i = 0; i < n; ++i) {
+        if (!level_ok(ctx, levels[i]) || levels[i] < 2 || !al16(a1[i]) || !al16(b1[i]) || !al16(a2[i]) ||
+            !al16(b2[i]) || !al16(keys[i]) || !al16(oa[i]) || !al16(ob[i]))
+            return CKKS_EINVAL;
+        e[i] = BatchEntry{BE_MULT, a1[i], b1[i], a2[i], b2[i], keys[i], oa[i], ob[i], levels[i], 1u};
+    }
+    return run_batch(ctx, n, e.data(), static_cast<u64 *>(ws), (cudaStream_t)stream);
+}
+
+extern "C" int ckks_mult(ckks_ctx *ctx, const uint64_t *a1, const uint64_t *b1, const uint64_t *a2,
+                         const uint64_t *b2, int level, const uint64_t *key, uint64_t *oa, uint64_t *ob, void *ws,
+                         ckks_stream_t stream) {
+    return ckks_mult_batch(ctx, 1, &a1, &b1, &a2, &b2, &level, &key, &oa, &ob, ws, stream);
 }
 
 extern "C" int ckks_ptmatvecmult(ckks_ctx *ctx, const uint64_t *a, const uint64_t *b, int ell, int nb, int ng,

@@ -189,24 +189,35 @@ static cudaError_t launch_split(const ckks_ctx *ctx, const GMAP &gm, int ngroups
     return cudaGetLastError();
 }
 
-// The basis conversions of one batched key-switching phase (ModUp digits or
-// ModDown polynomials of every ciphertext).  Needs the split conversion.
+// The basis conversions of one batched phase: ModUp digits (GM_MODUP), the
+// ModDown of both polynomials (GM_MODDOWN) or the Rescale of both polynomials
+// of the Mult entries (GM_RESCALE).  Needs the split conversion.
 cudaError_t launch_bconv_batch(const ckks_ctx *ctx, const KsBatchDesc &d, int down, cudaStream_t st) {
     GroupMapBatch gm;
     gm.d = d;
     gm.down = down;
     gm.modup = ctx->d_modup;
     gm.moddown = ctx->d_moddown;
+    gm.rescale = ctx->d_rescale;
     int groups = 0, n_all = 0;
     for (int c = 0; c < d.n; ++c) {
         const int ell = d.ct[c].ell, beta = (ell + d.alpha - 1) / d.alpha;
         gm.d.pre[c] = groups;
-        groups += down ? 2 : beta;
-        n_all = std::max(n_all, down ? ell : ell + d.k - std::min(d.alpha, ell - (beta - 1) * d.alpha));
+        if (down == GM_MODUP) {
+            groups += beta;
+            n_all = std::max(n_all, ell + d.k - std::min(d.alpha, ell - (beta - 1) * d.alpha));
+        } else if (down == GM_MODDOWN) {
+            groups += 2;
+            n_all = std::max(n_all, ell);
+        } else if (d.ct[c].ra != nullptr) {
+            groups += 2;
+            n_all = std::max(n_all, ell - 1);
+        }
     }
     gm.d.pre[d.n] = groups;
-    if (groups == 0) return cudaSuccess;
-    return launch_split(ctx, gm, groups, n_all, down ? d.k : d.alpha, st);
+    if (groups == 0 || n_all == 0) return cudaSuccess;
+    const int max_src = down == GM_MODUP ? d.alpha : down == GM_MODDOWN ? d.k : 1;
+    return launch_split(ctx, gm, groups, n_all, max_src, st);
 }
 
 cudaError_t launch_bconv(const ckks_ctx *ctx, const BConvLaunch &l, int max_src, cudaStream_t st) {

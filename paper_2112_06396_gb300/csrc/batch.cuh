@@ -23,6 +23,7 @@ struct LimbIO {
     const u64 *ex;
     u64 *eout;
     const u64 *eadd;
+    const ulonglong2 *cmul;  // scale table (indexed by prime) of the epilogue
     uint32_t galois;
     int accumulate;
 };
@@ -40,6 +41,7 @@ struct MapList {
         io.ex = nullptr;
         io.eout = nullptr;
         io.eadd = nullptr;
+        io.cmul = e.cmul;
         io.galois = 1;
         io.accumulate = 0;
         if (e.mode == EPI_SCALE) {
@@ -53,20 +55,27 @@ struct MapList {
         }
         return io;
     }
-    __device__ __forceinline__ const ulonglong2 *cmul() const { return e.cmul; }
 };
 
 // ---------------------------------------------------------------- batched key switching
 constexpr int kMaxCts = 64;
 
-// One ciphertext of a batch.  b == nullptr: KeySwitch of a (outputs u, v);
-// otherwise HRotate with one rotation (Algorithm 4): (u, v + Automorph_g(b)).
-// ws: this ciphertext's workspace, laid out for its level:
+// One entry of a batch: a key switch of a (evaluation form, [ell][N]) whose
+// ModDown epilogue adds add[p] read through Automorph_galois to output p:
+//   KeySwitch:                 add = {0, 0}, galois = 1, outputs (u, v);
+//   HRotate, one rotation:     add = {0, b}, digits read through galois
+//                              (Algorithm 4): (u, v + Automorph_g(b));
+//   Mult (Algorithm 2):        a = a1*a2, add = {a1 b2 + a2 b1, b1 b2},
+//                              galois = 1, then ra/rb = Rescale(oa/ob).
+// ws: this entry's workspace, laid out for its level:
 //   ext [beta][ell+k][N] | uv [2][ell+k][N] | tmp (acoeff [ell][N], later
-//   pcoeff [2][k][N] and w [2][ell][N]).
+//   pcoeff [2][k][N] and w [2][ell][N]).  After the key switch the Rescale
+//   of a Mult entry reuses ext: c [2][N] | w [2][ell-1][N].
 struct CtDesc {
-    const u64 *a, *b, *key;
+    const u64 *a, *key;
+    const u64 *add[2];
     u64 *oa, *ob, *ws;
+    u64 *ra, *rb;  // Rescale outputs [ell-1][N] (Mult entries), else null
     int ell;
     uint32_t galois;
 };
@@ -108,23 +117,27 @@ __device__ __forceinline__ int batch_find(const KsBatchDesc &d, int l, int &i) {
     return lo;
 }
 
-// Per-ciphertext counts of the batched phases.
-enum { PH_INTT_A = 0, PH_NTT_UP = 1, PH_INTT_P = 2, PH_NTT_DOWN = 3 };
-__host__ __device__ __forceinline__ int phase_count(const KsBatchDesc &d, int ell, int phase) {
+// Per-entry limb counts of the batched phases (Rescale phases: Mult entries only).
+enum { PH_INTT_A = 0, PH_NTT_UP = 1, PH_INTT_P = 2, PH_NTT_DOWN = 3, PH_RS_INTT = 4, PH_RS_NTT = 5 };
+__host__ __device__ __forceinline__ int phase_count(const KsBatchDesc &d, const CtDesc &c, int phase) {
+    const int ell = c.ell;
     const int beta = (ell + d.alpha - 1) / d.alpha;
     switch (phase) {
     case PH_INTT_A: return ell;
     case PH_NTT_UP: return beta * (ell + d.k) - ell;
     case PH_INTT_P: return 2 * d.k;
-    default: return 2 * ell;
+    case PH_NTT_DOWN: return 2 * ell;
+    case PH_RS_INTT: return c.ra != nullptr ? 2 : 0;
+    default: return c.ra != nullptr ? 2 * (ell - 1) : 0;
     }
 }
 
 struct MapBatch {
     KsBatchDesc d;
     int phase;
-    int second;            // second pass: in place on the first pass's output
-    const ulonglong2 *cm;  // [P^-1]_q per prime (ModDown epilogue)
+    int second;               // second pass: in place on the first pass's output
+    const ulonglong2 *cm;     // [P^-1]_q per prime (ModDown epilogue)
+    const ulonglong2 *qlinv;  // [q_{ell-1}^-1]_{q_i} at ell*(L+k) + i (Rescale epilogue)
     __device__ __forceinline__ LimbIO get(int l, uint32_t N) const {
         int i;
         const int c = batch_find(d, l, i);
@@ -135,6 +148,7 @@ struct MapBatch {
         io.ex = nullptr;
         io.eout = nullptr;
         io.eadd = nullptr;
+        io.cmul = cm;
         io.galois = 1;
         io.accumulate = 0;
         if (phase == PH_INTT_A) {
@@ -165,7 +179,7 @@ struct MapBatch {
             io.src = lo.uv + (size_t(poly) * lo.ext + ell + m) * N;
             io.dst = lo.pcoeff + (size_t(poly) * d.k + m) * N;
             io.prime = d.L + m;
-        } else {
+        } else if (phase == PH_NTT_DOWN) {
             const int t = i >> 1, poly = i & 1;
             u64 *p = lo.w + (size_t(poly) * ell + t) * N;
             io.src = p;
@@ -173,13 +187,37 @@ struct MapBatch {
             io.prime = t;
             io.ex = lo.uv + (size_t(poly) * lo.ext + t) * N;
             io.eout = (poly ? ct.ob : ct.oa) + size_t(t) * N;
-            io.eadd = (poly && ct.b != nullptr) ? ct.b + size_t(t) * N : nullptr;
+            io.eadd = ct.add[poly] != nullptr ? ct.add[poly] + size_t(t) * N : nullptr;
             io.galois = ct.galois;
+        } else if (phase == PH_RS_INTT) {
+            // last limb of the key switch's output p -> c[p]
+            io.src = (i ? ct.ob : ct.oa) + size_t(ell - 1) * N;
+            io.dst = ct.ws + size_t(i) * N;
+            io.prime = ell - 1;
+        } else {
+            const int t = i >> 1, poly = i & 1;
+            u64 *p = ct.ws + (size_t(2) + size_t(poly) * (ell - 1) + t) * N;
+            io.src = p;
+            io.dst = p;
+            io.prime = t;
+            io.ex = (poly ? ct.ob : ct.oa) + size_t(t) * N;
+            io.eout = (poly ? ct.rb : ct.ra) + size_t(t) * N;
+            io.cmul = qlinv + size_t(ell) * (d.L + d.k);
         }
         if (second) io.src = io.dst;
         return io;
     }
-    __device__ __forceinline__ const ulonglong2 *cmul() const { return cm; }
+};
+
+// Tensor step of the Mult entries of a batch.
+struct TensorEntry {
+    const u64 *a1, *b1, *a2, *b2;
+    u64 *a3, *b3, *c3;
+    int ell;
+};
+struct TensorBatch {
+    int n, logN;
+    TensorEntry e[kMaxCts];
 };
 
 // Basis-conversion groups.
@@ -188,11 +226,13 @@ struct GroupMapList {
     __device__ __forceinline__ BConvGroup get(int gi) const { return l.g[gi]; }
 };
 
+enum { GM_MODUP = 0, GM_MODDOWN = 1, GM_RESCALE = 2 };
 struct GroupMapBatch {
     KsBatchDesc d;
-    int down;                   // 0: ModUp digits, 1: ModDown polynomials
+    int down;                   // GM_MODUP: digits; GM_MODDOWN / GM_RESCALE: 2 polynomials
     const BConvPlan *modup;     // [(L+1)*dnum]
     const BConvPlan *moddown;   // [L+1]
+    const BConvPlan *rescale;   // [L+1]
     __device__ __forceinline__ BConvGroup get(int gi) const {
         int i;
         const int c = batch_find(d, gi, i);
@@ -200,14 +240,18 @@ struct GroupMapBatch {
         const CtLayout lo = ct_layout(d, ct);
         const size_t N = size_t(1) << d.logN;
         BConvGroup g;
-        if (!down) {
+        if (down == GM_MODUP) {
             g.plan = modup + size_t(ct.ell) * d.dnum + i;
             g.src = lo.acoeff + size_t(i) * d.alpha * N;
             g.dst = lo.extp + size_t(i) * lo.ext * N;
-        } else {
+        } else if (down == GM_MODDOWN) {
             g.plan = moddown + ct.ell;
             g.src = lo.pcoeff + size_t(i) * d.k * N;
             g.dst = lo.w + size_t(i) * ct.ell * N;
+        } else {
+            g.plan = rescale + ct.ell;
+            g.src = ct.ws + size_t(i) * N;
+            g.dst = ct.ws + (size_t(2) + size_t(i) * (ct.ell - 1)) * N;
         }
         return g;
     }

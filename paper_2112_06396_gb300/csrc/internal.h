@@ -99,6 +99,7 @@ struct InnerArgs {
 };
 cudaError_t launch_inner_prod(const ckks_ctx *ctx, const InnerArgs &a, cudaStream_t st);
 cudaError_t launch_inner_prod_batch(const ckks_ctx *ctx, const KsBatchDesc &d, cudaStream_t st);
+cudaError_t launch_tensor(const ckks_ctx *ctx, const TensorBatch &T, cudaStream_t st);
 
 struct PmvArgs {
     const u64 *ext;      // hoisted ModUp outputs [beta][ell+k][N]

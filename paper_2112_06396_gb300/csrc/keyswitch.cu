@@ -11,6 +11,8 @@
 #include "common.cuh"
 #include "internal.h"
 
+#include <algorithm>
+
 namespace ckks {
 
 __device__ __forceinline__ ulonglong2 ld2(const u64 *p) { return *reinterpret_cast<const ulonglong2 *>(p); }
@@ -110,24 +112,30 @@ cudaError_t launch_inner_prod(const ckks_ctx *ctx, const InnerArgs &a, cudaStrea
     return cudaGetLastError();
 }
 
-// Batched KSKInnerProd: grid.y runs over the extended positions of every
-// ciphertext of the batch (ell_c + k each).  Each ciphertext reads its own
-// digits (its workspace), its own key and its own Galois element; its u, v land
-// in its workspace.  BMAX > 0: the digit loop is unrolled to BMAX with every
-// load issued up front; BMAX == 0: plain loop.
+// Batched KSKInnerProd.  The grid is (entry, coefficient tile, prime of the
+// extended basis) with the entry index fastest, so the CTAs of every entry at
+// one (tile, prime) are scheduled back to back: a key shared by several
+// entries is fetched from DRAM by the first of them and served from L2 to the
+// rest (cached loads, unlike the single-ciphertext kernel, whose key is used
+// once and streamed).  A chain prime q_i belongs to the entries with ell > i
+// (position i), a special prime p_m to every entry (position ell + m); CTAs of
+// entries below a chain prime exit at once.  Each entry reads its own digits
+// through its own Galois element and writes its u, v into its workspace.
 template <int BMAX>
 __global__ void __launch_bounds__(256) inner_prod_batch_kernel(const __grid_constant__ KsBatchDesc d,
                                                                const PrimeInfo *__restrict__ pinfo) {
+    const CtDesc &ct = d.ct[blockIdx.x];
+    const int ell = ct.ell;
+    const int pi = blockIdx.z;
+    if (pi < d.L && pi >= ell) return;
     const int logN = d.logN;
     const size_t N = size_t(1) << logN;
-    const uint32_t n0 = (blockIdx.x * blockDim.x + threadIdx.x) * 2;
+    const uint32_t n0 = (blockIdx.y * blockDim.x + threadIdx.x) * 2;
     if (n0 >= N) return;
-    int t;
-    const int c = batch_find(d, blockIdx.y, t);
-    const CtDesc &ct = d.ct[c];
+    const int LK = d.L + d.k, alpha = d.alpha;
+    const int t = pi < d.L ? pi : ell + (pi - d.L);
     const CtLayout lo = ct_layout(d, ct);
-    const int ell = ct.ell, LK = d.L + d.k, alpha = d.alpha, beta = lo.beta;
-    const int prime = t < ell ? t : d.L + (t - ell);
+    const int beta = lo.beta;
     const uint32_t g = ct.galois;
     const u64 *key = ct.key;
     u64 ul0 = 0, uh0 = 0, ul1 = 0, uh1 = 0, vl0 = 0, vh0 = 0, vl1 = 0, vh1 = 0;
@@ -139,8 +147,8 @@ __global__ void __launch_bounds__(256) inner_prod_batch_kernel(const __grid_cons
                 const bool own = t < ell && (t / alpha) == j;
                 const u64 *src = own ? ct.a + size_t(t) * N : lo.extp + (size_t(j) * lo.ext + t) * N;
                 dv[j] = ld2_perm(src, n0, g, logN);
-                ka[j] = ld2_stream(key + ((size_t(j) * 2 + 0) * LK + prime) * N + n0);
-                kb[j] = ld2_stream(key + ((size_t(j) * 2 + 1) * LK + prime) * N + n0);
+                ka[j] = ld2(key + ((size_t(j) * 2 + 0) * LK + pi) * N + n0);
+                kb[j] = ld2(key + ((size_t(j) * 2 + 1) * LK + pi) * N + n0);
             }
         }
 #pragma unroll
@@ -157,38 +165,71 @@ __global__ void __launch_bounds__(256) inner_prod_batch_kernel(const __grid_cons
             const bool own = t < ell && (t / alpha) == j;
             const u64 *src = own ? ct.a + size_t(t) * N : lo.extp + (size_t(j) * lo.ext + t) * N;
             const ulonglong2 dv = ld2_perm(src, n0, g, logN);
-            const ulonglong2 ka = ld2_stream(key + ((size_t(j) * 2 + 0) * LK + prime) * N + n0);
-            const ulonglong2 kb = ld2_stream(key + ((size_t(j) * 2 + 1) * LK + prime) * N + n0);
-            mac128(ul0, uh0, dv.x, ka.x);
-            mac128(ul1, uh1, dv.y, ka.y);
-            mac128(vl0, vh0, dv.x, kb.x);
-            mac128(vl1, vh1, dv.y, kb.y);
+            const ulonglong2 a2 = ld2(key + ((size_t(j) * 2 + 0) * LK + pi) * N + n0);
+            const ulonglong2 b2 = ld2(key + ((size_t(j) * 2 + 1) * LK + pi) * N + n0);
+            mac128(ul0, uh0, dv.x, a2.x);
+            mac128(ul1, uh1, dv.y, a2.y);
+            mac128(vl0, vh0, dv.x, b2.x);
+            mac128(vl1, vh1, dv.y, b2.y);
         }
     }
-    const PrimeInfo P = pinfo[prime];
+    const PrimeInfo P = pinfo[pi];
     st2(lo.uv + size_t(t) * N + n0, make_ulonglong2(reduce128(ul0, uh0, P), reduce128(ul1, uh1, P)));
     st2(lo.uv + (size_t(lo.ext) + t) * N + n0, make_ulonglong2(reduce128(vl0, vh0, P), reduce128(vl1, vh1, P)));
 }
 
 cudaError_t launch_inner_prod_batch(const ckks_ctx *ctx, const KsBatchDesc &d, cudaStream_t st) {
-    KsBatchDesc m = d;
-    int count = 0;
-    for (int c = 0; c < d.n; ++c) {
-        m.pre[c] = count;
-        count += d.ct[c].ell + d.k;
-    }
-    m.pre[d.n] = count;
-    if (count == 0) return cudaSuccess;
+    if (d.n == 0) return cudaSuccess;
+    int units = 0;
+    for (int c = 0; c < d.n; ++c) units += d.ct[c].ell + d.k;
     const int threads = 256;
-    dim3 grid(unsigned((ctx->N / 2 + threads - 1) / threads), unsigned(count));
-    ProfScope ps(ctx, K_INNER, count, st);
+    dim3 grid(unsigned(d.n), unsigned((ctx->N / 2 + threads - 1) / threads), unsigned(ctx->L + ctx->k));
+    ProfScope ps(ctx, K_INNER, units, st);
     switch (ctx->dnum) {
-    case 1: inner_prod_batch_kernel<1><<<grid, threads, 0, st>>>(m, ctx->d_pinfo); break;
-    case 2: inner_prod_batch_kernel<2><<<grid, threads, 0, st>>>(m, ctx->d_pinfo); break;
-    case 3: inner_prod_batch_kernel<3><<<grid, threads, 0, st>>>(m, ctx->d_pinfo); break;
-    case 4: inner_prod_batch_kernel<4><<<grid, threads, 0, st>>>(m, ctx->d_pinfo); break;
-    default: inner_prod_batch_kernel<0><<<grid, threads, 0, st>>>(m, ctx->d_pinfo);
+    case 1: inner_prod_batch_kernel<1><<<grid, threads, 0, st>>>(d, ctx->d_pinfo); break;
+    case 2: inner_prod_batch_kernel<2><<<grid, threads, 0, st>>>(d, ctx->d_pinfo); break;
+    case 3: inner_prod_batch_kernel<3><<<grid, threads, 0, st>>>(d, ctx->d_pinfo); break;
+    case 4: inner_prod_batch_kernel<4><<<grid, threads, 0, st>>>(d, ctx->d_pinfo); break;
+    default: inner_prod_batch_kernel<0><<<grid, threads, 0, st>>>(d, ctx->d_pinfo);
     }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ Mult tensor step
+// (a3, b3, c3) = (a1 a2, a1 b2 + a2 b1, b1 b2) slot-wise (Algorithm 2), for
+// every Mult entry of a batch.  Grid (entry, coefficient tile, limb).
+__global__ void __launch_bounds__(256) tensor_kernel(const __grid_constant__ TensorBatch T,
+                                                     const PrimeInfo *__restrict__ pinfo) {
+    const TensorEntry &e = T.e[blockIdx.x];
+    const int i = blockIdx.z;
+    if (i >= e.ell) return;
+    const size_t N = size_t(1) << T.logN;
+    const uint32_t n0 = (blockIdx.y * blockDim.x + threadIdx.x) * 2;
+    if (n0 >= N) return;
+    const size_t o = size_t(i) * N + n0;
+    const ulonglong2 a1 = ld2(e.a1 + o), b1 = ld2(e.b1 + o), a2 = ld2(e.a2 + o), b2 = ld2(e.b2 + o);
+    const PrimeInfo P = pinfo[i];
+    st2(e.a3 + o, make_ulonglong2(mul_mod(a1.x, a2.x, P), mul_mod(a1.y, a2.y, P)));
+    u64 l0 = 0, h0 = 0, l1 = 0, h1 = 0;
+    mac128(l0, h0, a1.x, b2.x);
+    mac128(l0, h0, a2.x, b1.x);
+    mac128(l1, h1, a1.y, b2.y);
+    mac128(l1, h1, a2.y, b1.y);
+    st2(e.b3 + o, make_ulonglong2(reduce128(l0, h0, P), reduce128(l1, h1, P)));
+    st2(e.c3 + o, make_ulonglong2(mul_mod(b1.x, b2.x, P), mul_mod(b1.y, b2.y, P)));
+}
+
+cudaError_t launch_tensor(const ckks_ctx *ctx, const TensorBatch &T, cudaStream_t st) {
+    if (T.n == 0) return cudaSuccess;
+    int maxell = 0, units = 0;
+    for (int c = 0; c < T.n; ++c) {
+        maxell = std::max(maxell, T.e[c].ell);
+        units += T.e[c].ell;
+    }
+    const int threads = 256;
+    dim3 grid(unsigned(T.n), unsigned((ctx->N / 2 + threads - 1) / threads), unsigned(maxell));
+    ProfScope ps(ctx, K_ELEMWISE, units, st);
+    tensor_kernel<<<grid, threads, 0, st>>>(T, ctx->d_pinfo);
     return cudaGetLastError();
 }
 

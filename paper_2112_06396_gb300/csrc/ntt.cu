@@ -187,7 +187,7 @@ ntt_pass_kernel(const __grid_constant__ MAP map, const PrimeInfo *__restrict__ p
                 // Epilogue operands are read-only for this launch: load a group of
                 // them through the non-coherent path before any store, so the
                 // loads overlap instead of waiting behind each store.
-                const ulonglong2 c = map.cmul()[prime];
+                const ulonglong2 c = io.cmul[prime];
                 const u64 *__restrict__ xp = io.ex;
                 const u64 *__restrict__ ap = io.eadd;
                 u64 *op = io.eout;
@@ -415,15 +415,16 @@ cudaError_t launch_ntt_batch(const ckks_ctx *ctx, const KsBatchDesc &d, int phas
     m.d = d;
     m.phase = phase;
     m.cm = ctx->d_Pinv;
+    m.qlinv = ctx->d_qlinv;
     int count = 0;
     for (int c = 0; c < d.n; ++c) {
         m.d.pre[c] = count;
-        count += phase_count(d, d.ct[c].ell, phase);
+        count += phase_count(d, d.ct[c], phase);
     }
     m.d.pre[d.n] = count;
     if (count == 0) return cudaSuccess;
-    if (phase == PH_INTT_A || phase == PH_INTT_P) return run_inv(m, count, ctx, st);
-    return run_fwd(m, count, phase == PH_NTT_DOWN, ctx, st);
+    if (phase == PH_INTT_A || phase == PH_INTT_P || phase == PH_RS_INTT) return run_inv(m, count, ctx, st);
+    return run_fwd(m, count, phase == PH_NTT_DOWN || phase == PH_RS_NTT, ctx, st);
 }
 
 }  // namespace ckks

@@ -47,6 +47,20 @@ def compulsory_hrotate_bytes(N, ell, k, L, dnum, r) -> int:
     return (2 * ell + r * (key_limbs(ell, k, L, dnum) + 2 * ell)) * limb_bytes(N)
 
 
+def compulsory_batch_keyswitch_bytes(N, levels, keys, k, L, dnum) -> int:
+    """A batch of KeySwitches: every entry's a in and (u, v) out (3 ell limbs),
+    plus every key limb some entry touches, read once (keys[i] names entry i's
+    key; entries with equal names share it)."""
+    touched = set()
+    for ell, key in zip(levels, keys):
+        for j in range(beta_of(ell, L, dnum)):
+            for row in range(2):
+                for t in range(ell + k):
+                    prime = t if t < ell else L + (t - ell)
+                    touched.add((key, j, row, prime))
+    return (3 * sum(levels) + len(touched)) * limb_bytes(N)
+
+
 def ntt_bytes_per_limb(N) -> int:
     """One transform of one limb: read it once, write it once."""
     return 2 * limb_bytes(N)
