@@ -241,6 +241,71 @@ def measure_batched(ctx, ckks, torch, reps=5):
             "hbm_frac_of_measured": comp / (t_batch * 1e-3) / 1e9 / load_peaks()["hbm_gbs"]}
 
 
+def measure_serving(ctx16, ckks, torch, n_req=400, rates=(2000, 4000, 8000, 16000), slo_ms=25.0):
+    """Serving loop: Poisson arrivals of HRotate (r=1) and Mult + relinearisation
+    + Rescale (50/50), N in {2^15, 2^16} (equiprobable), ell uniform in {3..24},
+    dnum=3, one relinearisation and 4 rotation keys resident per ring degree.
+    Continuous batching (up to 64 per batch, 4 streams) against serial
+    launches (batch 1, one stream) at the same offered rates."""
+    from paper_2112_06396_gb300 import serving
+
+    primes = ctx16.q + ctx16.p  # = 1 mod 2^17, hence valid for N = 2^15 too
+    ctx15 = ckks.Context(15, ctx16.q, ctx16.p, DNUM, device=ctx16.device.index)
+    ctxs = [ctx15, ctx16]
+    gs = [5, 25, 125, 625]
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(ctx16.device)
+    keys, cts = [], []
+    for c, cx in enumerate(ctxs):
+        s = dev(synth.ternary(cx.N, f"bench/serve/{c}/s"))
+        keys.append({g: _keygen(cx, torch, s, g, f"bench/serve/{c}/key{g}") for g in [0] + gs})
+        cts.append([dev(synth.uniform_residues(cx.q, cx.N, f"bench/serve/{c}/ct{j}")) for j in range(4)])
+    ops = synth.uniform_ints(n_req, 0, 1, "bench/serve/op")
+    which = synth.uniform_ints(n_req, 0, 1, "bench/serve/ctx")
+    levels = synth.uniform_ints(n_req, 3, 24, "bench/serve/level")
+    outs = [(ctxs[which[i]].empty(levels[i]), ctxs[which[i]].empty(levels[i])) for i in range(n_req)]
+    key_bytes = sum(k.numel() * 8 for kk in keys for k in kk.values())
+    budget = key_bytes + (24 << 30)
+
+    def run(rate, max_batch, streams):
+        srv = ckks.Server(ctxs, budget, max_batch=max_batch, streams=streams)
+        hd = [{g: srv.add_key(c, k) for g, k in keys[c].items()} for c in range(2)]
+        t = np.cumsum(synth.exponential_gaps(n_req, 1e3 / rate, f"bench/serve/gaps/{rate}"))
+        reqs = []
+        for i in range(n_req):
+            c, ell = which[i], levels[i]
+            a, b, a2, b2 = (x[:ell] for x in cts[c])
+            oa, ob = outs[i]
+            if ops[i] == 0:
+                g = gs[i % len(gs)]
+                reqs.append({"t_ms": float(t[i]), "op": "hrotate", "ctx": c, "level": ell, "a": a, "b": b,
+                             "galois": g, "key": hd[c][g], "oa": oa, "ob": ob})
+            else:
+                reqs.append({"t_ms": float(t[i]), "op": "mult", "ctx": c, "level": ell, "a": a, "b": b, "a2": a2,
+                             "b2": b2, "key": hd[c][0], "oa": oa[: ell - 1], "ob": ob[: ell - 1]})
+        _, st = serving.replay(srv, reqs)
+        stats = srv.stats()
+        srv.close()
+        st["batches"] = stats["batches"]
+        return st
+
+    run(4000, 64, 4)  # warm-up (kernel attributes, allocator)
+    table = []
+    for rate in rates:
+        table.append({"offered_per_s": rate, "batched": run(rate, 64, 4), "serial": run(rate, 1, 1)})
+    best = {}
+    for mode in ("batched", "serial"):
+        ok = [r[mode]["ops_per_s"] for r in table if r[mode]["p99_ms"] <= slo_ms]
+        best[mode] = max(ok) if ok else None
+    ctx15.close()
+    del keys, cts, outs
+    torch.cuda.empty_cache()
+    return {"shape": "Poisson arrivals, 50% HRotate(r=1) / 50% Mult+Relin+Rescale, N in {2^15, 2^16}, "
+                     "ell uniform in {3..24}, dnum=3, 5 keys resident per N; batched: up to 64 per batch on 4 "
+                     "streams; serial: one request at a time",
+            "requests_per_run": n_req, "p99_slo_ms": slo_ms, "by_rate": table,
+            "max_ops_per_s_within_slo": best}
+
+
 def measure_other_rows(ctx, ckks, torch, reps=5):
     """Rescale (Alg. 1's ModDown_{B,1}) of one ciphertext, and a CoeffToSlot-shaped
     PtMatVecMult: fftIter = 3 levels at ell = 24, 23, 22 (Alg. 8 with 8 baby x 4
@@ -521,6 +586,7 @@ def run_gpu(args, rank, world, local_rank):
             line["other_rows"] = measure_other_rows(ctx, ckks, torch)
             line["other_rows"]["batched_keyswitch"] = measure_batched(ctx, ckks, torch)
             line["other_rows"]["small_keyswitch"] = measure_small_keyswitch(ckks, torch)
+            line["other_rows"]["serving"] = measure_serving(ctx, ckks, torch)
         if world == 1 and not args.no_cpu_baseline:
             times = oracle_keyswitch_seconds(1)
             line["cpu_baseline"] = {"value": 1.0 / times[0], "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -36,7 +36,8 @@
  *    memory, 16-byte aligned, not shared with concurrently running calls.
  *  - Errors: CKKS_EINVAL for bad arguments (checked on the host before any
  *    launch), CKKS_ECUDA when a launch fails (ckks_last_cuda_error() gives the
- *    cudaError_t).  No call allocates device memory after ckks_ctx_create().
+ *    cudaError_t).  No call allocates device memory after ckks_ctx_create() except
+ *    ckks_server_create().
  */
 #ifndef CKKS_KS_H
 #define CKKS_KS_H
@@ -233,6 +234,63 @@ int ckks_ptmatvecmult(ckks_ctx *ctx, const uint64_t *d_a, const uint64_t *d_b, i
  * a rotation key for Rotate/HRotate with that g.  Workspace CKKS_OP_KEYGEN. */
 int ckks_keygen_ksk(ckks_ctx *ctx, const int64_t *d_s, const int64_t *d_e, const uint64_t *d_a, uint32_t galois,
                     uint64_t *d_key, void *ws, ckks_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Serving loop (no counterpart in the paper; it serves the paper's operations).
+ * A server owns one device arena for request workspace and nstreams CUDA
+ * streams.  Requests (HRotate with one rotation, KeySwitch, or Mult with
+ * relinearisation and Rescale) of any of the server's contexts (ring degrees)
+ * and any level are queued by ckks_server_submit; their ciphertexts are
+ * device buffers owned by the caller, which must keep them unchanged (inputs)
+ * and unread (outputs) until the request is reported finished.
+ * ckks_server_step retires finished batches and, for every free stream, forms
+ * a batch at once (continuous batching): the oldest pending request picks the
+ * context, then pending requests of that context join in arrival order, up to
+ * max_batch, while device memory admits them:
+ *   resident keys + sum over admitted requests (ciphertext bytes in and out +
+ *   workspace) <= mem_budget,
+ * where a key counts once, from ckks_server_add_key on.  A batch runs as one
+ * launch per pipeline step (the batched calls above), so the bits of every
+ * result are those of the single-ciphertext call.  ckks_server_poll returns
+ * finished requests with latency = device completion time - arrival_ms (the
+ * arrival time on the server's clock, ckks_server_now_ms; a negative
+ * arrival_ms means "at submission").  Nothing blocks; the caller calls step
+ * and poll in a loop.  Single-threaded: one thread at a time per server.
+ * ckks_server_create allocates the arena (mem_budget bytes) and is the only
+ * call of this library besides ckks_ctx_create that allocates device memory.
+ * Errors: CKKS_EINVAL for bad arguments, CKKS_ENOMEM when a key or a request
+ * can never fit the budget; after CKKS_ECUDA the server must be destroyed.
+ * ------------------------------------------------------------------------ */
+typedef struct ckks_server ckks_server;
+enum { CKKS_REQ_HROTATE = 1, CKKS_REQ_MULT = 2, CKKS_REQ_KEYSWITCH = 3 };
+typedef struct {
+    int op;                    /* CKKS_REQ_* */
+    int ctx;                   /* index into the server's contexts */
+    int level;                 /* ell of the inputs (>= 2 for Mult) */
+    const uint64_t *a, *b;     /* HRotate: (a, b); KeySwitch: a; Mult: first ciphertext */
+    const uint64_t *a2, *b2;   /* Mult: second ciphertext */
+    uint32_t galois;           /* HRotate: Galois element, odd, < 2N */
+    int key;                   /* handle from ckks_server_add_key (same context) */
+    uint64_t *oa, *ob;         /* outputs: [ell][N], Mult [ell-1][N] */
+    double arrival_ms;         /* on the server's clock; < 0: now */
+} ckks_request;
+typedef struct {
+    int pending, in_flight, finished_unpolled, lanes_busy;
+    size_t mem_budget, mem_keys, mem_in_flight;
+    long long batches, requests_launched;
+    int last_cuda_error;
+} ckks_server_stats_t;
+int ckks_server_create(ckks_ctx *const *ctxs, int nctx, size_t mem_budget, int max_batch, int nstreams,
+                       ckks_server **out);
+int ckks_server_destroy(ckks_server *srv);
+int ckks_server_add_key(ckks_server *srv, int ctx, const uint64_t *d_key, int *handle);
+double ckks_server_now_ms(const ckks_server *srv);
+int ckks_server_submit(ckks_server *srv, const ckks_request *req, uint64_t *id);
+int ckks_server_step(ckks_server *srv, int *n_launched);
+/* Up to max finished requests: ids[i], latency_ms[i] and done_ms[i] (device
+ * completion time on the server's clock; either array may be NULL); *n = count. */
+int ckks_server_poll(ckks_server *srv, int max, uint64_t *ids, double *latency_ms, double *done_ms, int *n);
+int ckks_server_stats(const ckks_server *srv, ckks_server_stats_t *stats);
 
 /* ------------------------------------------------------------------------
  * Measurement hook (no counterpart in the paper).  While enabled, every

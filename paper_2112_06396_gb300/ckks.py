@@ -36,6 +36,20 @@ class _Params(ctypes.Structure):
     _fields_ = [("logN", _i), ("L", _i), ("k", _i), ("dnum", _i), ("q", _u64p), ("p", _u64p)]
 
 
+REQ_HROTATE, REQ_MULT, REQ_KEYSWITCH = 1, 2, 3
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("op", _i), ("ctx", _i), ("level", _i), ("a", _vp), ("b", _vp), ("a2", _vp), ("b2", _vp),
+                ("galois", ctypes.c_uint32), ("key", _i), ("oa", _vp), ("ob", _vp), ("arrival_ms", ctypes.c_double)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("pending", _i), ("in_flight", _i), ("finished_unpolled", _i), ("lanes_busy", _i),
+                ("mem_budget", ctypes.c_size_t), ("mem_keys", ctypes.c_size_t), ("mem_in_flight", ctypes.c_size_t),
+                ("batches", ctypes.c_longlong), ("requests_launched", ctypes.c_longlong), ("last_cuda_error", _i)]
+
+
 _SIGS = {
     "ckks_strerror": (ctypes.c_char_p, [_i]),
     "ckks_gen_primes": (_i, [_i, _i, _i, _u64p]),
@@ -70,6 +84,15 @@ _SIGS = {
                              ctypes.POINTER(_vp), ctypes.POINTER(_i), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                              ctypes.POINTER(_vp), _vp, _vp]),
     "ckks_moddown_noalloc": (_i, [_vp, _vp, _i, _vp, _vp]),
+    "ckks_server_create": (_i, [ctypes.POINTER(_vp), _i, ctypes.c_size_t, _i, _i, ctypes.POINTER(_vp)]),
+    "ckks_server_destroy": (_i, [_vp]),
+    "ckks_server_add_key": (_i, [_vp, _i, _vp, ctypes.POINTER(_i)]),
+    "ckks_server_now_ms": (ctypes.c_double, [_vp]),
+    "ckks_server_submit": (_i, [_vp, ctypes.POINTER(_Request), ctypes.POINTER(ctypes.c_uint64)]),
+    "ckks_server_step": (_i, [_vp, ctypes.POINTER(_i)]),
+    "ckks_server_poll": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double),
+                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i)]),
+    "ckks_server_stats": (_i, [_vp, ctypes.POINTER(_Stats)]),
     "ckks_profile_enable": (_i, [_vp, _i]),
     "ckks_profile_reset": (_i, [_vp]),
     "ckks_profile_read": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
@@ -367,3 +390,94 @@ class Context:
         _check(lib().ckks_keygen_ksk(self._h, _p(s), _p(e), _p(a), galois, _p(key), _p(ws), _stream(stream)),
                self._h)
         return key
+
+
+class Server:
+    """Serving loop of the C ABI (ckks_server_*): continuous batching of
+    HRotate / KeySwitch / Mult requests over several contexts, admitted by
+    device memory.  The tensors of a request are kept referenced here until
+    the request is polled as finished."""
+
+    def __init__(self, contexts, mem_budget, max_batch=64, streams=4):
+        self.contexts = list(contexts)
+        arr = (_vp * len(self.contexts))(*[c._h for c in self.contexts])
+        h = ctypes.c_void_p()
+        _check(lib().ckks_server_create(arr, len(self.contexts), int(mem_budget), int(max_batch), int(streams),
+                                        ctypes.byref(h)))
+        self._h = h
+        self._keys = []
+        self._live = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(lib().ckks_server_destroy(self._h))
+            self._h = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_key(self, ctx, key):
+        hd = _i()
+        _check(lib().ckks_server_add_key(self._h, int(ctx), _p(key), ctypes.byref(hd)))
+        self._keys.append(key)
+        return hd.value
+
+    def now_ms(self):
+        return float(lib().ckks_server_now_ms(self._h))
+
+    def _submit(self, op, ctx, level, a, b, a2, b2, galois, key, oa, ob, arrival_ms):
+        r = _Request(op, int(ctx), int(level), _p(a), _p(b), _p(a2), _p(b2), int(galois), int(key), _p(oa), _p(ob),
+                     float(arrival_ms))
+        rid = ctypes.c_uint64()
+        _check(lib().ckks_server_submit(self._h, ctypes.byref(r), ctypes.byref(rid)))
+        self._live[rid.value] = (a, b, a2, b2, oa, ob)
+        return rid.value
+
+    def submit_hrotate(self, ctx, a, b, level, galois, key, oa, ob, arrival_ms=-1.0):
+        return self._submit(REQ_HROTATE, ctx, level, a, b, None, None, galois, key, oa, ob, arrival_ms)
+
+    def submit_keyswitch(self, ctx, a, level, key, oa, ob, arrival_ms=-1.0):
+        return self._submit(REQ_KEYSWITCH, ctx, level, a, None, None, None, 1, key, oa, ob, arrival_ms)
+
+    def submit_mult(self, ctx, ct1, ct2, level, key, oa, ob, arrival_ms=-1.0):
+        return self._submit(REQ_MULT, ctx, level, ct1[0], ct1[1], ct2[0], ct2[1], 1, key, oa, ob, arrival_ms)
+
+    def step(self):
+        n = _i()
+        _check(lib().ckks_server_step(self._h, ctypes.byref(n)))
+        return n.value
+
+    def poll(self, max_n=4096):
+        ids = (ctypes.c_uint64 * max_n)()
+        lat = (ctypes.c_double * max_n)()
+        done = (ctypes.c_double * max_n)()
+        n = _i()
+        _check(lib().ckks_server_poll(self._h, max_n, ids, lat, done, ctypes.byref(n)))
+        out = []
+        for i in range(n.value):
+            self._live.pop(ids[i], None)
+            out.append((int(ids[i]), float(lat[i]), float(done[i])))
+        return out
+
+    def stats(self):
+        st = _Stats()
+        _check(lib().ckks_server_stats(self._h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in _Stats._fields_}
+
+    def drain(self, sleep_s=0.0):
+        """Step until nothing is pending or in flight; returns the finished requests."""
+        import time
+
+        out = []
+        while True:
+            self.step()
+            out += self.poll()
+            st = self.stats()
+            if st["pending"] == 0 and st["in_flight"] == 0:
+                return out + self.poll()
+            if sleep_s:
+                time.sleep(sleep_s)

@@ -767,21 +767,9 @@ extern "C" int ckks_hrotate(ckks_ctx *ctx, const uint64_t *a, const uint64_t *b,
 }
 
 // ---- batched key switching and Mult
-// One entry of a batch (host side).
-enum { BE_KEYSWITCH = 0, BE_HROTATE = 1, BE_MULT = 2 };
-struct BatchEntry {
-    int kind;
-    const u64 *a, *b;    // KeySwitch: a; HRotate: (a, b); Mult: first ciphertext (a1, b1)
-    const u64 *a2, *b2;  // Mult: second ciphertext
-    const u64 *key;
-    u64 *oa, *ob;
-    int ell;
-    uint32_t galois;
-};
-
 // Per-entry workspace: the HRotate layout of its level, then for Mult entries
 // a3, b3, c3 and the key switch's outputs (a', b') before the Rescale.
-static size_t entry_ws_words(const ckks_ctx *c, int kind, int ell) {
+size_t ckks::entry_ws_words(const ckks_ctx *c, int kind, int ell) {
     return hr_layout(c, ell).total + (kind == BE_MULT ? size_t(5) * ell * c->N : 0);
 }
 
@@ -866,9 +854,9 @@ static int entry_one(ckks_ctx *ctx, const CtDesc &c, const TensorEntry *te, cuda
     return CKKS_OK;
 }
 
-// Runs a batch in groups of kMaxCts entries; the workspace holds every
-// entry's region (entry_ws_words) in batch order.
-static int run_batch(ckks_ctx *ctx, int n, const BatchEntry *e, u64 *w, cudaStream_t st) {
+// Runs a batch in groups of kMaxCts entries.  An entry's workspace is its ws
+// when set, else the next entry_ws_words region of w (batch order).
+int ckks::run_batch(ckks_ctx *ctx, int n, const BatchEntry *e, u64 *w, cudaStream_t st) {
     for (int c0 = 0; c0 < n; c0 += kMaxCts) {
         KsBatchDesc d{};
         d.n = std::min(n - c0, kMaxCts);
@@ -885,12 +873,12 @@ static int run_batch(ckks_ctx *ctx, int n, const BatchEntry *e, u64 *w, cudaStre
             const BatchEntry &x = e[c0 + c];
             te_of[c] = -1;
             TensorEntry te{};
-            d.ct[c] = entry_desc(ctx, x, w, &te);
+            d.ct[c] = entry_desc(ctx, x, x.ws != nullptr ? x.ws : w, &te);
             if (x.kind == BE_MULT) {
                 te_of[c] = T.n;
                 T.e[T.n++] = te;
             }
-            w += entry_ws_words(ctx, x.kind, x.ell);
+            if (x.ws == nullptr) w += entry_ws_words(ctx, x.kind, x.ell);
         }
         if (!ctx->split_bits) {
             for (int c = 0; c < d.n; ++c) RC(entry_one(ctx, d.ct[c], te_of[c] >= 0 ? &T.e[te_of[c]] : nullptr, st));
@@ -927,7 +915,7 @@ extern "C" int ckks_keyswitch_batch(ckks_ctx *ctx, int n, const uint64_t *const 
             return CKKS_EINVAL;
         if (rot && (!al16(b[i]) || galois == nullptr || !galois_ok(ctx, galois[i]))) return CKKS_EINVAL;
         e[i] = BatchEntry{rot ? BE_HROTATE : BE_KEYSWITCH, a[i], rot ? b[i] : nullptr, nullptr, nullptr, keys[i],
-                          oa[i], ob[i], levels[i], rot ? galois[i] : 1u};
+                          oa[i], ob[i], levels[i], rot ? galois[i] : 1u, nullptr};
     }
     return run_batch(ctx, n, e.data(), static_cast<u64 *>(ws), (cudaStream_t)stream);
 }
@@ -944,7 +932,7 @@ extern "C" int ckks_mult_batch(ckks_ctx *ctx, int n, const uint64_t *const *a1, 
         if (!level_ok(ctx, levels[i]) || levels[i] < 2 || !al16(a1[i]) || !al16(b1[i]) || !al16(a2[i]) ||
             !al16(b2[i]) || !al16(keys[i]) || !al16(oa[i]) || !al16(ob[i]))
             return CKKS_EINVAL;
-        e[i] = BatchEntry{BE_MULT, a1[i], b1[i], a2[i], b2[i], keys[i], oa[i], ob[i], levels[i], 1u};
+        e[i] = BatchEntry{BE_MULT, a1[i], b1[i], a2[i], b2[i], keys[i], oa[i], ob[i], levels[i], 1u, nullptr};
     }
     return run_batch(ctx, n, e.data(), static_cast<u64 *>(ws), (cudaStream_t)stream);
 }

@@ -101,6 +101,21 @@ cudaError_t launch_inner_prod(const ckks_ctx *ctx, const InnerArgs &a, cudaStrea
 cudaError_t launch_inner_prod_batch(const ckks_ctx *ctx, const KsBatchDesc &d, cudaStream_t st);
 cudaError_t launch_tensor(const ckks_ctx *ctx, const TensorBatch &T, cudaStream_t st);
 
+// ---- batch executor (abi.cu), shared with the serving loop (serve.cu)
+enum { BE_KEYSWITCH = 0, BE_HROTATE = 1, BE_MULT = 2 };
+struct BatchEntry {
+    int kind;
+    const u64 *a, *b;    // KeySwitch: a; HRotate: (a, b); Mult: first ciphertext (a1, b1)
+    const u64 *a2, *b2;  // Mult: second ciphertext
+    const u64 *key;
+    u64 *oa, *ob;        // outputs: [ell][N], Mult [ell-1][N]
+    int ell;
+    uint32_t galois;     // HRotate
+    u64 *ws;             // this entry's workspace (entry_ws_words), or null: packed
+};
+size_t entry_ws_words(const ckks_ctx *c, int kind, int ell);
+int run_batch(ckks_ctx *ctx, int n, const BatchEntry *e, u64 *w, cudaStream_t st);
+
 struct PmvArgs {
     const u64 *ext;      // hoisted ModUp outputs [beta][ell+k][N]
     const u64 *a, *b;    // input ciphertext [ell][N]

@@ -129,3 +129,10 @@ def uniform_ints(n: int, lo: int, hi: int, name: str, master: int = MASTER_SEED)
     shift = np.uint64(64 - bits)
     v = _accept(seed, n, lambda d: d >> shift, lambda x: x < np.uint64(span))
     return [int(x) + lo for x in v]
+
+
+def exponential_gaps(n: int, mean: float, name: str, master: int = MASTER_SEED) -> np.ndarray:
+    """n exponential inter-arrival gaps with the given mean (Poisson arrivals)."""
+    d = splitmix64(stream_seed(name, 0, master), n)
+    u = (d >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
+    return -np.log1p(-u) * mean
