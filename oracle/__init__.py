@@ -83,6 +83,8 @@ def _load():
                 "or_keyswitch": (ctypes.c_int, [P, ctypes.c_int, u64p, u64p, u64p, u64p]),
                 "or_rotate": (ctypes.c_int, [P, ctypes.c_int, u64p, u64p, ctypes.c_uint64, u64p, u64p, u64p]),
                 "or_mult": (ctypes.c_int, [P, ctypes.c_int, u64p, u64p, u64p, u64p, u64p, u64p, u64p]),
+                "or_newmult": (ctypes.c_int, [P, ctypes.c_int, u64p, u64p, u64p, u64p, u64p, u64p, u64p]),
+                "or_moddown_merged": (ctypes.c_int, [P, ctypes.c_int, u64p, u64p]),
                 "or_hrotate": (ctypes.c_int, [P, ctypes.c_int, u64p, u64p, ctypes.c_int, u64p,
                                               ctypes.POINTER(u64p), ctypes.POINTER(u64p), ctypes.POINTER(u64p)]),
                 "or_ptmatvec": (ctypes.c_int, [P, ctypes.c_int, u64p, u64p, ctypes.c_int, ctypes.c_int,
@@ -272,6 +274,25 @@ def mult(P: Params, ell, a1, b1, a2, b2, key):
     if _load().or_mult(P.c, ell, *[_u(x) for x in c], _u(oa), _u(ob)) != 0:
         raise ValueError("mult needs ell >= 2")
     return oa, ob
+
+
+def newmult(P: Params, ell, a1, b1, a2, b2, key):
+    """Algorithm 7 (NewMult): merged ModDown by P*q_{ell-1}; outputs at level ell-1."""
+    c = [np.ascontiguousarray(x, dtype=np.uint64) for x in (a1, b1, a2, b2, key)]
+    oa = np.zeros((ell - 1, P.N), dtype=np.uint64)
+    ob = np.zeros_like(oa)
+    if _load().or_newmult(P.c, ell, *[_u(x) for x in c], _u(oa), _u(ob)) != 0:
+        raise ValueError("newmult needs ell >= 2")
+    return oa, ob
+
+
+def moddown_merged(P: Params, ell, x):
+    """ModDown by P*q_{ell-1} of an [ell+k][N] polynomial: [ell-1][N]."""
+    x = np.ascontiguousarray(x, dtype=np.uint64)
+    out = np.zeros((ell - 1, P.N), dtype=np.uint64)
+    if _load().or_moddown_merged(P.c, ell, _u(x), _u(out)) != 0:
+        raise ValueError("moddown_merged needs ell >= 2")
+    return out
 
 
 def rotate(P: Params, ell, a, b, g, key):

@@ -386,6 +386,73 @@ int or_moddown(const or_params *P, int ell, const u64 *in, u64 *out) {
 }
 
 /* ------------------------------------------------------------------ */
+/* ModDown and Rescale merged (Sec. 5.1, NewMult): one fast basis       */
+/* conversion dividing by D = P * q_{ell-1}                             */
+/* ------------------------------------------------------------------ */
+
+/* The dropped basis D: p_0..p_{k-1}, then q_{ell-1}. */
+static u64 D_prime(const or_params *P, int ell, int m) { return m < P->k ? P->primes[P->L + m] : P->primes[ell - 1]; }
+static u64 D_mod(const or_params *P, int ell, u64 m) {
+    u64 r = 1 % m;
+    for (int i = 0; i <= P->k; i++) r = mulmod(r, D_prime(P, ell, i) % m, m);
+    return r;
+}
+/* [floor(D/2)]_m = (D - 1)/2 mod m (D is odd). */
+static u64 halfD_mod(const or_params *P, int ell, u64 m) {
+    return mulmod(submod(D_mod(P, ell, m), 1, m), invmod(2 % m, m), m);
+}
+
+/* in: [ell+k][N] evaluation form over C_ell U P; out: [ell-1][N] evaluation
+ * form over C_{ell-1}, out ~= round(in / (P q_{ell-1})) up to the fast
+ * conversion error.  Steps: (1) iNTT the k+1 limbs of D; (2) add
+ * [floor(D/2)]; (3) times [(D/d_m)^-1]_{d_m}; (4) z_i = sum_m y_m [D/d_m]_{q_i}
+ * - [floor(D/2)]_{q_i} for i < ell-1 (coefficient form); (5) NTT;
+ * (6) out_i = (in_i - z_hat_i) [D^-1]_{q_i}.  Needs ell >= 2. */
+int or_moddown_merged(const or_params *P, int ell, const u64 *in, u64 *out) {
+    if (ell < 2) return -1;
+    size_t N = N_of(P);
+    int nd = P->k + 1;
+    u64 *x = (u64 *)malloc(sizeof(u64) * nd * N);
+    for (int m = 0; m < nd; m++) {
+        u64 dm = D_prime(P, ell, m);
+        const u64 *src = in + (size_t)(m < P->k ? ell + m : ell - 1) * N;
+        memcpy(x + m * N, src, sizeof(u64) * N);
+        or_intt(x + m * N, P->logN, dm);
+        u64 H = halfD_mod(P, ell, dm);
+        u64 dhat = 1;
+        for (int m2 = 0; m2 < nd; m2++)
+            if (m2 != m) dhat = mulmod(dhat, D_prime(P, ell, m2) % dm, dm);
+        u64 c = invmod(dhat, dm);
+        for (size_t n = 0; n < N; n++) x[m * N + n] = mulmod(addmod(x[m * N + n], H, dm), c, dm);
+    }
+    u64 *w = (u64 *)malloc(sizeof(u64) * N);
+    for (int i = 0; i < ell - 1; i++) {
+        u64 qi = P->primes[i];
+        u64 *cst = (u64 *)malloc(sizeof(u64) * nd);
+        for (int m = 0; m < nd; m++) {
+            u64 dhat = 1;
+            for (int m2 = 0; m2 < nd; m2++)
+                if (m2 != m) dhat = mulmod(dhat, D_prime(P, ell, m2) % qi, qi);
+            cst[m] = dhat;
+        }
+        u64 H = halfD_mod(P, ell, qi);
+        for (size_t n = 0; n < N; n++) {
+            u64 acc = 0;
+            for (int m = 0; m < nd; m++) acc = addmod(acc, mulmod(x[m * N + n] % qi, cst[m], qi), qi);
+            w[n] = submod(acc, H, qi);
+        }
+        free(cst);
+        or_ntt(w, P->logN, qi);
+        u64 Dinv = invmod(D_mod(P, ell, qi), qi);
+        for (size_t n = 0; n < N; n++)
+            out[(size_t)i * N + n] = mulmod(submod(in[(size_t)i * N + n], w[n], qi), Dinv, qi);
+    }
+    free(w);
+    free(x);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
 /* Rescale = ModDown_{B,1} (Algorithm 1): exact rounded division by     */
 /* the last limb q_{ell-1}                                             */
 /* ------------------------------------------------------------------ */
@@ -476,6 +543,49 @@ int or_mult(const or_params *P, int ell, const u64 *a1, const u64 *b1, const u64
     or_rescale(P, ell, u, oa);
     or_rescale(P, ell, v, ob);
     free(a3); free(b3); free(c3); free(u); free(v);
+    return 0;
+}
+
+/* Algorithm 7 (NewMult, Sec. 5.1): the tensor step of Algorithm 2; ModUp of
+ * the digits of a3 and KSKInnerProd with the key for s^2 give (u_hat, v_hat)
+ * over C_ell U P; PModUp lifts b3 and c3 to the same basis and they are added
+ * before any ModDown, so the ModDown by P and the Rescale by q_{ell-1} of
+ * Algorithm 2 become one merged ModDown per polynomial.  Outputs at level
+ * ell-1.  Needs ell >= 2. */
+int or_newmult(const or_params *P, int ell, const u64 *a1, const u64 *b1, const u64 *a2, const u64 *b2,
+               const u64 *key, u64 *oa, u64 *ob) {
+    if (ell < 2) return -1;
+    size_t N = N_of(P), sz = (size_t)ell * N;
+    int beta = p_beta(P, ell), ext = ell + P->k;
+    u64 *a3 = (u64 *)malloc(sizeof(u64) * sz), *b3 = (u64 *)malloc(sizeof(u64) * sz);
+    u64 *c3 = (u64 *)malloc(sizeof(u64) * sz);
+    for (int i = 0; i < ell; i++) {
+        u64 q = P->primes[i];
+        for (size_t n = 0; n < N; n++) {
+            size_t o = (size_t)i * N + n;
+            a3[o] = mulmod(a1[o], a2[o], q);
+            b3[o] = addmod(mulmod(a1[o], b2[o], q), mulmod(a2[o], b1[o], q), q);
+            c3[o] = mulmod(b1[o], b2[o], q);
+        }
+    }
+    u64 *digits = (u64 *)malloc(sizeof(u64) * beta * ext * N);
+    for (int j = 0; j < beta; j++) or_modup(P, ell, j, a3, digits + (size_t)j * ext * N);
+    u64 *uh = (u64 *)malloc(sizeof(u64) * ext * N), *vh = (u64 *)malloc(sizeof(u64) * ext * N);
+    or_ksk_inner_prod(P, ell, digits, key, uh, vh);
+    u64 *bh = (u64 *)malloc(sizeof(u64) * ext * N), *ch = (u64 *)malloc(sizeof(u64) * ext * N);
+    or_pmodup(P, ell, b3, bh);
+    or_pmodup(P, ell, c3, ch);
+    for (int t = 0; t < ext; t++) {
+        u64 pt = prime_at(P, ell, t);
+        for (size_t n = 0; n < N; n++) {
+            size_t o = (size_t)t * N + n;
+            uh[o] = addmod(uh[o], bh[o], pt);
+            vh[o] = addmod(vh[o], ch[o], pt);
+        }
+    }
+    or_moddown_merged(P, ell, uh, oa);
+    or_moddown_merged(P, ell, vh, ob);
+    free(a3); free(b3); free(c3); free(digits); free(uh); free(vh); free(bh); free(ch);
     return 0;
 }
 

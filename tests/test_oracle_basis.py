@@ -61,6 +61,30 @@ def test_moddown_crt(oracle_lib, L, k, dnum, ell):
         assert 0 <= eps < P.k
 
 
+@pytest.mark.parametrize("L,k,dnum,ell", [(6, 3, 2, 6), (6, 3, 2, 2), (7, 3, 3, 4)])
+def test_moddown_merged_crt(oracle_lib, L, k, dnum, ell):
+    """The merged ModDown of NewMult divides by D = P * q_{ell-1}: per
+    coefficient, out = round(X / D) - eps (mod Q_{ell-1}) with eps in [0, k+1)
+    (the fast conversion over the k+1 limbs of D), X the CRT value of the
+    input over C_ell U P."""
+    P = make_params(oracle_lib, L=L, k=k, dnum=dnum)
+    ext = P.ext_primes(ell)
+    x = synth.uniform_residues(ext, P.N, "pin/mdmerged/x")
+    out = oracle_lib.moddown_merged(P, ell, x)
+    assert out.shape == (ell - 1, P.N)
+    X = crt_columns(oracle_lib.ntt_limbs(P, ell, x, inverse=True), ext)
+    qs = [int(v) for v in P.primes[:ell]]
+    D = prod(int(v) for v in P.primes[P.L:]) * qs[-1]
+    Qd = prod(qs[:-1])
+    Y = crt_columns(np.stack([oracle_lib.intt(out[i], P.logN, qs[i]) for i in range(ell - 1)]), qs[:-1])
+    seen = set()
+    for xv, yv in zip(X, Y):
+        eps = ((xv + D // 2) // D - yv) % Qd
+        assert 0 <= eps <= P.k
+        seen.add(eps)
+    assert len(seen) > 1  # the conversion error really occurs (not a vacuous bound)
+
+
 @pytest.mark.parametrize("ell", [2, 3, 6])
 def test_rescale_exact(oracle_lib, ell):
     P = make_params(oracle_lib)

@@ -196,3 +196,38 @@ def test_mult_decrypts_to_rescaled_product(oracle_lib, logN, L, k, dnum, ell):
     oa2, ob2 = oracle_lib.mult(P, ell, a2, b2, a1, b1, rlk)
     np.testing.assert_array_equal(oa, oa2)
     np.testing.assert_array_equal(ob, ob2)
+
+
+@pytest.mark.parametrize("logN,L,k,dnum,ell", [(6, 6, 3, 2, 6), (6, 7, 3, 3, 4), (6, 6, 3, 2, 2)])
+def test_newmult_decrypts_to_rescaled_product(oracle_lib, logN, L, k, dnum, ell):
+    """Algorithm 7: the lifted sum P*(m1*m2) + E is divided by P*q_{ell-1} in one
+    merged ModDown, so |Dec(out) - m1*m2 / q_{ell-1}| <= E/(P q_{ell-1}) +
+    (h_s + 1)/2 + (k + 1)(h_s + 1) + 1 (rounding of both polynomials, the fast
+    conversion error over k+1 limbs), E the ModUp / inner-product noise."""
+    P = params(oracle_lib, logN, L, k, dnum)
+    s = synth.ternary(P.N, "pin/newmult/s")
+    rlk = make_key(oracle_lib, P, s, oracle_lib.sq_secret(P, s), "pin/newmult/rlk")
+    ql = int(P.primes[ell - 1])
+    delta = 1 << (ql.bit_length() // 2 + 4)
+    cts, ms = [], []
+    for i in range(2):
+        x = synth.small_uniform(P.N, f"pin/newmult/x{i}", 8)
+        m = delta * x + synth.gaussian(P.N, f"pin/newmult/e{i}")
+        a = synth.uniform_residues(P.primes[:ell], P.N, f"pin/newmult/a{i}")
+        cts.append((a, oracle_lib.encrypt(P, ell, s, m, a)))
+        ms.append([int(v) for v in m])
+    (a1, b1), (a2, b2) = cts
+    oa, ob = oracle_lib.newmult(P, ell, a1, b1, a2, b2, rlk)
+    got = decrypt_int(oracle_lib, P, ell - 1, s, oa, ob)
+    prod_m = negacyclic_mul(ms[0], ms[1])
+    hs = int(np.count_nonzero(s))
+    alpha, beta = P.alpha, P.beta(ell)
+    Pp = prod(int(x) for x in P.primes[P.L:])
+    qmax = max(prod(int(x) for x in P.primes[j * alpha:min((j + 1) * alpha, ell)]) for j in range(beta))
+    bound = beta * alpha * P.N * 19 * qmax / (Pp * ql) + (hs + 1) / 2 + (P.k + 1) * (hs + 1) + 1
+    err = max(abs(g * ql - t) for g, t in zip(got, prod_m)) / ql
+    assert err <= bound
+    assert max(abs(t) for t in prod_m) / ql > 100 * bound
+    # the same product as Algorithm 2 up to the two methods' error terms, but other bits
+    ra, rb = oracle_lib.mult(P, ell, a1, b1, a2, b2, rlk)
+    assert not (np.array_equal(ra, oa) and np.array_equal(rb, ob))
