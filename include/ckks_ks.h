@@ -70,7 +70,8 @@ enum {
     CKKS_OP_RESCALE = 6,
     CKKS_OP_PTMATVEC = 7,
     CKKS_OP_KEYGEN = 8,
-    CKKS_OP_MULT = 9
+    CKKS_OP_MULT = 9,
+    CKKS_OP_NEWMULT = 10
 };
 
 typedef struct {
@@ -212,6 +213,25 @@ int ckks_mult_batch(ckks_ctx *ctx, int n, const uint64_t *const *d_a1, const uin
                     const uint64_t *const *d_keys, uint64_t *const *d_oa, uint64_t *const *d_ob, void *ws,
                     ckks_stream_t stream);
 
+/* NewMult (Algorithm 7, Sec. 5.1): the product of ckks_mult with its two
+ * ModDowns merged.  The tensor step and the ModUp / KSKInnerProd of a3 are
+ * those of Algorithm 2; PModUp(b3) and PModUp(c3) (P times the polynomial on
+ * the chain limbs, 0 on the P-limbs) are added to (u_hat, v_hat) inside the
+ * inner product, and one ModDown by D = P*q_{ell-1} per polynomial (fast basis
+ * conversion from the k P-limbs and q_{ell-1} to q_0..q_{ell-2}, rounding by
+ * adding floor(D/2), then (x - conv) * D^-1) gives the outputs at level
+ * ell-1.  Same message as ckks_mult within the error bounds, different bits.
+ * Workspace CKKS_OP_NEWMULT; batched form as ckks_mult_batch.  Needs
+ * k + 1 <= 32 (CKKS_EUNSUPPORTED otherwise). */
+int ckks_newmult(ckks_ctx *ctx, const uint64_t *d_a1, const uint64_t *d_b1, const uint64_t *d_a2,
+                 const uint64_t *d_b2, int level, const uint64_t *d_key, uint64_t *d_oa, uint64_t *d_ob, void *ws,
+                 ckks_stream_t stream);
+int ckks_newmult_batch_workspace_bytes(const ckks_ctx *ctx, int n, const int *levels, size_t *bytes);
+int ckks_newmult_batch(ckks_ctx *ctx, int n, const uint64_t *const *d_a1, const uint64_t *const *d_b1,
+                       const uint64_t *const *d_a2, const uint64_t *const *d_b2, const int *levels,
+                       const uint64_t *const *d_keys, uint64_t *const *d_oa, uint64_t *const *d_ob, void *ws,
+                       ckks_stream_t stream);
+
 /* PtMatVecMult with hoisted ModUp and ModDown (Algorithm 8) in baby-step /
  * giant-step form (Sec. 5.2): nb baby steps, ng giant steps, diagonal (t, i) =
  * d_diag[t*nb + i], an [ell+k][N] evaluation-form plaintext over the extended
@@ -262,16 +282,16 @@ int ckks_keygen_ksk(ckks_ctx *ctx, const int64_t *d_s, const int64_t *d_e, const
  * can never fit the budget; after CKKS_ECUDA the server must be destroyed.
  * ------------------------------------------------------------------------ */
 typedef struct ckks_server ckks_server;
-enum { CKKS_REQ_HROTATE = 1, CKKS_REQ_MULT = 2, CKKS_REQ_KEYSWITCH = 3 };
+enum { CKKS_REQ_HROTATE = 1, CKKS_REQ_MULT = 2, CKKS_REQ_KEYSWITCH = 3, CKKS_REQ_NEWMULT = 4 };
 typedef struct {
     int op;                    /* CKKS_REQ_* */
     int ctx;                   /* index into the server's contexts */
-    int level;                 /* ell of the inputs (>= 2 for Mult) */
-    const uint64_t *a, *b;     /* HRotate: (a, b); KeySwitch: a; Mult: first ciphertext */
-    const uint64_t *a2, *b2;   /* Mult: second ciphertext */
+    int level;                 /* ell of the inputs (>= 2 for Mult / NewMult) */
+    const uint64_t *a, *b;     /* HRotate: (a, b); KeySwitch: a; (New)Mult: first ciphertext */
+    const uint64_t *a2, *b2;   /* (New)Mult: second ciphertext */
     uint32_t galois;           /* HRotate: Galois element, odd, < 2N */
     int key;                   /* handle from ckks_server_add_key (same context) */
-    uint64_t *oa, *ob;         /* outputs: [ell][N], Mult [ell-1][N] */
+    uint64_t *oa, *ob;         /* outputs: [ell][N], (New)Mult [ell-1][N] */
     double arrival_ms;         /* on the server's clock; < 0: now */
 } ckks_request;
 typedef struct {

@@ -25,7 +25,8 @@ _i = ctypes.c_int
 _lib = None
 
 CKKS_OK, CKKS_EINVAL, CKKS_ENOMEM, CKKS_ECUDA, CKKS_EUNSUPPORTED = 0, 1, 2, 3, 4
-OP_MODUP, OP_MODDOWN, OP_KEYSWITCH, OP_ROTATE, OP_HROTATE, OP_RESCALE, OP_PTMATVEC, OP_KEYGEN, OP_MULT = range(1, 10)
+(OP_MODUP, OP_MODDOWN, OP_KEYSWITCH, OP_ROTATE, OP_HROTATE, OP_RESCALE, OP_PTMATVEC, OP_KEYGEN, OP_MULT,
+ OP_NEWMULT) = range(1, 11)
 
 
 class CkksError(RuntimeError):
@@ -36,7 +37,7 @@ class _Params(ctypes.Structure):
     _fields_ = [("logN", _i), ("L", _i), ("k", _i), ("dnum", _i), ("q", _u64p), ("p", _u64p)]
 
 
-REQ_HROTATE, REQ_MULT, REQ_KEYSWITCH = 1, 2, 3
+REQ_HROTATE, REQ_MULT, REQ_KEYSWITCH, REQ_NEWMULT = 1, 2, 3, 4
 
 
 class _Request(ctypes.Structure):
@@ -80,6 +81,11 @@ _SIGS = {
                                   ctypes.POINTER(_vp), _vp, _vp]),
     "ckks_mult": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _vp, _vp, _vp, _vp, _vp]),
     "ckks_mult_batch_workspace_bytes": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_size_t)]),
+    "ckks_newmult": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _vp, _vp, _vp, _vp, _vp]),
+    "ckks_newmult_batch_workspace_bytes": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_size_t)]),
+    "ckks_newmult_batch": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                ctypes.POINTER(_vp), ctypes.POINTER(_i), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                ctypes.POINTER(_vp), _vp, _vp]),
     "ckks_mult_batch": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                              ctypes.POINTER(_vp), ctypes.POINTER(_i), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                              ctypes.POINTER(_vp), _vp, _vp]),
@@ -336,35 +342,41 @@ class Context:
         _check(lib().ckks_keyswitch_batch(self._h, n, ap, bp, lv, gp, kp, oa, ob, _p(ws), _stream(stream)), self._h)
         return outs
 
-    def mult(self, a1, b1, a2, b2, level, key, oa=None, ob=None, ws=None, stream=None):
-        """Algorithm 2: Mult + relinearisation + Rescale; outputs at level-1."""
+    def mult(self, a1, b1, a2, b2, level, key, oa=None, ob=None, ws=None, stream=None, new=False):
+        """Algorithm 2 (Mult + relinearisation + Rescale), or Algorithm 7 (NewMult)
+        with new=True; outputs at level-1."""
         oa = self.empty(level - 1) if oa is None else oa
         ob = self.empty(level - 1) if ob is None else ob
-        ws = self.workspace(OP_MULT, level) if ws is None else ws
-        _check(lib().ckks_mult(self._h, _p(a1), _p(b1), _p(a2), _p(b2), level, _p(key), _p(oa), _p(ob), _p(ws),
-                               _stream(stream)), self._h)
+        ws = self.workspace(OP_NEWMULT if new else OP_MULT, level) if ws is None else ws
+        fn = lib().ckks_newmult if new else lib().ckks_mult
+        _check(fn(self._h, _p(a1), _p(b1), _p(a2), _p(b2), level, _p(key), _p(oa), _p(ob), _p(ws), _stream(stream)),
+               self._h)
         return oa, ob
 
-    def mult_batch_workspace(self, levels):
+    def newmult(self, a1, b1, a2, b2, level, key, oa=None, ob=None, ws=None, stream=None):
+        return self.mult(a1, b1, a2, b2, level, key, oa, ob, ws, stream, new=True)
+
+    def mult_batch_workspace(self, levels, new=False):
         n = len(levels)
         lv = (_i * max(n, 1))(*[int(x) for x in levels])
         nbytes = ctypes.c_size_t()
-        _check(lib().ckks_mult_batch_workspace_bytes(self._h, n, lv, ctypes.byref(nbytes)))
+        fn = lib().ckks_newmult_batch_workspace_bytes if new else lib().ckks_mult_batch_workspace_bytes
+        _check(fn(self._h, n, lv, ctypes.byref(nbytes)))
         return torch.empty(max(nbytes.value // 8, 2), dtype=torch.uint64, device=self.device)
 
-    def mult_batch(self, cts1, cts2, levels, keys, outs=None, ws=None, stream=None):
+    def mult_batch(self, cts1, cts2, levels, keys, outs=None, ws=None, stream=None, new=False):
         """cts1, cts2: lists of (a, b); returns [(oa, ob)] at level-1 each."""
         n = len(cts1)
         if outs is None:
             outs = [(self.empty(levels[i] - 1), self.empty(levels[i] - 1)) for i in range(n)]
-        ws = self.mult_batch_workspace(levels) if ws is None else ws
+        ws = self.mult_batch_workspace(levels, new) if ws is None else ws
         m = max(n, 1)
         arr = lambda xs: (_vp * m)(*[x.data_ptr() for x in xs])
         lv = (_i * m)(*[int(x) for x in levels])
-        _check(lib().ckks_mult_batch(self._h, n, arr([c[0] for c in cts1]), arr([c[1] for c in cts1]),
-                                     arr([c[0] for c in cts2]), arr([c[1] for c in cts2]), lv, arr(keys),
-                                     arr([o[0] for o in outs]), arr([o[1] for o in outs]), _p(ws), _stream(stream)),
-               self._h)
+        fn = lib().ckks_newmult_batch if new else lib().ckks_mult_batch
+        _check(fn(self._h, n, arr([c[0] for c in cts1]), arr([c[1] for c in cts1]), arr([c[0] for c in cts2]),
+                  arr([c[1] for c in cts2]), lv, arr(keys), arr([o[0] for o in outs]), arr([o[1] for o in outs]),
+                  _p(ws), _stream(stream)), self._h)
         return outs
 
     def ptmatvecmult(self, a, b, level, nb, ng, g_baby, g_giant, key_baby, key_giant, diags, rescale=True,
@@ -443,8 +455,9 @@ class Server:
     def submit_keyswitch(self, ctx, a, level, key, oa, ob, arrival_ms=-1.0):
         return self._submit(REQ_KEYSWITCH, ctx, level, a, None, None, None, 1, key, oa, ob, arrival_ms)
 
-    def submit_mult(self, ctx, ct1, ct2, level, key, oa, ob, arrival_ms=-1.0):
-        return self._submit(REQ_MULT, ctx, level, ct1[0], ct1[1], ct2[0], ct2[1], 1, key, oa, ob, arrival_ms)
+    def submit_mult(self, ctx, ct1, ct2, level, key, oa, ob, arrival_ms=-1.0, new=False):
+        return self._submit(REQ_NEWMULT if new else REQ_MULT, ctx, level, ct1[0], ct1[1], ct2[0], ct2[1], 1, key, oa,
+                            ob, arrival_ms)
 
     def step(self):
         n = _i()

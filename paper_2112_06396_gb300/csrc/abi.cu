@@ -252,6 +252,37 @@ extern "C" int ckks_ctx_create(const ckks_params *prm, int device, ckks_ctx **ou
             }
         }
     }
+    // merged ModDown of NewMult: D = P * q_{ell-1} (sources p_0..p_{k-1} and
+    // q_{ell-1}) -> q_0..q_{ell-2}, rounding constant floor(D/2) = (D-1)/2
+    std::vector<BConvPlan> mdrs(L + 1);
+    for (auto &pl : mdrs) fill_plan(pl);
+    auto D_mod = [&](int ell, u64 m) { return hmul(prod_mod(L, L + k, -1, m), primes[ell - 1] % m, m); };
+    auto halfD = [&](int ell, u64 m) { return hmul((D_mod(ell, m) + m - 1) % m, hinv(2, m), m); };
+    auto Dhat_mod = [&](int ell, int src, u64 m) {  // (D / d_src) mod m; src k is q_{ell-1}
+        if (src == k) return prod_mod(L, L + k, -1, m);
+        return hmul(prod_mod(L, L + k, L + src, m), primes[ell - 1] % m, m);
+    };
+    if (k + 1 <= kMaxSrc) {
+        for (int ell = 2; ell <= L; ++ell) {
+            BConvPlan &pl = mdrs[ell];
+            pl.n_src = k + 1;
+            for (int m = 0; m <= k; ++m) {
+                const int pe = m < k ? L + m : ell - 1;
+                const u64 dm = primes[pe];
+                pl.src_prime[m] = uint16_t(pe);
+                pl.src_add[m] = halfD(ell, dm);
+                pl.src_mul[m] = hinv(Dhat_mod(ell, m, dm), dm);
+                pl.src_mul_s[m] = shoup_of(pl.src_mul[m], dm);
+            }
+            pl.n_dst = ell - 1;
+            for (int t = 0; t < ell - 1; ++t) {
+                pl.dst_pos[t] = uint16_t(t);
+                pl.dst_prime[t] = uint16_t(t);
+                pl.dst_sub[t] = halfD(ell, primes[t]);
+                for (int m = 0; m <= k; ++m) pl.mat[t][m] = Dhat_mod(ell, m, primes[t]);
+            }
+        }
+    }
     // split form of every plan's matrix for the 32-bit multiply-add basis conversion
     if (c->split_bits) {
         const int W = c->split_bits;
@@ -270,6 +301,7 @@ extern "C" int ckks_ctx_create(const ckks_params *prm, int device, ckks_ctx **ou
         for (auto &pl : modup) split(pl);
         for (auto &pl : mdown) split(pl);
         for (auto &pl : resc) split(pl);
+        for (auto &pl : mdrs) split(pl);
     }
     std::vector<ulonglong2> Pinv(LK), Pmod(LK), qlinv(size_t(L + 1) * LK);
     for (int i = 0; i < LK; ++i) {
@@ -279,10 +311,13 @@ extern "C" int ckks_ctx_create(const ckks_params *prm, int device, ckks_ctx **ou
         const u64 pinv = pm == 0 ? 0 : hinv(pm, q);
         Pinv[i] = make_ulonglong2(pinv, shoup_of(pinv, q));
     }
+    std::vector<ulonglong2> Dinv(size_t(L + 1) * LK);
     for (int ell = 2; ell <= L; ++ell)
         for (int i = 0; i < ell - 1; ++i) {
             const u64 q = primes[i], v = hinv(primes[ell - 1] % q, q);
             qlinv[size_t(ell) * LK + i] = make_ulonglong2(v, shoup_of(v, q));
+            const u64 dv = hinv(D_mod(ell, q), q);
+            Dinv[size_t(ell) * LK + i] = make_ulonglong2(dv, shoup_of(dv, q));
         }
 
     // ---- one device allocation
@@ -301,6 +336,8 @@ extern "C" int ckks_ctx_create(const ckks_params *prm, int device, ckks_ctx **ou
     const size_t o_pinv = take(sizeof(ulonglong2) * LK);
     const size_t o_pmod = take(sizeof(ulonglong2) * LK);
     const size_t o_qlinv = take(sizeof(ulonglong2) * qlinv.size());
+    const size_t o_mdrs = take(sizeof(BConvPlan) * mdrs.size());
+    const size_t o_dinv = take(sizeof(ulonglong2) * Dinv.size());
     int prev = 0;
     cudaGetDevice(&prev);
     cudaError_t err = cudaSetDevice(device);
@@ -321,6 +358,8 @@ extern "C" int ckks_ctx_create(const ckks_params *prm, int device, ckks_ctx **ou
     c->d_Pinv = reinterpret_cast<ulonglong2 *>(base + o_pinv);
     c->d_Pmod = reinterpret_cast<ulonglong2 *>(base + o_pmod);
     c->d_qlinv = reinterpret_cast<ulonglong2 *>(base + o_qlinv);
+    c->d_mdmerged = reinterpret_cast<BConvPlan *>(base + o_mdrs);
+    c->d_Dinv = reinterpret_cast<ulonglong2 *>(base + o_dinv);
     struct Up {
         void *dst;
         const void *src;
@@ -333,7 +372,9 @@ extern "C" int ckks_ctx_create(const ckks_params *prm, int device, ckks_ctx **ou
                {c->d_rescale, resc.data(), sizeof(BConvPlan) * resc.size()},
                {c->d_Pinv, Pinv.data(), sizeof(ulonglong2) * LK},
                {c->d_Pmod, Pmod.data(), sizeof(ulonglong2) * LK},
-               {c->d_qlinv, qlinv.data(), sizeof(ulonglong2) * qlinv.size()}};
+               {c->d_qlinv, qlinv.data(), sizeof(ulonglong2) * qlinv.size()},
+               {c->d_mdmerged, mdrs.data(), sizeof(BConvPlan) * mdrs.size()},
+               {c->d_Dinv, Dinv.data(), sizeof(ulonglong2) * Dinv.size()}};
     for (auto &u : ups)
         if (err == cudaSuccess) err = cudaMemcpy(u.dst, u.src, u.n, cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = ntt_set_attributes(c);
@@ -541,6 +582,56 @@ static int rescale_polys(ckks_ctx *ctx, int ell, int npolys, const u64 *const in
     return CKKS_OK;
 }
 
+// The merged ModDown of NewMult (Algorithm 7) over npolys extended polynomials
+// in[p] ([ell+k][N]) to out[p] ([ell-1][N]): iNTT of the k P-limbs and of the
+// q_{ell-1} limb -> basis conversion from D = P*q_{ell-1} to q_0..q_{ell-2}
+// with rounding -> NTT with the (x - w) * D^-1 epilogue.
+// Scratch: pcoeff [npolys*(k+1)][N], w [npolys*(ell-1)][N].
+static int moddown_merged_polys(ckks_ctx *ctx, int ell, int npolys, const u64 *const in[2], u64 *const out[2],
+                                u64 *pcoeff, u64 *w, cudaStream_t st) {
+    const size_t N = ctx->N;
+    const int k = ctx->k, ns = k + 1, nd = ell - 1;
+    LimbList inv;  // prime-major: both polynomials' limbs of one prime are adjacent
+    for (int m = 0; m < ns; ++m)
+        for (int p = 0; p < npolys; ++p) {
+            const int pos = m < k ? ell + m : ell - 1;
+            inv.add(in[p] + size_t(pos) * N, pcoeff + size_t(p * ns + m) * N, m < k ? ctx->L + m : ell - 1);
+        }
+    RC(run_ntt(ctx, inv, true, st));
+    BConvLaunch l{};
+    l.ngroups = npolys;
+    l.chunk = nd;
+    l.chunks = 1;
+    for (int p = 0; p < npolys; ++p) {
+        l.g[p].plan = ctx->d_mdmerged + ell;
+        l.g[p].src = pcoeff + size_t(p) * ns * N;
+        l.g[p].dst = w + size_t(p) * nd * N;
+    }
+    CK(launch_bconv(ctx, l, ns, st));
+    NttBatch b;
+    b.count = npolys * nd;
+    for (int t = 0; t < nd; ++t)
+        for (int p = 0; p < npolys; ++p) {
+            u64 *q = w + (size_t(p) * nd + t) * N;
+            b.src[t * npolys + p] = q;
+            b.dst[t * npolys + p] = q;
+            b.prime[t * npolys + p] = uint16_t(t);
+        }
+    Epi e{};
+    e.mode = EPI_SCALE;
+    e.npolys = npolys;
+    for (int p = 0; p < 2; ++p) {
+        e.x[p] = p < npolys ? in[p] : nullptr;
+        e.out[p] = p < npolys ? out[p] : nullptr;
+        e.add[p] = nullptr;
+    }
+    e.galois = 1;
+    e.accumulate = 0;
+    e.cmul = ctx->d_Dinv + size_t(ell) * (ctx->L + ctx->k);
+    CK(launch_ntt_fwd(ctx, b, &e, st));
+    return CKKS_OK;
+}
+
 // ---- workspace layouts (in words)
 struct KsLayout {
     size_t uv, ext, acoeff, pcoeff, w, total;
@@ -637,6 +728,10 @@ extern "C" int ckks_workspace_bytes(const ckks_ctx *c, int op, int ell, int r, s
     case CKKS_OP_MULT:
         if (ell < 2) return CKKS_EINVAL;
         w = hr_layout(c, ell).total + size_t(5) * ell * N;
+        break;
+    case CKKS_OP_NEWMULT:
+        if (ell < 2) return CKKS_EINVAL;
+        w = hr_layout(c, ell).total + size_t(3) * ell * N;
         break;
     default: return CKKS_EINVAL;
     }
@@ -770,7 +865,8 @@ extern "C" int ckks_hrotate(ckks_ctx *ctx, const uint64_t *a, const uint64_t *b,
 // Per-entry workspace: the HRotate layout of its level, then for Mult entries
 // a3, b3, c3 and the key switch's outputs (a', b') before the Rescale.
 size_t ckks::entry_ws_words(const ckks_ctx *c, int kind, int ell) {
-    return hr_layout(c, ell).total + (kind == BE_MULT ? size_t(5) * ell * c->N : 0);
+    const size_t extra = kind == BE_MULT ? 5 : kind == BE_NEWMULT ? 3 : 0;
+    return hr_layout(c, ell).total + extra * ell * c->N;
 }
 
 static size_t batch_ws_words(const ckks_ctx *c, int n, const int *levels, int kind) {
@@ -803,7 +899,16 @@ static CtDesc entry_desc(const ckks_ctx *ctx, const BatchEntry &e, u64 *ws, Tens
     x.ws = ws;
     x.ell = e.ell;
     x.galois = 1;
-    if (e.kind == BE_MULT) {
+    if (e.kind == BE_NEWMULT) {
+        u64 *m = ws + hr_layout(ctx, e.ell).total;
+        *te = TensorEntry{e.a, e.b, e.a2, e.b2, m, m + lN, m + 2 * lN, e.ell};
+        x.a = m;
+        x.add[0] = m + lN;
+        x.add[1] = m + 2 * lN;
+        x.oa = e.oa;
+        x.ob = e.ob;
+        x.merged = 1;
+    } else if (e.kind == BE_MULT) {
         u64 *m = ws + hr_layout(ctx, e.ell).total;
         *te = TensorEntry{e.a, e.b, e.a2, e.b2, m, m + lN, m + 2 * lN, e.ell};
         x.a = m;
@@ -839,8 +944,18 @@ static int entry_one(ckks_ctx *ctx, const CtDesc &c, const TensorEntry *te, cuda
     const HrLayout lo = hr_layout(ctx, c.ell);
     RC(modup_all(ctx, c.a, c.ell, c.ws + lo.ext, c.ws + lo.tmp, st));
     u64 *u = c.ws + lo.uv, *v = u + size_t(c.ell + ctx->k) * N;
-    InnerArgs ia{c.ws + lo.ext, c.a, c.key, u, v, c.ell, c.galois};
+    InnerArgs ia{c.ws + lo.ext, c.a, c.key, u, v, c.ell, c.galois, {nullptr, nullptr}};
+    if (c.merged) {
+        ia.padd[0] = c.add[0];
+        ia.padd[1] = c.add[1];
+    }
     CK(launch_inner_prod(ctx, ia, st));
+    if (c.merged) {
+        const u64 *in[2] = {u, v};
+        u64 *out[2] = {c.oa, c.ob};
+        return moddown_merged_polys(ctx, c.ell, 2, in, out, c.ws + lo.tmp,
+                                    c.ws + lo.tmp + size_t(2) * (ctx->k + 1) * N, st);
+    }
     const u64 *in[2] = {u, v};
     u64 *out[2] = {c.oa, c.ob};
     const u64 *add[2] = {c.add[0], c.add[1]};
@@ -874,7 +989,7 @@ int ckks::run_batch(ckks_ctx *ctx, int n, const BatchEntry *e, u64 *w, cudaStrea
             te_of[c] = -1;
             TensorEntry te{};
             d.ct[c] = entry_desc(ctx, x, x.ws != nullptr ? x.ws : w, &te);
-            if (x.kind == BE_MULT) {
+            if (x.kind == BE_MULT || x.kind == BE_NEWMULT) {
                 te_of[c] = T.n;
                 T.e[T.n++] = te;
             }
@@ -920,21 +1035,50 @@ extern "C" int ckks_keyswitch_batch(ckks_ctx *ctx, int n, const uint64_t *const 
     return run_batch(ctx, n, e.data(), static_cast<u64 *>(ws), (cudaStream_t)stream);
 }
 
-extern "C" int ckks_mult_batch(ckks_ctx *ctx, int n, const uint64_t *const *a1, const uint64_t *const *b1,
-                               const uint64_t *const *a2, const uint64_t *const *b2, const int *levels,
-                               const uint64_t *const *keys, uint64_t *const *oa, uint64_t *const *ob, void *ws,
-                               ckks_stream_t stream) {
+static int mult_like_batch(ckks_ctx *ctx, int kind, int n, const uint64_t *const *a1, const uint64_t *const *b1,
+                           const uint64_t *const *a2, const uint64_t *const *b2, const int *levels,
+                           const uint64_t *const *keys, uint64_t *const *oa, uint64_t *const *ob, void *ws,
+                           ckks_stream_t stream) {
     if (ctx == nullptr || n < 0) return CKKS_EINVAL;
     if (n == 0) return CKKS_OK;
     if (!a1 || !b1 || !a2 || !b2 || !levels || !keys || !oa || !ob || !al16(ws)) return CKKS_EINVAL;
+    if (kind == BE_NEWMULT && ctx->k + 1 > kMaxSrc) return CKKS_EUNSUPPORTED;
     std::vector<BatchEntry> e(n);
     for (int i = 0; i < n; ++i) {
         if (!level_ok(ctx, levels[i]) || levels[i] < 2 || !al16(a1[i]) || !al16(b1[i]) || !al16(a2[i]) ||
             !al16(b2[i]) || !al16(keys[i]) || !al16(oa[i]) || !al16(ob[i]))
             return CKKS_EINVAL;
-        e[i] = BatchEntry{BE_MULT, a1[i], b1[i], a2[i], b2[i], keys[i], oa[i], ob[i], levels[i], 1u, nullptr};
+        e[i] = BatchEntry{kind, a1[i], b1[i], a2[i], b2[i], keys[i], oa[i], ob[i], levels[i], 1u, nullptr};
     }
     return run_batch(ctx, n, e.data(), static_cast<u64 *>(ws), (cudaStream_t)stream);
+}
+
+extern "C" int ckks_mult_batch(ckks_ctx *ctx, int n, const uint64_t *const *a1, const uint64_t *const *b1,
+                               const uint64_t *const *a2, const uint64_t *const *b2, const int *levels,
+                               const uint64_t *const *keys, uint64_t *const *oa, uint64_t *const *ob, void *ws,
+                               ckks_stream_t stream) {
+    return mult_like_batch(ctx, BE_MULT, n, a1, b1, a2, b2, levels, keys, oa, ob, ws, stream);
+}
+
+extern "C" int ckks_newmult_batch_workspace_bytes(const ckks_ctx *ctx, int n, const int *levels, size_t *bytes) {
+    if (ctx == nullptr || bytes == nullptr || n < 0 || (n > 0 && levels == nullptr)) return CKKS_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (!level_ok(ctx, levels[i]) || levels[i] < 2) return CKKS_EINVAL;
+    *bytes = batch_ws_words(ctx, n, levels, BE_NEWMULT) * sizeof(u64);
+    return CKKS_OK;
+}
+
+extern "C" int ckks_newmult_batch(ckks_ctx *ctx, int n, const uint64_t *const *a1, const uint64_t *const *b1,
+                                  const uint64_t *const *a2, const uint64_t *const *b2, const int *levels,
+                                  const uint64_t *const *keys, uint64_t *const *oa, uint64_t *const *ob, void *ws,
+                                  ckks_stream_t stream) {
+    return mult_like_batch(ctx, BE_NEWMULT, n, a1, b1, a2, b2, levels, keys, oa, ob, ws, stream);
+}
+
+extern "C" int ckks_newmult(ckks_ctx *ctx, const uint64_t *a1, const uint64_t *b1, const uint64_t *a2,
+                            const uint64_t *b2, int level, const uint64_t *key, uint64_t *oa, uint64_t *ob, void *ws,
+                            ckks_stream_t stream) {
+    return ckks_newmult_batch(ctx, 1, &a1, &b1, &a2, &b2, &level, &key, &oa, &ob, ws, stream);
 }
 
 extern "C" int ckks_mult(ckks_ctx *ctx, const uint64_t *a1, const uint64_t *b1, const uint64_t *a2,

@@ -199,24 +199,27 @@ cudaError_t launch_bconv_batch(const ckks_ctx *ctx, const KsBatchDesc &d, int do
     gm.modup = ctx->d_modup;
     gm.moddown = ctx->d_moddown;
     gm.rescale = ctx->d_rescale;
-    int groups = 0, n_all = 0;
+    gm.merged = ctx->d_mdmerged;
+    int groups = 0, n_all = 0, max_src = 1;
     for (int c = 0; c < d.n; ++c) {
-        const int ell = d.ct[c].ell, beta = (ell + d.alpha - 1) / d.alpha;
+        const CtDesc &x = d.ct[c];
+        const int ell = x.ell, beta = (ell + d.alpha - 1) / d.alpha;
         gm.d.pre[c] = groups;
         if (down == GM_MODUP) {
             groups += beta;
             n_all = std::max(n_all, ell + d.k - std::min(d.alpha, ell - (beta - 1) * d.alpha));
+            max_src = std::max(max_src, d.alpha);
         } else if (down == GM_MODDOWN) {
             groups += 2;
-            n_all = std::max(n_all, ell);
-        } else if (d.ct[c].ra != nullptr) {
+            n_all = std::max(n_all, ell - x.merged);
+            max_src = std::max(max_src, d.k + x.merged);
+        } else if (x.ra != nullptr) {
             groups += 2;
             n_all = std::max(n_all, ell - 1);
         }
     }
     gm.d.pre[d.n] = groups;
     if (groups == 0 || n_all == 0) return cudaSuccess;
-    const int max_src = down == GM_MODUP ? d.alpha : down == GM_MODDOWN ? d.k : 1;
     return launch_split(ctx, gm, groups, n_all, max_src, st);
 }
 

@@ -66,11 +66,15 @@ constexpr int kMaxCts = 64;
 //   HRotate, one rotation:     add = {0, b}, digits read through galois
 //                              (Algorithm 4): (u, v + Automorph_g(b));
 //   Mult (Algorithm 2):        a = a1*a2, add = {a1 b2 + a2 b1, b1 b2},
-//                              galois = 1, then ra/rb = Rescale(oa/ob).
+//                              galois = 1, then ra/rb = Rescale(oa/ob);
+//   NewMult (Algorithm 7):     merged = 1: the inner product adds
+//                              PModUp(add[p]) on the chain positions and one
+//                              ModDown by D = P*q_{ell-1} (sources: the k
+//                              P-limbs and q_{ell-1}) writes oa/ob [ell-1][N].
 // ws: this entry's workspace, laid out for its level:
 //   ext [beta][ell+k][N] | uv [2][ell+k][N] | tmp (acoeff [ell][N], later
-//   pcoeff [2][k][N] and w [2][ell][N]).  After the key switch the Rescale
-//   of a Mult entry reuses ext: c [2][N] | w [2][ell-1][N].
+//   pcoeff [2][k(+1)][N] and w [2][ell(-1)][N]).  After the key switch the
+//   Rescale of a Mult entry reuses ext: c [2][N] | w [2][ell-1][N].
 struct CtDesc {
     const u64 *a, *key;
     const u64 *add[2];
@@ -78,6 +82,7 @@ struct CtDesc {
     u64 *ra, *rb;  // Rescale outputs [ell-1][N] (Mult entries), else null
     int ell;
     uint32_t galois;
+    int merged;    // NewMult entry
 };
 
 struct KsBatchDesc {
@@ -101,7 +106,7 @@ __host__ __device__ __forceinline__ CtLayout ct_layout(const KsBatchDesc &d, con
     o.uv = c.ws + size_t(o.beta) * o.ext * N;
     o.acoeff = o.uv + size_t(2) * o.ext * N;
     o.pcoeff = o.acoeff;
-    o.w = o.pcoeff + size_t(2) * d.k * N;
+    o.w = o.pcoeff + size_t(2) * (d.k + c.merged) * N;
     return o;
 }
 
@@ -125,8 +130,8 @@ __host__ __device__ __forceinline__ int phase_count(const KsBatchDesc &d, const 
     switch (phase) {
     case PH_INTT_A: return ell;
     case PH_NTT_UP: return beta * (ell + d.k) - ell;
-    case PH_INTT_P: return 2 * d.k;
-    case PH_NTT_DOWN: return 2 * ell;
+    case PH_INTT_P: return 2 * (d.k + c.merged);
+    case PH_NTT_DOWN: return 2 * (ell - c.merged);
     case PH_RS_INTT: return c.ra != nullptr ? 2 : 0;
     default: return c.ra != nullptr ? 2 * (ell - 1) : 0;
     }
@@ -138,6 +143,7 @@ struct MapBatch {
     int second;               // second pass: in place on the first pass's output
     const ulonglong2 *cm;     // [P^-1]_q per prime (ModDown epilogue)
     const ulonglong2 *qlinv;  // [q_{ell-1}^-1]_{q_i} at ell*(L+k) + i (Rescale epilogue)
+    const ulonglong2 *dinv;   // [(P q_{ell-1})^-1]_{q_i} at ell*(L+k) + i (merged ModDown epilogue)
     __device__ __forceinline__ LimbIO get(int l, uint32_t N) const {
         int i;
         const int c = batch_find(d, l, i);
@@ -175,20 +181,24 @@ struct MapBatch {
             io.dst = p;
             io.prime = t < ell ? t : d.L + (t - ell);
         } else if (phase == PH_INTT_P) {
+            // the k P-limbs (and for NewMult q_{ell-1} as source k) of both polynomials
             const int m = i >> 1, poly = i & 1;
-            io.src = lo.uv + (size_t(poly) * lo.ext + ell + m) * N;
-            io.dst = lo.pcoeff + (size_t(poly) * d.k + m) * N;
-            io.prime = d.L + m;
+            const int pos = m < d.k ? ell + m : ell - 1;
+            io.src = lo.uv + (size_t(poly) * lo.ext + pos) * N;
+            io.dst = lo.pcoeff + (size_t(poly) * (d.k + ct.merged) + m) * N;
+            io.prime = m < d.k ? d.L + m : ell - 1;
         } else if (phase == PH_NTT_DOWN) {
             const int t = i >> 1, poly = i & 1;
-            u64 *p = lo.w + (size_t(poly) * ell + t) * N;
+            const int nout = ell - ct.merged;
+            u64 *p = lo.w + (size_t(poly) * nout + t) * N;
             io.src = p;
             io.dst = p;
             io.prime = t;
             io.ex = lo.uv + (size_t(poly) * lo.ext + t) * N;
             io.eout = (poly ? ct.ob : ct.oa) + size_t(t) * N;
-            io.eadd = ct.add[poly] != nullptr ? ct.add[poly] + size_t(t) * N : nullptr;
+            io.eadd = (!ct.merged && ct.add[poly] != nullptr) ? ct.add[poly] + size_t(t) * N : nullptr;
             io.galois = ct.galois;
+            if (ct.merged) io.cmul = dinv + size_t(ell) * (d.L + d.k);
         } else if (phase == PH_RS_INTT) {
             // last limb of the key switch's output p -> c[p]
             io.src = (i ? ct.ob : ct.oa) + size_t(ell - 1) * N;
@@ -233,6 +243,7 @@ struct GroupMapBatch {
     const BConvPlan *modup;     // [(L+1)*dnum]
     const BConvPlan *moddown;   // [L+1]
     const BConvPlan *rescale;   // [L+1]
+    const BConvPlan *merged;    // [L+1]: D = P*q_{ell-1} -> q_0..q_{ell-2}
     __device__ __forceinline__ BConvGroup get(int gi) const {
         int i;
         const int c = batch_find(d, gi, i);
@@ -245,9 +256,9 @@ struct GroupMapBatch {
             g.src = lo.acoeff + size_t(i) * d.alpha * N;
             g.dst = lo.extp + size_t(i) * lo.ext * N;
         } else if (down == GM_MODDOWN) {
-            g.plan = moddown + ct.ell;
-            g.src = lo.pcoeff + size_t(i) * d.k * N;
-            g.dst = lo.w + size_t(i) * ct.ell * N;
+            g.plan = (ct.merged ? merged : moddown) + ct.ell;
+            g.src = lo.pcoeff + size_t(i) * (d.k + ct.merged) * N;
+            g.dst = lo.w + size_t(i) * (ct.ell - ct.merged) * N;
         } else {
             g.plan = rescale + ct.ell;
             g.src = ct.ws + size_t(i) * N;

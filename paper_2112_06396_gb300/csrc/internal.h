@@ -23,9 +23,11 @@ struct ckks_ctx {
     ckks::BConvPlan *d_modup;         // [(L+1)*dnum]: plan (ell, digit j) at ell*dnum + j
     ckks::BConvPlan *d_moddown;       // [L+1]: P -> q_0..q_{ell-1} with rounding
     ckks::BConvPlan *d_rescale;       // [L+1]: q_{ell-1} -> q_0..q_{ell-2} with rounding
+    ckks::BConvPlan *d_mdmerged;      // [L+1]: P*q_{ell-1} -> q_0..q_{ell-2} with rounding (NewMult)
     ulonglong2 *d_Pinv;               // [L+k]: [P^-1]_{q} (chain entries used)
     ulonglong2 *d_Pmod;               // [L+k]: [P]_{q}
     ulonglong2 *d_qlinv;              // [(L+1)*(L+k)]: [q_{ell-1}^-1]_{q_i} at ell*(L+k) + i
+    ulonglong2 *d_Dinv;               // [(L+1)*(L+k)]: [(P q_{ell-1})^-1]_{q_i} at ell*(L+k) + i
     int last_cuda_error;
     // measurement hook (ckks_profile_*): event pairs around every launch
     struct ProfRec {
@@ -96,13 +98,14 @@ struct InnerArgs {
     u64 *u, *v;          // [ell+k][N]
     int ell;
     uint32_t galois;     // 1 = no automorphism
+    const u64 *padd[2];  // optional [ell][N]: u += P*padd[0], v += P*padd[1] on the chain positions (NewMult)
 };
 cudaError_t launch_inner_prod(const ckks_ctx *ctx, const InnerArgs &a, cudaStream_t st);
 cudaError_t launch_inner_prod_batch(const ckks_ctx *ctx, const KsBatchDesc &d, cudaStream_t st);
 cudaError_t launch_tensor(const ckks_ctx *ctx, const TensorBatch &T, cudaStream_t st);
 
 // ---- batch executor (abi.cu), shared with the serving loop (serve.cu)
-enum { BE_KEYSWITCH = 0, BE_HROTATE = 1, BE_MULT = 2 };
+enum { BE_KEYSWITCH = 0, BE_HROTATE = 1, BE_MULT = 2, BE_NEWMULT = 3 };
 struct BatchEntry {
     int kind;
     const u64 *a, *b;    // KeySwitch: a; HRotate: (a, b); Mult: first ciphertext (a1, b1)

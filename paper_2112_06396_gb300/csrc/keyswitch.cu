@@ -37,9 +37,21 @@ __device__ __forceinline__ ulonglong2 ld2_perm(const u64 *limb, uint32_t n0, uin
 // u_t = sum_{j<beta} d_j[t] * key[j][0][t'], v_t = sum_j d_j[t] * key[j][1][t']
 // (t' = key row of position t), with d_j read through Automorph_g.  The
 // digit's own limbs come from `own` when given (ModUp copies them unchanged).
+// With padd set (NewMult), P*padd[0] and P*padd[1] join the sums on the chain
+// positions (PModUp is 0 on the P positions), before the one reduction.
+__device__ __forceinline__ void add_pmodup(const InnerArgs &A, int t, uint32_t n0, size_t N, ulonglong2 pm, u64 &ul0,
+                                           u64 &uh0, u64 &ul1, u64 &uh1, u64 &vl0, u64 &vh0, u64 &vl1, u64 &vh1) {
+    if (A.padd[0] == nullptr || t >= A.ell) return;
+    const ulonglong2 b = ld2(A.padd[0] + size_t(t) * N + n0), c = ld2(A.padd[1] + size_t(t) * N + n0);
+    mac128(ul0, uh0, b.x, pm.x);
+    mac128(ul1, uh1, b.y, pm.x);
+    mac128(vl0, vh0, c.x, pm.x);
+    mac128(vl1, vh1, c.y, pm.x);
+}
+
 template <int BETA>
 __global__ void __launch_bounds__(256) inner_prod_kernel(InnerArgs A, const PrimeInfo *__restrict__ pinfo, int logN,
-                                                         int L, int k, int alpha) {
+                                                         int L, int k, int alpha, const ulonglong2 *__restrict__ Pmod) {
     const size_t N = size_t(1) << logN;
     const uint32_t n0 = (blockIdx.x * blockDim.x + threadIdx.x) * 2;
     if (n0 >= N) return;
@@ -65,13 +77,15 @@ __global__ void __launch_bounds__(256) inner_prod_kernel(InnerArgs A, const Prim
         mac128(vl0, vh0, dv[j].x, kb[j].x);
         mac128(vl1, vh1, dv[j].y, kb[j].y);
     }
+    add_pmodup(A, t, n0, N, Pmod[prime], ul0, uh0, ul1, uh1, vl0, vh0, vl1, vh1);
     st2(A.u + size_t(t) * N + n0, make_ulonglong2(reduce128(ul0, uh0, P), reduce128(ul1, uh1, P)));
     st2(A.v + size_t(t) * N + n0, make_ulonglong2(reduce128(vl0, vh0, P), reduce128(vl1, vh1, P)));
 }
 
 // beta > 4: loop over digits
 __global__ void __launch_bounds__(256) inner_prod_kernel_any(InnerArgs A, const PrimeInfo *__restrict__ pinfo, int logN,
-                                                             int L, int k, int alpha) {
+                                                             int L, int k, int alpha,
+                                                             const ulonglong2 *__restrict__ Pmod) {
     const size_t N = size_t(1) << logN;
     const uint32_t n0 = (blockIdx.x * blockDim.x + threadIdx.x) * 2;
     if (n0 >= N) return;
@@ -92,6 +106,7 @@ __global__ void __launch_bounds__(256) inner_prod_kernel_any(InnerArgs A, const 
         mac128(vl0, vh0, dv.x, kb.x);
         mac128(vl1, vh1, dv.y, kb.y);
     }
+    add_pmodup(A, t, n0, N, Pmod[prime], ul0, uh0, ul1, uh1, vl0, vh0, vl1, vh1);
     st2(A.u + size_t(t) * N + n0, make_ulonglong2(reduce128(ul0, uh0, P), reduce128(ul1, uh1, P)));
     st2(A.v + size_t(t) * N + n0, make_ulonglong2(reduce128(vl0, vh0, P), reduce128(vl1, vh1, P)));
 }
@@ -102,12 +117,12 @@ cudaError_t launch_inner_prod(const ckks_ctx *ctx, const InnerArgs &a, cudaStrea
     ProfScope ps(ctx, K_INNER, a.ell + ctx->k, st);
     const int beta = beta_of(ctx, a.ell);
     switch (beta) {
-    case 1: inner_prod_kernel<1><<<grid, threads, 0, st>>>(a, ctx->d_pinfo, ctx->logN, ctx->L, ctx->k, ctx->alpha); break;
-    case 2: inner_prod_kernel<2><<<grid, threads, 0, st>>>(a, ctx->d_pinfo, ctx->logN, ctx->L, ctx->k, ctx->alpha); break;
-    case 3: inner_prod_kernel<3><<<grid, threads, 0, st>>>(a, ctx->d_pinfo, ctx->logN, ctx->L, ctx->k, ctx->alpha); break;
-    case 4: inner_prod_kernel<4><<<grid, threads, 0, st>>>(a, ctx->d_pinfo, ctx->logN, ctx->L, ctx->k, ctx->alpha); break;
+    case 1: inner_prod_kernel<1><<<grid, threads, 0, st>>>(a, ctx->d_pinfo, ctx->logN, ctx->L, ctx->k, ctx->alpha, ctx->d_Pmod); break;
+    case 2: inner_prod_kernel<2><<<grid, threads, 0, st>>>(a, ctx->d_pinfo, ctx->logN, ctx->L, ctx->k, ctx->alpha, ctx->d_Pmod); break;
+    case 3: inner_prod_kernel<3><<<grid, threads, 0, st>>>(a, ctx->d_pinfo, ctx->logN, ctx->L, ctx->k, ctx->alpha, ctx->d_Pmod); break;
+    case 4: inner_prod_kernel<4><<<grid, threads, 0, st>>>(a, ctx->d_pinfo, ctx->logN, ctx->L, ctx->k, ctx->alpha, ctx->d_Pmod); break;
     default:
-        inner_prod_kernel_any<<<grid, threads, 0, st>>>(a, ctx->d_pinfo, ctx->logN, ctx->L, ctx->k, ctx->alpha);
+        inner_prod_kernel_any<<<grid, threads, 0, st>>>(a, ctx->d_pinfo, ctx->logN, ctx->L, ctx->k, ctx->alpha, ctx->d_Pmod);
     }
     return cudaGetLastError();
 }
@@ -123,7 +138,8 @@ cudaError_t launch_inner_prod(const ckks_ctx *ctx, const InnerArgs &a, cudaStrea
 // through its own Galois element and writes its u, v into its workspace.
 template <int BMAX>
 __global__ void __launch_bounds__(256) inner_prod_batch_kernel(const __grid_constant__ KsBatchDesc d,
-                                                               const PrimeInfo *__restrict__ pinfo) {
+                                                               const PrimeInfo *__restrict__ pinfo,
+                                                               const ulonglong2 *__restrict__ Pmod) {
     const CtDesc &ct = d.ct[blockIdx.x];
     const int ell = ct.ell;
     const int pi = blockIdx.z;
@@ -173,6 +189,15 @@ __global__ void __launch_bounds__(256) inner_prod_batch_kernel(const __grid_cons
             mac128(vl1, vh1, dv.y, b2.y);
         }
     }
+    if (ct.merged && t < ell) {
+        // NewMult: PModUp(b3), PModUp(c3) join the sums before the one reduction
+        const u64 pm = Pmod[pi].x;
+        const ulonglong2 b = ld2(ct.add[0] + size_t(t) * N + n0), c = ld2(ct.add[1] + size_t(t) * N + n0);
+        mac128(ul0, uh0, b.x, pm);
+        mac128(ul1, uh1, b.y, pm);
+        mac128(vl0, vh0, c.x, pm);
+        mac128(vl1, vh1, c.y, pm);
+    }
     const PrimeInfo P = pinfo[pi];
     st2(lo.uv + size_t(t) * N + n0, make_ulonglong2(reduce128(ul0, uh0, P), reduce128(ul1, uh1, P)));
     st2(lo.uv + (size_t(lo.ext) + t) * N + n0, make_ulonglong2(reduce128(vl0, vh0, P), reduce128(vl1, vh1, P)));
@@ -186,11 +211,11 @@ cudaError_t launch_inner_prod_batch(const ckks_ctx *ctx, const KsBatchDesc &d, c
     dim3 grid(unsigned(d.n), unsigned((ctx->N / 2 + threads - 1) / threads), unsigned(ctx->L + ctx->k));
     ProfScope ps(ctx, K_INNER, units, st);
     switch (ctx->dnum) {
-    case 1: inner_prod_batch_kernel<1><<<grid, threads, 0, st>>>(d, ctx->d_pinfo); break;
-    case 2: inner_prod_batch_kernel<2><<<grid, threads, 0, st>>>(d, ctx->d_pinfo); break;
-    case 3: inner_prod_batch_kernel<3><<<grid, threads, 0, st>>>(d, ctx->d_pinfo); break;
-    case 4: inner_prod_batch_kernel<4><<<grid, threads, 0, st>>>(d, ctx->d_pinfo); break;
-    default: inner_prod_batch_kernel<0><<<grid, threads, 0, st>>>(d, ctx->d_pinfo);
+    case 1: inner_prod_batch_kernel<1><<<grid, threads, 0, st>>>(d, ctx->d_pinfo, ctx->d_Pmod); break;
+    case 2: inner_prod_batch_kernel<2><<<grid, threads, 0, st>>>(d, ctx->d_pinfo, ctx->d_Pmod); break;
+    case 3: inner_prod_batch_kernel<3><<<grid, threads, 0, st>>>(d, ctx->d_pinfo, ctx->d_Pmod); break;
+    case 4: inner_prod_batch_kernel<4><<<grid, threads, 0, st>>>(d, ctx->d_pinfo, ctx->d_Pmod); break;
+    default: inner_prod_batch_kernel<0><<<grid, threads, 0, st>>>(d, ctx->d_pinfo, ctx->d_Pmod);
     }
     return cudaGetLastError();
 }

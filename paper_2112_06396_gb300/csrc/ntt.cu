@@ -416,6 +416,7 @@ cudaError_t launch_ntt_batch(const ckks_ctx *ctx, const KsBatchDesc &d, int phas
     m.phase = phase;
     m.cm = ctx->d_Pinv;
     m.qlinv = ctx->d_qlinv;
+    m.dinv = ctx->d_Dinv;
     int count = 0;
     for (int c = 0; c < d.n; ++c) {
         m.d.pre[c] = count;

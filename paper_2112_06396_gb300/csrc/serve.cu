@@ -146,19 +146,30 @@ static size_t ct_bytes(const ckks_ctx *c, int op, int ell) {
     default: return (size_t(4) * ell + size_t(2) * (ell - 1)) * limb;
     }
 }
-static int kind_of(int op) { return op == CKKS_REQ_HROTATE ? BE_HROTATE : op == CKKS_REQ_MULT ? BE_MULT : BE_KEYSWITCH; }
+static int kind_of(int op) {
+    switch (op) {
+    case CKKS_REQ_HROTATE: return BE_HROTATE;
+    case CKKS_REQ_MULT: return BE_MULT;
+    case CKKS_REQ_NEWMULT: return BE_NEWMULT;
+    default: return BE_KEYSWITCH;
+    }
+}
 
 extern "C" int ckks_server_submit(ckks_server *s, const ckks_request *r, uint64_t *id) {
     if (s == nullptr || r == nullptr || id == nullptr) return CKKS_EINVAL;
     if (r->ctx < 0 || r->ctx >= int(s->ctxs.size())) return CKKS_EINVAL;
-    if (r->op != CKKS_REQ_HROTATE && r->op != CKKS_REQ_MULT && r->op != CKKS_REQ_KEYSWITCH) return CKKS_EINVAL;
+    if (r->op != CKKS_REQ_HROTATE && r->op != CKKS_REQ_MULT && r->op != CKKS_REQ_KEYSWITCH &&
+        r->op != CKKS_REQ_NEWMULT)
+        return CKKS_EINVAL;
     const ckks_ctx *c = s->ctxs[size_t(r->ctx)];
-    const int min_level = r->op == CKKS_REQ_MULT ? 2 : 1;
+    const bool mult = r->op == CKKS_REQ_MULT || r->op == CKKS_REQ_NEWMULT;
+    if (r->op == CKKS_REQ_NEWMULT && c->k + 1 > kMaxSrc) return CKKS_EUNSUPPORTED;
+    const int min_level = mult ? 2 : 1;
     if (r->level < min_level || r->level > c->L) return CKKS_EINVAL;
     if (r->key < 0 || r->key >= int(s->keys.size()) || s->keys[size_t(r->key)].ctx != r->ctx) return CKKS_EINVAL;
     if (!al16(r->a) || !al16(r->oa) || !al16(r->ob)) return CKKS_EINVAL;
     if (r->op != CKKS_REQ_KEYSWITCH && !al16(r->b)) return CKKS_EINVAL;
-    if (r->op == CKKS_REQ_MULT && (!al16(r->a2) || !al16(r->b2))) return CKKS_EINVAL;
+    if (mult && (!al16(r->a2) || !al16(r->b2))) return CKKS_EINVAL;
     if (r->op == CKKS_REQ_HROTATE && (!(r->galois & 1u) || r->galois >= uint32_t(2 * c->N))) return CKKS_EINVAL;
     SchedReq q{s->next_id, r->ctx, entry_ws_words(c, kind_of(r->op), r->level) * sizeof(u64),
                ct_bytes(c, r->op, r->level)};

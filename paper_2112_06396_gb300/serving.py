@@ -14,7 +14,7 @@ import statistics
 
 def replay(server, requests, max_wall_s=600.0):
     """requests: list of dicts with keys t_ms (arrival offset), op ('hrotate',
-    'mult' or 'keyswitch'), ctx, level, a, b (and a2, b2 for mult), galois,
+    'mult', 'newmult' or 'keyswitch'), ctx, level, a, b (and a2, b2 for mult), galois,
     key (server handle), oa, ob; sorted by t_ms.  Returns (results, stats):
     results maps request index -> (latency_ms, done_ms); stats has the
     throughput over the run and p50 / p99 latencies."""
@@ -33,9 +33,9 @@ def replay(server, requests, max_wall_s=600.0):
             if r["op"] == "hrotate":
                 rid = server.submit_hrotate(r["ctx"], r["a"], r["b"], r["level"], r["galois"], r["key"], r["oa"],
                                             r["ob"], arr)
-            elif r["op"] == "mult":
+            elif r["op"] in ("mult", "newmult"):
                 rid = server.submit_mult(r["ctx"], (r["a"], r["b"]), (r["a2"], r["b2"]), r["level"], r["key"],
-                                         r["oa"], r["ob"], arr)
+                                         r["oa"], r["ob"], arr, new=r["op"] == "newmult")
             else:
                 rid = server.submit_keyswitch(r["ctx"], r["a"], r["level"], r["key"], r["oa"], r["ob"], arr)
             ids[rid] = i

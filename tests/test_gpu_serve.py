@@ -1,5 +1,5 @@
 """The serving loop through the C ABI: requests of two ring degrees, mixed
-operations (HRotate, KeySwitch, Mult + relinearisation + Rescale) and mixed
+operations (HRotate, KeySwitch, Mult + relinearisation + Rescale, NewMult) and mixed
 levels arrive while others run; every result must carry the bits of the same
 request run alone (tolerance 0, exact modular arithmetic), whatever batch it
 landed in and whatever ran beside it."""
@@ -25,7 +25,7 @@ class Pool:
             self.keys.append({g: dev(S.key(g, f"gpu/serve/{c}/key{g}")[0]) for g in [0] + self.gs})
 
     def requests(self, n, tag, gap_ms=0.02):
-        ops = synth.uniform_ints(n, 0, 2, f"{tag}/op")
+        ops = synth.uniform_ints(n, 0, 3, f"{tag}/op")
         ctxs = synth.uniform_ints(n, 0, 1, f"{tag}/ctx")
         lv = synth.uniform_ints(n, 2, 6, f"{tag}/level")
         gaps = synth.exponential_gaps(n, gap_ms, f"{tag}/gaps")
@@ -39,10 +39,10 @@ class Pool:
             if ops[i] == 0:
                 g = self.gs[i % 2]
                 r.update(op="hrotate", galois=g, kkey=g, oa=S.ctx.empty(ell), ob=S.ctx.empty(ell))
-            elif ops[i] == 1:
+            elif ops[i] in (1, 3):
                 a2, b2 = S.ct(ell, f"{tag}/{i}/2")
-                r.update(op="mult", a2=dev(a2), b2=dev(b2), galois=1, kkey=0, oa=S.ctx.empty(ell - 1),
-                         ob=S.ctx.empty(ell - 1))
+                r.update(op="mult" if ops[i] == 1 else "newmult", a2=dev(a2), b2=dev(b2), galois=1, kkey=0,
+                         oa=S.ctx.empty(ell - 1), ob=S.ctx.empty(ell - 1))
             else:
                 r.update(op="keyswitch", galois=1, kkey=0, oa=S.ctx.empty(ell), ob=S.ctx.empty(ell))
             reqs.append(r)
@@ -54,8 +54,8 @@ class Pool:
         ell = r["level"]
         if r["op"] == "hrotate":
             ((oa, ob),) = ctx.hrotate(r["a"], r["b"], ell, [r["galois"]], [key])
-        elif r["op"] == "mult":
-            oa, ob = ctx.mult(r["a"], r["b"], r["a2"], r["b2"], ell, key)
+        elif r["op"] in ("mult", "newmult"):
+            oa, ob = ctx.mult(r["a"], r["b"], r["a2"], r["b2"], ell, key, new=r["op"] == "newmult")
         else:
             oa, ob = ctx.keyswitch(r["a"], ell, key)
         return host(oa), host(ob)
@@ -113,9 +113,9 @@ def test_memory_admission_limits_what_runs(pool):
     t0 = srv.now_ms()
     ids = []
     for r in reqs:
-        if r["op"] == "mult":
+        if r["op"] in ("mult", "newmult"):
             ids.append(srv.submit_mult(r["ctx"], (r["a"], r["b"]), (r["a2"], r["b2"]), r["level"], r["key"], r["oa"],
-                                       r["ob"], t0))
+                                       r["ob"], t0, new=r["op"] == "newmult"))
         elif r["op"] == "hrotate":
             ids.append(srv.submit_hrotate(r["ctx"], r["a"], r["b"], r["level"], r["galois"], r["key"], r["oa"],
                                           r["ob"], t0))
