@@ -85,6 +85,8 @@ def _load():
                 "or_mult": (ctypes.c_int, [P, ctypes.c_int, u64p, u64p, u64p, u64p, u64p, u64p, u64p]),
                 "or_newmult": (ctypes.c_int, [P, ctypes.c_int, u64p, u64p, u64p, u64p, u64p, u64p, u64p]),
                 "or_moddown_merged": (ctypes.c_int, [P, ctypes.c_int, u64p, u64p]),
+                "or_prng_key_a": (ctypes.c_uint64, [P, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_uint64]),
+                "or_prng_key_a_fill": (ctypes.c_int, [P, ctypes.c_uint64, u64p]),
                 "or_hrotate": (ctypes.c_int, [P, ctypes.c_int, u64p, u64p, ctypes.c_int, u64p,
                                               ctypes.POINTER(u64p), ctypes.POINTER(u64p), ctypes.POINTER(u64p)]),
                 "or_ptmatvec": (ctypes.c_int, [P, ctypes.c_int, u64p, u64p, ctypes.c_int, ctypes.c_int,
@@ -368,6 +370,17 @@ def keygen(P: Params, a, s, sp_eval, e):
     key = np.zeros((P.dnum, 2, P.L + P.k, P.N), dtype=np.uint64)
     _load().or_keygen(P.c, _u(a), _i(s), _u(sp_eval), _i(e), _u(key))
     return key
+
+
+def prng_key_a(P: Params, seed: int):
+    """The uniform half a of a compressed key: [dnum][L+k][N] from the seed (Sec. 5.4)."""
+    a = np.zeros((P.dnum, P.L + P.k, P.N), dtype=np.uint64)
+    _load().or_prng_key_a_fill(P.c, seed & 0xFFFFFFFFFFFFFFFF, _u(a))
+    return a
+
+
+def prng_key_a_element(P: Params, seed: int, j: int, l: int, n: int) -> int:
+    return int(_load().or_prng_key_a(P.c, seed & 0xFFFFFFFFFFFFFFFF, j, l, n))
 
 
 def encrypt(P: Params, ell, s, m_plus_e, a):

@@ -764,6 +764,47 @@ int or_keygen(const or_params *P, const u64 *a, const int64_t *s, const u64 *sp,
     return 0;
 }
 
+/* Key compression (Sec. 5.4): the uniform half a_j of a key-switching key is
+ * regenerated from a 64-bit seed instead of being stored.  The generator is
+ * SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
+ * generators", OOPSLA 2014): draw c of seed s is mix(s + (c + 1) * gamma) with
+ * gamma = 0x9E3779B97F4A7C15 and mix(z): z ^= z >> 30; z *= 0xBF58476D1CE4E5B9;
+ * z ^= z >> 27; z *= 0x94D049BB133111EB; z ^= z >> 31.  Element (j, l, n) of a
+ * (digit j, key limb l of the L+k, coefficient n; evaluation form) takes the
+ * draws 16e .. 16e+15 with e = (j*(L+k) + l)*N + n and keeps the first whose
+ * top b bits (b = bit length of the limb's prime q) are below q; if none is,
+ * the last draw's top bits mod q. */
+static u64 sm_mix(u64 z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+static int bitlen(u64 x) {
+    int b = 0;
+    while (x) { b++; x >>= 1; }
+    return b;
+}
+u64 or_prng_key_a(const or_params *P, u64 seed, int j, int l, u64 n) {
+    u64 q = P->primes[l];
+    int b = bitlen(q);
+    u64 e = ((u64)j * (u64)(P->L + P->k) + (u64)l) * (u64)N_of(P) + n;
+    u64 v = 0;
+    for (int r = 0; r < 16; r++) {
+        v = sm_mix(seed + (16 * e + (u64)r + 1) * 0x9E3779B97F4A7C15ull) >> (64 - b);
+        if (v < q) return v;
+    }
+    return v % q;
+}
+/* a: [dnum][L+k][N], the whole uniform half of the key for this seed. */
+int or_prng_key_a_fill(const or_params *P, u64 seed, u64 *a) {
+    size_t N = N_of(P);
+    int LK = P->L + P->k;
+    for (int j = 0; j < P->dnum; j++)
+        for (int l = 0; l < LK; l++)
+            for (size_t n = 0; n < N; n++) a[((size_t)j * LK + l) * N + n] = or_prng_key_a(P, seed, j, l, n);
+    return 0;
+}
+
 /* s' for a rotation key: sigma_g(s), evaluation form over all L+k primes. */
 int or_rot_secret(const or_params *P, const int64_t *s, u64 g, u64 *out) {
     size_t N = N_of(P);
