@@ -71,7 +71,8 @@ enum {
     CKKS_OP_PTMATVEC = 7,
     CKKS_OP_KEYGEN = 8,
     CKKS_OP_MULT = 9,
-    CKKS_OP_NEWMULT = 10
+    CKKS_OP_NEWMULT = 10,
+    CKKS_OP_KEYGEN_SEEDED = 11
 };
 
 typedef struct {
@@ -255,6 +256,29 @@ int ckks_ptmatvecmult(ckks_ctx *ctx, const uint64_t *d_a, const uint64_t *d_b, i
 int ckks_keygen_ksk(ckks_ctx *ctx, const int64_t *d_s, const int64_t *d_e, const uint64_t *d_a, uint32_t galois,
                     uint64_t *d_key, void *ws, ckks_stream_t stream);
 
+/* Compressed keys (Sec. 5.4): the rows a_j of a key are uniformly random, so
+ * they are regenerated from a 64-bit seed where they are used instead of being
+ * stored and read; a compressed key is the rows b_j only, [dnum][L+k][N]
+ * (half the bytes of a full key).  Element (j, l, n) of a_j is drawn from
+ * SplitMix64 (Steele, Lea and Flood, OOPSLA 2014) seeded with `seed`: draws
+ * 16e .. 16e+15 with e = (j*(L+k) + l)*N + n, the first whose top b bits
+ * (b = bit length of the limb's prime q_l) are below q_l, else the last
+ * one's top bits mod q_l.
+ * ckks_keygen_ksk_seeded: as ckks_keygen_ksk with a_j from the seed; writes
+ *   key_b [dnum][L+k][N].  Workspace CKKS_OP_KEYGEN_SEEDED.
+ * ckks_ksk_expand: the full key [dnum][2][L+k][N] of a compressed key.
+ * ckks_keyswitch_batch_seeded: ckks_keyswitch_batch with compressed keys
+ *   keys_b[i] and seeds[i]; same bits as the full keys (ckks_ksk_expand);
+ *   contexts whose primes are too wide for the split basis conversion return
+ *   CKKS_EUNSUPPORTED. */
+int ckks_keygen_ksk_seeded(ckks_ctx *ctx, const int64_t *d_s, const int64_t *d_e, uint64_t seed, uint32_t galois,
+                           uint64_t *d_key_b, void *ws, ckks_stream_t stream);
+int ckks_ksk_expand(ckks_ctx *ctx, const uint64_t *d_key_b, uint64_t seed, uint64_t *d_key, ckks_stream_t stream);
+int ckks_keyswitch_batch_seeded(ckks_ctx *ctx, int n, const uint64_t *const *d_a, const uint64_t *const *d_b,
+                                const int *levels, const uint32_t *galois, const uint64_t *const *d_keys_b,
+                                const uint64_t *seeds, uint64_t *const *d_oa, uint64_t *const *d_ob, void *ws,
+                                ckks_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * Serving loop (no counterpart in the paper; it serves the paper's operations).
  * A server owns one device arena for request workspace and nstreams CUDA
@@ -304,6 +328,8 @@ int ckks_server_create(ckks_ctx *const *ctxs, int nctx, size_t mem_budget, int m
                        ckks_server **out);
 int ckks_server_destroy(ckks_server *srv);
 int ckks_server_add_key(ckks_server *srv, int ctx, const uint64_t *d_key, int *handle);
+/* A compressed key (rows b_j only, a_j from seed) counts half the bytes. */
+int ckks_server_add_key_seeded(ckks_server *srv, int ctx, const uint64_t *d_key_b, uint64_t seed, int *handle);
 double ckks_server_now_ms(const ckks_server *srv);
 int ckks_server_submit(ckks_server *srv, const ckks_request *req, uint64_t *id);
 int ckks_server_step(ckks_server *srv, int *n_launched);

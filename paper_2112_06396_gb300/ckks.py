@@ -26,7 +26,7 @@ _lib = None
 
 CKKS_OK, CKKS_EINVAL, CKKS_ENOMEM, CKKS_ECUDA, CKKS_EUNSUPPORTED = 0, 1, 2, 3, 4
 (OP_MODUP, OP_MODDOWN, OP_KEYSWITCH, OP_ROTATE, OP_HROTATE, OP_RESCALE, OP_PTMATVEC, OP_KEYGEN, OP_MULT,
- OP_NEWMULT) = range(1, 11)
+ OP_NEWMULT, OP_KEYGEN_SEEDED) = range(1, 12)
 
 
 class CkksError(RuntimeError):
@@ -93,6 +93,13 @@ _SIGS = {
     "ckks_server_create": (_i, [ctypes.POINTER(_vp), _i, ctypes.c_size_t, _i, _i, ctypes.POINTER(_vp)]),
     "ckks_server_destroy": (_i, [_vp]),
     "ckks_server_add_key": (_i, [_vp, _i, _vp, ctypes.POINTER(_i)]),
+    "ckks_server_add_key_seeded": (_i, [_vp, _i, _vp, ctypes.c_uint64, ctypes.POINTER(_i)]),
+    "ckks_keygen_ksk_seeded": (_i, [_vp, _vp, _vp, ctypes.c_uint64, ctypes.c_uint32, _vp, _vp, _vp]),
+    "ckks_ksk_expand": (_i, [_vp, _vp, ctypes.c_uint64, _vp, _vp]),
+    "ckks_keyswitch_batch_seeded": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_i),
+                                         ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(_vp),
+                                         ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                         _vp, _vp]),
     "ckks_server_now_ms": (ctypes.c_double, [_vp]),
     "ckks_server_submit": (_i, [_vp, ctypes.POINTER(_Request), ctypes.POINTER(ctypes.c_uint64)]),
     "ckks_server_step": (_i, [_vp, ctypes.POINTER(_i)]),
@@ -323,10 +330,12 @@ class Context:
         _check(lib().ckks_batch_workspace_bytes(self._h, n, lv, ctypes.byref(nbytes)))
         return torch.empty(max(nbytes.value // 8, 2), dtype=torch.uint64, device=self.device)
 
-    def keyswitch_batch(self, a, b, levels, galois, keys, outs=None, ws=None, stream=None):
+    def keyswitch_batch(self, a, b, levels, galois, keys, outs=None, ws=None, stream=None, seeds=None):
         """Batched key switching.  a, keys: lists of tensors; b: None or a list
         whose None entries make KeySwitch entries (others are one-rotation
-        HRotates by galois[i]); levels: list of ints.  Returns [(oa, ob)]."""
+        HRotates by galois[i]); levels: list of ints; seeds: None (full keys)
+        or one seed per entry (keys are then compressed, b rows only).
+        Returns [(oa, ob)]."""
         n = len(a)
         if outs is None:
             outs = [(self.empty(levels[i]), self.empty(levels[i])) for i in range(n)]
@@ -339,8 +348,30 @@ class Context:
         kp = (_vp * m)(*[x.data_ptr() for x in keys])
         oa = (_vp * m)(*[o[0].data_ptr() for o in outs])
         ob = (_vp * m)(*[o[1].data_ptr() for o in outs])
-        _check(lib().ckks_keyswitch_batch(self._h, n, ap, bp, lv, gp, kp, oa, ob, _p(ws), _stream(stream)), self._h)
+        if seeds is None:
+            _check(lib().ckks_keyswitch_batch(self._h, n, ap, bp, lv, gp, kp, oa, ob, _p(ws), _stream(stream)),
+                   self._h)
+        else:
+            sd = (ctypes.c_uint64 * m)(*[int(x) & 0xFFFFFFFFFFFFFFFF for x in seeds])
+            _check(lib().ckks_keyswitch_batch_seeded(self._h, n, ap, bp, lv, gp, kp, sd, oa, ob, _p(ws),
+                                                     _stream(stream)), self._h)
         return outs
+
+    def keygen_ksk_seeded(self, s, e, seed, galois, key_b=None, ws=None, stream=None):
+        """Compressed key (rows b_j only, [dnum][L+k][N]); a_j comes from seed."""
+        key_b = torch.empty((self.dnum, self.L + self.k, self.N), dtype=torch.uint64,
+                            device=self.device) if key_b is None else key_b
+        ws = self.workspace(OP_KEYGEN_SEEDED, 1) if ws is None else ws
+        _check(lib().ckks_keygen_ksk_seeded(self._h, _p(s), _p(e), int(seed) & 0xFFFFFFFFFFFFFFFF, int(galois),
+                                            _p(key_b), _p(ws), _stream(stream)), self._h)
+        return key_b
+
+    def ksk_expand(self, key_b, seed, key=None, stream=None):
+        key = torch.empty((self.dnum, 2, self.L + self.k, self.N), dtype=torch.uint64,
+                          device=self.device) if key is None else key
+        _check(lib().ckks_ksk_expand(self._h, _p(key_b), int(seed) & 0xFFFFFFFFFFFFFFFF, _p(key), _stream(stream)),
+               self._h)
+        return key
 
     def mult(self, a1, b1, a2, b2, level, key, oa=None, ob=None, ws=None, stream=None, new=False):
         """Algorithm 2 (Mult + relinearisation + Rescale), or Algorithm 7 (NewMult)
@@ -432,9 +463,14 @@ class Server:
         except Exception:
             pass
 
-    def add_key(self, ctx, key):
+    def add_key(self, ctx, key, seed=None):
+        """Register a resident key; with seed, key is a compressed key (rows b_j only)."""
         hd = _i()
-        _check(lib().ckks_server_add_key(self._h, int(ctx), _p(key), ctypes.byref(hd)))
+        if seed is None:
+            _check(lib().ckks_server_add_key(self._h, int(ctx), _p(key), ctypes.byref(hd)))
+        else:
+            _check(lib().ckks_server_add_key_seeded(self._h, int(ctx), _p(key), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                                    ctypes.byref(hd)))
         self._keys.append(key)
         return hd.value
 

@@ -733,6 +733,7 @@ extern "C" int ckks_workspace_bytes(const ckks_ctx *c, int op, int ell, int r, s
         if (ell < 2) return CKKS_EINVAL;
         w = hr_layout(c, ell).total + size_t(3) * ell * N;
         break;
+    case CKKS_OP_KEYGEN_SEEDED: w = size_t(4) * (c->L + c->k) * N; break;
     default: return CKKS_EINVAL;
     }
     *bytes = w * sizeof(u64);
@@ -899,6 +900,8 @@ static CtDesc entry_desc(const ckks_ctx *ctx, const BatchEntry &e, u64 *ws, Tens
     x.ws = ws;
     x.ell = e.ell;
     x.galois = 1;
+    x.compressed = e.compressed;
+    x.seed = e.seed;
     if (e.kind == BE_NEWMULT) {
         u64 *m = ws + hr_layout(ctx, e.ell).total;
         *te = TensorEntry{e.a, e.b, e.a2, e.b2, m, m + lN, m + 2 * lN, e.ell};
@@ -934,6 +937,7 @@ static CtDesc entry_desc(const ckks_ctx *ctx, const BatchEntry &e, u64 *ws, Tens
 // primes are too wide for the split basis conversion).
 static int entry_one(ckks_ctx *ctx, const CtDesc &c, const TensorEntry *te, cudaStream_t st) {
     const size_t N = ctx->N;
+    if (c.compressed) return CKKS_EUNSUPPORTED;  // compressed keys need the batched inner product
     if (te != nullptr) {
         TensorBatch T;
         T.n = 1;
@@ -1017,9 +1021,10 @@ int ckks::run_batch(ckks_ctx *ctx, int n, const BatchEntry *e, u64 *w, cudaStrea
     return CKKS_OK;
 }
 
-extern "C" int ckks_keyswitch_batch(ckks_ctx *ctx, int n, const uint64_t *const *a, const uint64_t *const *b,
-                                    const int *levels, const uint32_t *galois, const uint64_t *const *keys,
-                                    uint64_t *const *oa, uint64_t *const *ob, void *ws, ckks_stream_t stream) {
+static int keyswitch_batch_any(ckks_ctx *ctx, int n, const uint64_t *const *a, const uint64_t *const *b,
+                               const int *levels, const uint32_t *galois, const uint64_t *const *keys,
+                               const uint64_t *seeds, uint64_t *const *oa, uint64_t *const *ob, void *ws,
+                               ckks_stream_t stream) {
     if (ctx == nullptr || n < 0) return CKKS_EINVAL;
     if (n == 0) return CKKS_OK;
     if (!a || !levels || !keys || !oa || !ob || !al16(ws)) return CKKS_EINVAL;
@@ -1030,9 +1035,24 @@ extern "C" int ckks_keyswitch_batch(ckks_ctx *ctx, int n, const uint64_t *const 
             return CKKS_EINVAL;
         if (rot && (!al16(b[i]) || galois == nullptr || !galois_ok(ctx, galois[i]))) return CKKS_EINVAL;
         e[i] = BatchEntry{rot ? BE_HROTATE : BE_KEYSWITCH, a[i], rot ? b[i] : nullptr, nullptr, nullptr, keys[i],
-                          oa[i], ob[i], levels[i], rot ? galois[i] : 1u, nullptr};
+                          oa[i], ob[i], levels[i], rot ? galois[i] : 1u, nullptr, seeds != nullptr,
+                          seeds != nullptr ? seeds[i] : 0};
     }
     return run_batch(ctx, n, e.data(), static_cast<u64 *>(ws), (cudaStream_t)stream);
+}
+
+extern "C" int ckks_keyswitch_batch(ckks_ctx *ctx, int n, const uint64_t *const *a, const uint64_t *const *b,
+                                    const int *levels, const uint32_t *galois, const uint64_t *const *keys,
+                                    uint64_t *const *oa, uint64_t *const *ob, void *ws, ckks_stream_t stream) {
+    return keyswitch_batch_any(ctx, n, a, b, levels, galois, keys, nullptr, oa, ob, ws, stream);
+}
+
+extern "C" int ckks_keyswitch_batch_seeded(ckks_ctx *ctx, int n, const uint64_t *const *a, const uint64_t *const *b,
+                                           const int *levels, const uint32_t *galois,
+                                           const uint64_t *const *keys_b, const uint64_t *seeds, uint64_t *const *oa,
+                                           uint64_t *const *ob, void *ws, ckks_stream_t stream) {
+    if (seeds == nullptr && n > 0) return CKKS_EINVAL;
+    return keyswitch_batch_any(ctx, n, a, b, levels, galois, keys_b, seeds, oa, ob, ws, stream);
 }
 
 static int mult_like_batch(ckks_ctx *ctx, int kind, int n, const uint64_t *const *a1, const uint64_t *const *b1,
@@ -1048,7 +1068,7 @@ static int mult_like_batch(ckks_ctx *ctx, int kind, int n, const uint64_t *const
         if (!level_ok(ctx, levels[i]) || levels[i] < 2 || !al16(a1[i]) || !al16(b1[i]) || !al16(a2[i]) ||
             !al16(b2[i]) || !al16(keys[i]) || !al16(oa[i]) || !al16(ob[i]))
             return CKKS_EINVAL;
-        e[i] = BatchEntry{kind, a1[i], b1[i], a2[i], b2[i], keys[i], oa[i], ob[i], levels[i], 1u, nullptr};
+        e[i] = BatchEntry{kind, a1[i], b1[i], a2[i], b2[i], keys[i], oa[i], ob[i], levels[i], 1u, nullptr, 0, 0};
     }
     return run_batch(ctx, n, e.data(), static_cast<u64 *>(ws), (cudaStream_t)stream);
 }
@@ -1167,6 +1187,46 @@ extern "C" int ckks_keygen_ksk(ckks_ctx *ctx, const int64_t *s, const int64_t *e
         RC(run_ntt(ctx, le, false, st));
         CK(launch_keygen_row(ctx, a + size_t(j) * LK * N, sh, sp, eh, j, key + size_t(2 * j) * LK * N,
                              key + size_t(2 * j + 1) * LK * N, st));
+    }
+    return CKKS_OK;
+}
+
+// Compressed keys (Sec. 5.4): only the rows b_j are stored; a_j comes from the seed.
+extern "C" int ckks_keygen_ksk_seeded(ckks_ctx *ctx, const int64_t *s, const int64_t *e, uint64_t seed, uint32_t g,
+                                      uint64_t *key_b, void *ws, ckks_stream_t stream) {
+    if (ctx == nullptr || !al16(s) || !al16(e) || !al16(key_b) || !al16(ws) || (g != 0 && !galois_ok(ctx, g)))
+        return CKKS_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t N = ctx->N;
+    const int LK = ctx->L + ctx->k;
+    u64 *sh = static_cast<u64 *>(ws), *sp = sh + size_t(LK) * N, *eh = sp + size_t(LK) * N, *aj = eh + size_t(LK) * N;
+    LimbList ls, le;
+    for (int l = 0; l < LK; ++l) {
+        ls.add(sh + l * N, sh + l * N, l);
+        le.add(eh + l * N, eh + l * N, l);
+    }
+    CK(launch_signed_to_res(ctx, s, sh, st));
+    RC(run_ntt(ctx, ls, false, st));
+    if (g != 0) CK(launch_automorph(ctx, sh, sp, LK, g, st));
+    else CK(launch_square(ctx, sh, sp, st));
+    for (int j = 0; j < ctx->dnum; ++j) {
+        CK(launch_key_a_fill(ctx, seed, j, 1, aj, st));
+        CK(launch_signed_to_res(ctx, e + size_t(j) * N, eh, st));
+        RC(run_ntt(ctx, le, false, st));
+        CK(launch_keygen_row(ctx, aj, sh, sp, eh, j, nullptr, key_b + size_t(j) * LK * N, st));
+    }
+    return CKKS_OK;
+}
+
+extern "C" int ckks_ksk_expand(ckks_ctx *ctx, const uint64_t *key_b, uint64_t seed, uint64_t *key,
+                               ckks_stream_t stream) {
+    if (ctx == nullptr || !al16(key_b) || !al16(key) || key_b == key) return CKKS_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t row = size_t(ctx->L + ctx->k) * ctx->N;
+    for (int j = 0; j < ctx->dnum; ++j) {
+        CK(launch_key_a_fill(ctx, seed, j, 1, key + size_t(2 * j) * row, st));
+        CK(cudaMemcpyAsync(key + size_t(2 * j + 1) * row, key_b + size_t(j) * row, row * sizeof(u64),
+                           cudaMemcpyDeviceToDevice, st));
     }
     return CKKS_OK;
 }

@@ -82,7 +82,9 @@ struct CtDesc {
     u64 *ra, *rb;  // Rescale outputs [ell-1][N] (Mult entries), else null
     int ell;
     uint32_t galois;
-    int merged;    // NewMult entry
+    int merged;      // NewMult entry
+    int compressed;  // key holds only the b rows [dnum][L+k][N]; a is regenerated from seed
+    u64 seed;
 };
 
 struct KsBatchDesc {

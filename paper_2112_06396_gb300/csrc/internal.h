@@ -103,6 +103,7 @@ struct InnerArgs {
 cudaError_t launch_inner_prod(const ckks_ctx *ctx, const InnerArgs &a, cudaStream_t st);
 cudaError_t launch_inner_prod_batch(const ckks_ctx *ctx, const KsBatchDesc &d, cudaStream_t st);
 cudaError_t launch_tensor(const ckks_ctx *ctx, const TensorBatch &T, cudaStream_t st);
+cudaError_t launch_key_a_fill(const ckks_ctx *ctx, u64 seed, int j0, int ndig, u64 *dst, cudaStream_t st);
 
 // ---- batch executor (abi.cu), shared with the serving loop (serve.cu)
 enum { BE_KEYSWITCH = 0, BE_HROTATE = 1, BE_MULT = 2, BE_NEWMULT = 3 };
@@ -115,6 +116,8 @@ struct BatchEntry {
     int ell;
     uint32_t galois;     // HRotate
     u64 *ws;             // this entry's workspace (entry_ws_words), or null: packed
+    int compressed;      // key = b rows only [dnum][L+k][N], a regenerated from seed
+    u64 seed;
 };
 size_t entry_ws_words(const ckks_ctx *c, int kind, int ell);
 int run_batch(ckks_ctx *ctx, int n, const BatchEntry *e, u64 *w, cudaStream_t st);

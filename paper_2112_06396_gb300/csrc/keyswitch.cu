@@ -10,6 +10,7 @@
 #include "batch.cuh"
 #include "common.cuh"
 #include "internal.h"
+#include "prng.cuh"
 
 #include <algorithm>
 
@@ -163,8 +164,24 @@ __global__ void __launch_bounds__(256) inner_prod_batch_kernel(const __grid_cons
                 const bool own = t < ell && (t / alpha) == j;
                 const u64 *src = own ? ct.a + size_t(t) * N : lo.extp + (size_t(j) * lo.ext + t) * N;
                 dv[j] = ld2_perm(src, n0, g, logN);
-                ka[j] = ld2(key + ((size_t(j) * 2 + 0) * LK + pi) * N + n0);
-                kb[j] = ld2(key + ((size_t(j) * 2 + 1) * LK + pi) * N + n0);
+                if (ct.compressed) {
+                    kb[j] = ld2(key + (size_t(j) * LK + pi) * N + n0);
+                } else {
+                    ka[j] = ld2(key + ((size_t(j) * 2 + 0) * LK + pi) * N + n0);
+                    kb[j] = ld2(key + ((size_t(j) * 2 + 1) * LK + pi) * N + n0);
+                }
+            }
+        }
+        if (ct.compressed) {
+            // the key's uniform half, regenerated while the loads are in flight
+            const u64 q = pinfo[pi].p;
+            const int shift = __clzll(q);
+#pragma unroll
+            for (int j = 0; j < BMAX; j++) {
+                if (j < beta) {
+                    const u64 e = (u64(j) * LK + pi) * N + n0;
+                    ka[j] = make_ulonglong2(key_a_element(ct.seed, e, q, shift), key_a_element(ct.seed, e + 1, q, shift));
+                }
             }
         }
 #pragma unroll
@@ -177,12 +194,21 @@ __global__ void __launch_bounds__(256) inner_prod_batch_kernel(const __grid_cons
             }
         }
     } else {
+        const u64 q = pinfo[pi].p;
+        const int shift = __clzll(q);
         for (int j = 0; j < beta; j++) {
             const bool own = t < ell && (t / alpha) == j;
             const u64 *src = own ? ct.a + size_t(t) * N : lo.extp + (size_t(j) * lo.ext + t) * N;
             const ulonglong2 dv = ld2_perm(src, n0, g, logN);
-            const ulonglong2 a2 = ld2(key + ((size_t(j) * 2 + 0) * LK + pi) * N + n0);
-            const ulonglong2 b2 = ld2(key + ((size_t(j) * 2 + 1) * LK + pi) * N + n0);
+            ulonglong2 a2, b2;
+            if (ct.compressed) {
+                const u64 e = (u64(j) * LK + pi) * N + n0;
+                a2 = make_ulonglong2(key_a_element(ct.seed, e, q, shift), key_a_element(ct.seed, e + 1, q, shift));
+                b2 = ld2(key + (size_t(j) * LK + pi) * N + n0);
+            } else {
+                a2 = ld2(key + ((size_t(j) * 2 + 0) * LK + pi) * N + n0);
+                b2 = ld2(key + ((size_t(j) * 2 + 1) * LK + pi) * N + n0);
+            }
             mac128(ul0, uh0, dv.x, a2.x);
             mac128(ul1, uh1, dv.y, a2.y);
             mac128(vl0, vh0, dv.x, b2.x);
@@ -255,6 +281,27 @@ cudaError_t launch_tensor(const ckks_ctx *ctx, const TensorBatch &T, cudaStream_
     dim3 grid(unsigned(T.n), unsigned((ctx->N / 2 + threads - 1) / threads), unsigned(maxell));
     ProfScope ps(ctx, K_ELEMWISE, units, st);
     tensor_kernel<<<grid, threads, 0, st>>>(T, ctx->d_pinfo);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ compressed keys
+// a[(j*(L+k) + l)*N + n] for digits j0 .. j0+gridDim.z-1, written at
+// dst + ((j - j0)*(L+k) + l)*N + n: the key half regenerated from the seed.
+__global__ void __launch_bounds__(256) key_a_fill_kernel(u64 seed, int j0, u64 *__restrict__ dst,
+                                                         const PrimeInfo *__restrict__ pinfo, int logN, int LK) {
+    const size_t N = size_t(1) << logN;
+    const size_t n = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int l = blockIdx.y, j = j0 + int(blockIdx.z);
+    const u64 q = pinfo[l].p;
+    dst[(size_t(blockIdx.z) * LK + l) * N + n] = key_a_element(seed, (u64(j) * LK + l) * N + n, q, __clzll(q));
+}
+
+cudaError_t launch_key_a_fill(const ckks_ctx *ctx, u64 seed, int j0, int ndig, u64 *dst, cudaStream_t st) {
+    const int threads = 256;
+    dim3 grid(unsigned((ctx->N + threads - 1) / threads), unsigned(ctx->L + ctx->k), unsigned(ndig));
+    ProfScope ps(ctx, K_ELEMWISE, double(ctx->L + ctx->k) * ndig, st);
+    key_a_fill_kernel<<<grid, threads, 0, st>>>(seed, j0, dst, ctx->d_pinfo, ctx->logN, ctx->L + ctx->k);
     return cudaGetLastError();
 }
 
@@ -443,7 +490,7 @@ __global__ void keygen_row_kernel(const u64 *__restrict__ a, const u64 *__restri
         const ulonglong2 c = Pmod[l];
         b = add_mod(b, shoup_mul(sp[o], c.x, c.y, P.p), P.p);
     }
-    row0[o] = av;
+    if (row0 != nullptr) row0[o] = av;  // null: compressed key, only b is kept
     row1[o] = b;
 }
 

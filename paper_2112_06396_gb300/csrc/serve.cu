@@ -35,6 +35,8 @@ struct ckks_server {
     struct Key {
         int ctx;
         const u64 *ptr;
+        int compressed;
+        u64 seed;
     };
     std::vector<Key> keys;
     void *arena = nullptr;
@@ -125,15 +127,25 @@ extern "C" int ckks_server_destroy(ckks_server *s) {
     return CKKS_OK;
 }
 
-extern "C" int ckks_server_add_key(ckks_server *s, int ctx, const uint64_t *d_key, int *handle) {
+static int add_key(ckks_server *s, int ctx, const uint64_t *d_key, int compressed, u64 seed, int *handle) {
     if (s == nullptr || handle == nullptr || ctx < 0 || ctx >= int(s->ctxs.size()) || !al16(d_key))
         return CKKS_EINVAL;
     const ckks_ctx *c = s->ctxs[size_t(ctx)];
-    const size_t bytes = size_t(c->dnum) * 2 * (c->L + c->k) * c->N * sizeof(u64);
+    if (compressed && !c->split_bits) return CKKS_EUNSUPPORTED;
+    const size_t bytes = size_t(c->dnum) * (compressed ? 1 : 2) * (c->L + c->k) * c->N * sizeof(u64);
     if (!s->sched->add_resident(bytes)) return CKKS_ENOMEM;
-    s->keys.push_back({ctx, d_key});
+    s->keys.push_back({ctx, d_key, compressed, seed});
     *handle = int(s->keys.size()) - 1;
     return CKKS_OK;
+}
+
+extern "C" int ckks_server_add_key(ckks_server *s, int ctx, const uint64_t *d_key, int *handle) {
+    return add_key(s, ctx, d_key, 0, 0, handle);
+}
+
+extern "C" int ckks_server_add_key_seeded(ckks_server *s, int ctx, const uint64_t *d_key_b, uint64_t seed,
+                                          int *handle) {
+    return add_key(s, ctx, d_key_b, 1, seed, handle);
 }
 
 extern "C" double ckks_server_now_ms(const ckks_server *s) { return s ? host_ms(s) : 0.0; }
@@ -227,6 +239,8 @@ extern "C" int ckks_server_step(ckks_server *s, int *n_launched) {
             be.a2 = r.a2;
             be.b2 = r.b2;
             be.key = s->keys[size_t(r.key)].ptr;
+            be.compressed = s->keys[size_t(r.key)].compressed;
+            be.seed = s->keys[size_t(r.key)].seed;
             be.oa = r.oa;
             be.ob = r.ob;
             be.ell = r.level;
