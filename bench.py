@@ -219,6 +219,21 @@ def measure_batched(ctx, ckks, torch, reps=5):
             torch.cuda.current_stream().wait_stream(st)
 
     t_four = _timed(torch, four, reps)
+    # the batched call captured once in a CUDA graph and replayed
+    gst = torch.cuda.Stream()
+    with torch.cuda.stream(gst):
+        ctx.keyswitch_batch(a, None, levels, None, keys, outs=outs, ws=ws, stream=gst)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=gst):
+        ctx.keyswitch_batch(a, None, levels, None, keys, outs=outs, ws=ws, stream=gst)
+    t_graph = _timed(torch, graph.replay, reps)
+    # the same batch with the key compressed (rows b only; a regenerated from a seed)
+    seed = synth.stream_seed("bench/batch/seed")
+    e_key = np.stack([synth.gaussian(N, f"bench/batch/key/e{j}") for j in range(DNUM)])
+    key_b = ctx.keygen_ksk_seeded(s, dev(e_key), seed, 0)
+    t_comp = _timed(torch, lambda: ctx.keyswitch_batch(a, None, levels, None, [key_b] * len(levels), outs=outs,
+                                                       ws=ws, seeds=[seed] * len(levels)), reps)
     ctx.profile(True)
     ctx.profile_reset()
     ctx.keyswitch_batch(a, None, levels, None, keys, outs=outs, ws=ws)
@@ -227,13 +242,17 @@ def measure_batched(ctx, ckks, torch, reps=5):
     ctx.profile(False)
     comp = traffic.compulsory_batch_keyswitch_bytes(N, levels, [0] * len(levels), K_SP, L, DNUM)
     n = len(levels)
-    del a, outs, ws, ws1, ws4
+    key_b_bytes = key_b.numel() * 8
+    del a, outs, ws, ws1, ws4, graph, key_b
     torch.cuda.empty_cache()
     return {"shape": "64 KeySwitch, ell uniform in {4..24} (seeded), N=2^16, k=8, dnum=3, one shared key",
             "levels_sum": sum(levels),
             "batched": {"ms_per_batch": t_batch, "keyswitch_per_s": n / t_batch * 1e3,
                         "launches": sum(v[1] for v in prof.values()),
                         "kernel_ms": {k: v[0] for k, v in prof.items() if v[1]}},
+            "graph_replay": {"ms_per_batch": t_graph, "keyswitch_per_s": n / t_graph * 1e3},
+            "compressed_key": {"ms_per_batch": t_comp, "keyswitch_per_s": n / t_comp * 1e3,
+                               "key_bytes": key_b_bytes},
             "serial_one_stream": {"ms_per_batch": t_serial, "keyswitch_per_s": n / t_serial * 1e3},
             "four_streams": {"ms_per_batch": t_four, "keyswitch_per_s": n / t_four * 1e3},
             "speedup_vs_serial": t_serial / t_batch,
@@ -367,7 +386,7 @@ def measure_other_rows(ctx, ckks, torch, reps=5):
 
 def ntt_source_hash():
     h = hashlib.sha256()
-    for f in ("ntt.cu", "common.cuh"):
+    for f in ("ntt.cu", "common.cuh", "batch.cuh"):
         with open(os.path.join(ROOT, "paper_2112_06396_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -449,6 +468,10 @@ def run_gpu(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     primes = ckks.ckks_gen_primes(BITS, LOGN, L + K_SP)
     ctx = ckks.Context(LOGN, primes[:L], primes[L:], DNUM, device=local_rank)
+    tune_choice, tune_times = [0, 0, 0, 0], []
+    if not args.no_tune:
+        tune_choice, tune_times = ctx.autotune(limbs=128)  # NTT tile shapes for this GPU (ckks_autotune)
+    torch.cuda.synchronize()
     C = args.batch
     items = make_workload(ctx, C, rank, torch)
     lanes = Lanes(ctx, args.streams, torch, ckks)
@@ -562,7 +585,10 @@ def run_gpu(args, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded residues; keys from a seeded ternary secret)",
-            "config": {**base_config(C), "parallelism": f"replicas x{world}"},
+            "config": {**base_config(C), "parallelism": f"replicas x{world}",
+                       "ntt_tile_shapes": {"choice": tune_choice, "ms": [round(t, 4) for t in tune_times],
+                                           "legend": "[column pass <=48 limbs, column pass larger, block pass <=48, "
+                                                     "block pass larger]; 0 default width, 1 half, 2 double"}},
             "clocks": clk, "gpu_launches": int(round(launches_per_step * args.steps)),
             "wall_s_timed": t_wall,
             "hbm": {"compulsory_bytes_per_keyswitch": ks_bytes,
@@ -608,6 +634,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-rows", action="store_true", help="skip the Rescale / PtMatVecMult side measurements")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default NTT tile shapes (no autotuning)")
     args = ap.parse_args()
     global STREAMS
     STREAMS = args.streams

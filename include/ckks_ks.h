@@ -279,6 +279,22 @@ int ckks_keyswitch_batch_seeded(ckks_ctx *ctx, int n, const uint64_t *const *d_a
                                 const uint64_t *seeds, uint64_t *const *d_oa, uint64_t *const *d_ob, void *ws,
                                 ckks_stream_t stream);
 
+/* NTT autotuner (no counterpart in the paper).  Each NTT pass (the column
+ * pass and the block pass of the two-pass transform) exists in three tile
+ * shapes (CTA widths: the default, half, double) for logN >= 14 with primes
+ * below 2^57.  ckks_autotune times every shape, forward and inverse, on 24
+ * limbs and on min(128, ws_bytes / (8N)) limbs of the workspace (zeroed, then
+ * transformed in place), synchronises the stream, and keeps the fastest shape
+ * per pass and per launch size (<= 48 limbs, larger) in the context.
+ * choice (optional, 4 ints): [column pass small, column pass large, block pass
+ * small, block pass large], 0 = default, 1 = half width, 2 = double width.
+ * times (optional, 12 floats): ms per forward+inverse pass for
+ * [(pass * 2 + size class) * 3 + shape], the order of choice.  ckks_tune_set applies a saved
+ * choice.  Results are identical for every shape; only the speed changes.
+ * Contexts outside the tuned range keep the default (choice all 0). */
+int ckks_autotune(ckks_ctx *ctx, void *ws, size_t ws_bytes, ckks_stream_t stream, int *choice, float *times);
+int ckks_tune_set(ckks_ctx *ctx, const int *choice);
+
 /* ------------------------------------------------------------------------
  * Serving loop (no counterpart in the paper; it serves the paper's operations).
  * A server owns one device arena for request workspace and nstreams CUDA

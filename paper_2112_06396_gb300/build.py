@@ -15,7 +15,10 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libckks_ks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
+# -split-compile=0: device code of a translation unit is optimised on all host
+# threads (the NTT unit holds one kernel per ring degree, pass, tile shape and
+# limb mapping)
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-split-compile=0"]
 
 
 def nvcc() -> str:

@@ -93,6 +93,8 @@ _SIGS = {
     "ckks_server_create": (_i, [ctypes.POINTER(_vp), _i, ctypes.c_size_t, _i, _i, ctypes.POINTER(_vp)]),
     "ckks_server_destroy": (_i, [_vp]),
     "ckks_server_add_key": (_i, [_vp, _i, _vp, ctypes.POINTER(_i)]),
+    "ckks_autotune": (_i, [_vp, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_float)]),
+    "ckks_tune_set": (_i, [_vp, ctypes.POINTER(_i)]),
     "ckks_server_add_key_seeded": (_i, [_vp, _i, _vp, ctypes.c_uint64, ctypes.POINTER(_i)]),
     "ckks_keygen_ksk_seeded": (_i, [_vp, _vp, _vp, ctypes.c_uint64, ctypes.c_uint32, _vp, _vp, _vp]),
     "ckks_ksk_expand": (_i, [_vp, _vp, ctypes.c_uint64, _vp, _vp]),
@@ -225,6 +227,19 @@ class Context:
             _check(lib().ckks_profile_read(self._h, i, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(u)), self._h)
             out[name] = (ms.value, int(n.value), u.value)
         return out
+
+    def autotune(self, limbs=128, stream=None):
+        """Time the NTT tile shapes and keep the fastest (ckks_autotune).
+        Returns (choice[4], times_ms[12])."""
+        ws = torch.empty((limbs, self.N), dtype=torch.uint64, device=self.device)
+        ch = (_i * 4)()
+        tm = (ctypes.c_float * 12)()
+        _check(lib().ckks_autotune(self._h, _p(ws), limbs * self.N * 8, _stream(stream), ch, tm), self._h)
+        return list(ch), list(tm)
+
+    def tune_set(self, choice):
+        ch = (_i * 4)(*[int(x) for x in choice])
+        _check(lib().ckks_tune_set(self._h, ch))
 
     # ------------------------------------------------------------ memory
     def empty(self, nlimbs):

@@ -1231,6 +1231,30 @@ extern "C" int ckks_ksk_expand(ckks_ctx *ctx, const uint64_t *key_b, uint64_t se
     return CKKS_OK;
 }
 
+// ------------------------------------------------------------------ autotuner
+extern "C" int ckks_autotune(ckks_ctx *ctx, void *ws, size_t ws_bytes, ckks_stream_t stream, int *choice,
+                             float *times) {
+    if (ctx == nullptr || !al16(ws)) return CKKS_EINVAL;
+    const size_t limb = size_t(ctx->N) * sizeof(u64);
+    const int large = int(std::min<size_t>(kMaxBatch, ws_bytes / limb));
+    const int small = 24;
+    if (large < small) return CKKS_EINVAL;
+    if (times)
+        for (int i = 0; i < 12; ++i) times[i] = 0.f;
+    CK(ntt_autotune(ctx, static_cast<u64 *>(ws), small, large, (cudaStream_t)stream, times));
+    if (choice)
+        for (int i = 0; i < 4; ++i) choice[i] = ctx->ntt_csel[i / 2][i % 2];
+    return CKKS_OK;
+}
+
+extern "C" int ckks_tune_set(ckks_ctx *ctx, const int *choice) {
+    if (ctx == nullptr || choice == nullptr) return CKKS_EINVAL;
+    for (int i = 0; i < 4; ++i)
+        if (choice[i] < 0 || choice[i] > 2) return CKKS_EINVAL;
+    for (int i = 0; i < 4; ++i) ctx->ntt_csel[i / 2][i % 2] = choice[i];
+    return CKKS_OK;
+}
+
 // ------------------------------------------------------------------ measurement hook
 extern "C" int ckks_profile_enable(ckks_ctx *ctx, int on) {
     if (ctx == nullptr) return CKKS_EINVAL;

@@ -29,6 +29,9 @@ struct ckks_ctx {
     ulonglong2 *d_qlinv;              // [(L+1)*(L+k)]: [q_{ell-1}^-1]_{q_i} at ell*(L+k) + i
     ulonglong2 *d_Dinv;               // [(L+1)*(L+k)]: [(P q_{ell-1})^-1]_{q_i} at ell*(L+k) + i
     int last_cuda_error;
+    // NTT tile shape per pass (0 column, 1 block) and batch class (count <=
+    // kTuneSmallBatch, larger): 0 default width, 1 half, 2 double (ntt_autotune)
+    int ntt_csel[2][2] = {{0, 0}, {0, 0}};
     // measurement hook (ckks_profile_*): event pairs around every launch
     struct ProfRec {
         cudaEvent_t a, b;
@@ -87,6 +90,8 @@ cudaError_t ntt_set_attributes(const ckks_ctx *ctx);
 cudaError_t launch_ntt_fwd(const ckks_ctx *ctx, const NttBatch &b, const Epi *epi, cudaStream_t st);
 cudaError_t launch_ntt_inv(const ckks_ctx *ctx, const NttBatch &b, cudaStream_t st);
 cudaError_t launch_ntt_batch(const ckks_ctx *ctx, const KsBatchDesc &d, int phase, cudaStream_t st);
+constexpr int kTuneSmallBatch = 48;
+cudaError_t ntt_autotune(ckks_ctx *ctx, u64 *scratch, int small, int large, cudaStream_t st, float *times_out);
 cudaError_t launch_bconv(const ckks_ctx *ctx, const BConvLaunch &l, int max_src, cudaStream_t st);
 cudaError_t launch_bconv_batch(const ckks_ctx *ctx, const KsBatchDesc &d, int down, cudaStream_t st);
 

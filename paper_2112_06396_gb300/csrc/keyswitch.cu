@@ -137,7 +137,7 @@ cudaError_t launch_inner_prod(const ckks_ctx *ctx, const InnerArgs &a, cudaStrea
 // (position i), a special prime p_m to every entry (position ell + m); CTAs of
 // entries below a chain prime exit at once.  Each entry reads its own digits
 // through its own Galois element and writes its u, v into its workspace.
-template <int BMAX>
+template <int BMAX, bool COMP>
 __global__ void __launch_bounds__(256) inner_prod_batch_kernel(const __grid_constant__ KsBatchDesc d,
                                                                const PrimeInfo *__restrict__ pinfo,
                                                                const ulonglong2 *__restrict__ Pmod) {
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(256) inner_prod_batch_kernel(const __grid_cons
                 const bool own = t < ell && (t / alpha) == j;
                 const u64 *src = own ? ct.a + size_t(t) * N : lo.extp + (size_t(j) * lo.ext + t) * N;
                 dv[j] = ld2_perm(src, n0, g, logN);
-                if (ct.compressed) {
+                if (COMP && ct.compressed) {
                     kb[j] = ld2(key + (size_t(j) * LK + pi) * N + n0);
                 } else {
                     ka[j] = ld2(key + ((size_t(j) * 2 + 0) * LK + pi) * N + n0);
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(256) inner_prod_batch_kernel(const __grid_cons
                 }
             }
         }
-        if (ct.compressed) {
+        if (COMP && ct.compressed) {
             // the key's uniform half, regenerated while the loads are in flight
             const u64 q = pinfo[pi].p;
             const int shift = __clzll(q);
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(256) inner_prod_batch_kernel(const __grid_cons
             const u64 *src = own ? ct.a + size_t(t) * N : lo.extp + (size_t(j) * lo.ext + t) * N;
             const ulonglong2 dv = ld2_perm(src, n0, g, logN);
             ulonglong2 a2, b2;
-            if (ct.compressed) {
+            if (COMP && ct.compressed) {
                 const u64 e = (u64(j) * LK + pi) * N + n0;
                 a2 = make_ulonglong2(key_a_element(ct.seed, e, q, shift), key_a_element(ct.seed, e + 1, q, shift));
                 b2 = ld2(key + (size_t(j) * LK + pi) * N + n0);
@@ -236,13 +236,19 @@ cudaError_t launch_inner_prod_batch(const ckks_ctx *ctx, const KsBatchDesc &d, c
     const int threads = 256;
     dim3 grid(unsigned(d.n), unsigned((ctx->N / 2 + threads - 1) / threads), unsigned(ctx->L + ctx->k));
     ProfScope ps(ctx, K_INNER, units, st);
+    bool comp = false;
+    for (int c = 0; c < d.n; ++c) comp = comp || d.ct[c].compressed;
+#define CKKS_IPB(B)                                                                                                \
+    (comp ? inner_prod_batch_kernel<B, true><<<grid, threads, 0, st>>>(d, ctx->d_pinfo, ctx->d_Pmod)             \
+          : inner_prod_batch_kernel<B, false><<<grid, threads, 0, st>>>(d, ctx->d_pinfo, ctx->d_Pmod))
     switch (ctx->dnum) {
-    case 1: inner_prod_batch_kernel<1><<<grid, threads, 0, st>>>(d, ctx->d_pinfo, ctx->d_Pmod); break;
-    case 2: inner_prod_batch_kernel<2><<<grid, threads, 0, st>>>(d, ctx->d_pinfo, ctx->d_Pmod); break;
-    case 3: inner_prod_batch_kernel<3><<<grid, threads, 0, st>>>(d, ctx->d_pinfo, ctx->d_Pmod); break;
-    case 4: inner_prod_batch_kernel<4><<<grid, threads, 0, st>>>(d, ctx->d_pinfo, ctx->d_Pmod); break;
-    default: inner_prod_batch_kernel<0><<<grid, threads, 0, st>>>(d, ctx->d_pinfo, ctx->d_Pmod);
+    case 1: CKKS_IPB(1); break;
+    case 2: CKKS_IPB(2); break;
+    case 3: CKKS_IPB(3); break;
+    case 4: CKKS_IPB(4); break;
+    default: CKKS_IPB(0);
     }
+#undef CKKS_IPB
     return cudaGetLastError();
 }
 

@@ -286,7 +286,11 @@ ntt_pass_kernel(const __grid_constant__ MAP map, const PrimeInfo *__restrict__ p
 // ------------------------------------------------------------------ host side
 namespace {
 
-template <int LOGN, bool INV, bool CONTIG, bool EPI, bool SMALLP, class MAP>
+// CSEL picks the CTA width (the tile shape): 0 = the default below, 1 = half
+// of it, 2 = twice it.  The autotuner (ntt_autotune) chooses per pass and per
+// batch size; widths other than the default exist for logN >= 14 with small
+// primes (the key-switching shapes), elsewhere every CSEL maps to 0.
+template <int LOGN, bool INV, bool CONTIG, bool EPI, bool SMALLP, int CSEL, class MAP>
 cudaError_t launch_one_p(const MAP &m, int count, const ckks_ctx *ctx, cudaStream_t st, bool set_attr) {
     // pass S transforms columns of 2^L1 rows, pass C blocks of 2^L2 words
     constexpr int L2 = LOGN >> 1, L1 = LOGN - L2;
@@ -300,7 +304,8 @@ cudaError_t launch_one_p(const MAP &m, int count, const ckks_ctx *ctx, cudaStrea
     // for pass S, 64 for pass C, measured best at N=2^16) keep barriers local and
     // let many independent CTAs hide the load latency; clamped to the number of
     // columns / blocks of the matrix view
-    constexpr int WANT = (CONTIG ? 64 : 128) / TPC > 0 ? (CONTIG ? 64 : 128) / TPC : 1;
+    constexpr int BASE = (CONTIG ? 64 : 128) * (CSEL == 2 ? 2 : 1) / (CSEL == 1 ? 2 : 1);
+    constexpr int WANT = BASE / TPC > 0 ? BASE / TPC : 1;
     constexpr int C = WANT < (1 << OTHER) ? WANT : (1 << OTHER);
     const size_t smem = CONTIG ? size_t(C) * (R + TPC) * 8 : size_t(R) * C * 8 + size_t(R) * 16;
     auto kern = ntt_pass_kernel<LOGN, LOGR, A, C, INV, CONTIG, EPI, SMALLP, MAP>;
@@ -311,27 +316,39 @@ cudaError_t launch_one_p(const MAP &m, int count, const ckks_ctx *ctx, cudaStrea
 }
 
 template <int LOGN, bool INV, bool CONTIG, bool EPI, class MAP>
-cudaError_t launch_one(const MAP &m, int count, const ckks_ctx *ctx, cudaStream_t st, bool set_attr) {
+cudaError_t launch_one(const MAP &m, int count, const ckks_ctx *ctx, cudaStream_t st, bool set_attr, int csel) {
+    constexpr bool TUNED = LOGN >= 14;
     if (set_attr) {
-        cudaError_t e = launch_one_p<LOGN, INV, CONTIG, EPI, true>(m, count, ctx, st, true);
-        if (e != cudaSuccess) return e;
-        return launch_one_p<LOGN, INV, CONTIG, EPI, false>(m, count, ctx, st, true);
+        cudaError_t e = launch_one_p<LOGN, INV, CONTIG, EPI, false, 0>(m, count, ctx, st, true);
+        if (e == cudaSuccess) e = launch_one_p<LOGN, INV, CONTIG, EPI, true, 0>(m, count, ctx, st, true);
+        if (TUNED && e == cudaSuccess) e = launch_one_p<LOGN, INV, CONTIG, EPI, true, TUNED ? 1 : 0>(m, count, ctx, st, true);
+        if (TUNED && e == cudaSuccess) e = launch_one_p<LOGN, INV, CONTIG, EPI, true, TUNED ? 2 : 0>(m, count, ctx, st, true);
+        return e;
     }
-    if (ctx->small_primes) return launch_one_p<LOGN, INV, CONTIG, EPI, true>(m, count, ctx, st, false);
-    return launch_one_p<LOGN, INV, CONTIG, EPI, false>(m, count, ctx, st, false);
+    if (!ctx->small_primes) return launch_one_p<LOGN, INV, CONTIG, EPI, false, 0>(m, count, ctx, st, false);
+    if (TUNED && csel == 1) return launch_one_p<LOGN, INV, CONTIG, EPI, true, TUNED ? 1 : 0>(m, count, ctx, st, false);
+    if (TUNED && csel == 2) return launch_one_p<LOGN, INV, CONTIG, EPI, true, TUNED ? 2 : 0>(m, count, ctx, st, false);
+    return launch_one_p<LOGN, INV, CONTIG, EPI, true, 0>(m, count, ctx, st, false);
+}
+
+// The tuned width of a pass for a launch of `count` limbs (-1: use the table).
+inline int csel_for(const ckks_ctx *ctx, bool contig, int count, int force) {
+    if (force >= 0) return force;
+    return ctx->ntt_csel[contig ? 1 : 0][count > kTuneSmallBatch ? 1 : 0];
 }
 
 template <bool INV, bool CONTIG, bool EPI, class MAP>
-cudaError_t dispatch(const MAP &m, int count, const ckks_ctx *ctx, cudaStream_t st, bool set_attr) {
+cudaError_t dispatch(const MAP &m, int count, const ckks_ctx *ctx, cudaStream_t st, bool set_attr, int force = -1) {
+    const int cs = csel_for(ctx, CONTIG, count, force);
     switch (ctx->logN) {
-    case 10: return launch_one<10, INV, CONTIG, EPI>(m, count, ctx, st, set_attr);
-    case 11: return launch_one<11, INV, CONTIG, EPI>(m, count, ctx, st, set_attr);
-    case 12: return launch_one<12, INV, CONTIG, EPI>(m, count, ctx, st, set_attr);
-    case 13: return launch_one<13, INV, CONTIG, EPI>(m, count, ctx, st, set_attr);
-    case 14: return launch_one<14, INV, CONTIG, EPI>(m, count, ctx, st, set_attr);
-    case 15: return launch_one<15, INV, CONTIG, EPI>(m, count, ctx, st, set_attr);
-    case 16: return launch_one<16, INV, CONTIG, EPI>(m, count, ctx, st, set_attr);
-    case 17: return launch_one<17, INV, CONTIG, EPI>(m, count, ctx, st, set_attr);
+    case 10: return launch_one<10, INV, CONTIG, EPI>(m, count, ctx, st, set_attr, cs);
+    case 11: return launch_one<11, INV, CONTIG, EPI>(m, count, ctx, st, set_attr, cs);
+    case 12: return launch_one<12, INV, CONTIG, EPI>(m, count, ctx, st, set_attr, cs);
+    case 13: return launch_one<13, INV, CONTIG, EPI>(m, count, ctx, st, set_attr, cs);
+    case 14: return launch_one<14, INV, CONTIG, EPI>(m, count, ctx, st, set_attr, cs);
+    case 15: return launch_one<15, INV, CONTIG, EPI>(m, count, ctx, st, set_attr, cs);
+    case 16: return launch_one<16, INV, CONTIG, EPI>(m, count, ctx, st, set_attr, cs);
+    case 17: return launch_one<17, INV, CONTIG, EPI>(m, count, ctx, st, set_attr, cs);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -426,6 +443,71 @@ cudaError_t launch_ntt_batch(const ckks_ctx *ctx, const KsBatchDesc &d, int phas
     if (count == 0) return cudaSuccess;
     if (phase == PH_INTT_A || phase == PH_INTT_P || phase == PH_RS_INTT) return run_inv(m, count, ctx, st);
     return run_fwd(m, count, phase == PH_NTT_DOWN || phase == PH_RS_NTT, ctx, st);
+}
+
+// ------------------------------------------------------------------ autotuner
+// Times every CTA width of the column pass (S) and the block pass (C), forward
+// and inverse together, on `small` and `large` limbs of scratch data (in
+// place, values are transformed and transformed back), and keeps the fastest
+// per pass and batch-size class in the context.  scratch: at least
+// large * N words.  Returns the chosen widths through ctx->ntt_csel.
+cudaError_t ntt_autotune(ckks_ctx *ctx, u64 *scratch, int small, int large, cudaStream_t st, float *times_out) {
+    if (ctx->logN < 14 || !ctx->small_primes) return cudaSuccess;  // one width only
+    cudaEvent_t e0, e1;
+    cudaError_t err = cudaEventCreate(&e0);
+    if (err != cudaSuccess) return err;
+    if ((err = cudaEventCreate(&e1)) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return err;
+    }
+    const bool prof = ctx->prof_on;
+    ctx->prof_on = false;
+    err = cudaMemsetAsync(scratch, 0, size_t(large) * ctx->N * sizeof(u64), st);
+    const int counts[2] = {small, large};
+    for (int bucket = 0; bucket < 2 && err == cudaSuccess; ++bucket) {
+        const int count = counts[bucket];
+        MapList m{};
+        m.b.count = count;
+        for (int l = 0; l < count; ++l) {
+            m.b.src[l] = scratch + size_t(l) * ctx->N;
+            m.b.dst[l] = scratch + size_t(l) * ctx->N;
+            m.b.prime[l] = uint16_t(l % (ctx->L + ctx->k));
+        }
+        m.e.mode = EPI_STORE;
+        for (int contig = 0; contig < 2 && err == cudaSuccess; ++contig) {
+            float best = 1e30f;
+            int pick = 0;
+            for (int cs = 0; cs < 3 && err == cudaSuccess; ++cs) {
+                auto run = [&]() {
+                    m.second = 1;
+                    cudaError_t e2 = contig ? dispatch<false, true, false>(m, count, ctx, st, false, cs)
+                                            : dispatch<false, false, false>(m, count, ctx, st, false, cs);
+                    if (e2 == cudaSuccess)
+                        e2 = contig ? dispatch<true, true, false>(m, count, ctx, st, false, cs)
+                                    : dispatch<true, false, false>(m, count, ctx, st, false, cs);
+                    return e2;
+                };
+                err = run();  // warm-up
+                if (err != cudaSuccess) break;
+                cudaEventRecord(e0, st);
+                for (int r = 0; r < 5 && err == cudaSuccess; ++r) err = run();
+                cudaEventRecord(e1, st);
+                if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (err == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+                if (times_out) times_out[(contig * 2 + bucket) * 3 + cs] = ms / 5;
+                if (ms < best) {
+                    best = ms;
+                    pick = cs;
+                }
+            }
+            ctx->ntt_csel[contig][bucket] = pick;
+        }
+    }
+    ctx->prof_on = prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return err;
 }
 
 }  // namespace ckks

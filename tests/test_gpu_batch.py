@@ -144,3 +144,31 @@ def test_batch_64_uneven_levels_headline_shape(cfgB):
     outs2 = ctx.keyswitch_batch(da, None, levels, None, [dkey] * 64)
     for (u1, v1), (u2, v2) in zip(outs, outs2):
         assert torch.equal(u1, u2) and torch.equal(v1, v2)
+
+
+def test_batch_captured_in_a_cuda_graph(cfg1):
+    """The batched call launches only kernels on the caller's stream (no
+    allocation, no synchronisation), so it can be captured once in a CUDA graph
+    and replayed; the replay gives the same bits as the direct call."""
+    S = cfg1
+    levels = [6, 2, 5, 3, 6, 1]
+    key = dev(S.key(0, "gpu/graph/key")[0])
+    a = [dev(S.ct(ell, f"gpu/graph/{i}")[0]) for i, ell in enumerate(levels)]
+    want = S.ctx.keyswitch_batch(a, None, levels, None, [key] * len(levels))
+    outs = [(S.ctx.empty(ell), S.ctx.empty(ell)) for ell in levels]
+    ws = S.ctx.batch_workspace(levels)
+    st = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(st):
+        S.ctx.keyswitch_batch(a, None, levels, None, [key] * len(levels), outs=outs, ws=ws, stream=st)  # warm-up
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        S.ctx.keyswitch_batch(a, None, levels, None, [key] * len(levels), outs=outs, ws=ws, stream=st)
+    for o in outs:
+        o[0].zero_()
+        o[1].zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    for (ga, gb), (wa, wb) in zip(outs, want):
+        assert torch.equal(ga, wa) and torch.equal(gb, wb)
