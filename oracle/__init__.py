@@ -85,6 +85,9 @@ def _load():
                 "or_mult": (ctypes.c_int, [P, ctypes.c_int, u64p, u64p, u64p, u64p, u64p, u64p, u64p]),
                 "or_newmult": (ctypes.c_int, [P, ctypes.c_int, u64p, u64p, u64p, u64p, u64p, u64p, u64p]),
                 "or_moddown_merged": (ctypes.c_int, [P, ctypes.c_int, u64p, u64p]),
+                "or_newmult_sum": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(u64p),
+                                                  ctypes.POINTER(u64p), ctypes.POINTER(u64p), ctypes.POINTER(u64p),
+                                                  u64p, u64p, u64p]),
                 "or_prng_key_a": (ctypes.c_uint64, [P, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_uint64]),
                 "or_prng_key_a_fill": (ctypes.c_int, [P, ctypes.c_uint64, u64p]),
                 "or_hrotate": (ctypes.c_int, [P, ctypes.c_int, u64p, u64p, ctypes.c_int, u64p,
@@ -285,6 +288,25 @@ def newmult(P: Params, ell, a1, b1, a2, b2, key):
     ob = np.zeros_like(oa)
     if _load().or_newmult(P.c, ell, *[_u(x) for x in c], _u(oa), _u(ob)) != 0:
         raise ValueError("newmult needs ell >= 2")
+    return oa, ob
+
+
+def newmult_sum(P: Params, ell, cts1, cts2, key):
+    """Sum of NewMult over pairs with one merged ModDown (Sec. 5.1); cts: lists of (a, b)."""
+    keep = []
+
+    def arr(xs):
+        xs = [np.ascontiguousarray(x, dtype=np.uint64) for x in xs]
+        keep.extend(xs)
+        return _ptr_array(xs)
+
+    key = np.ascontiguousarray(key, dtype=np.uint64)
+    oa = np.zeros((ell - 1, P.N), dtype=np.uint64)
+    ob = np.zeros_like(oa)
+    rc = _load().or_newmult_sum(P.c, ell, len(cts1), arr([c[0] for c in cts1]), arr([c[1] for c in cts1]),
+                                arr([c[0] for c in cts2]), arr([c[1] for c in cts2]), _u(key), _u(oa), _u(ob))
+    if rc != 0:
+        raise ValueError("newmult_sum needs ell >= 2 and at least one pair")
     return oa, ob
 
 

@@ -589,6 +589,51 @@ int or_newmult(const or_params *P, int ell, const u64 *a1, const u64 *b1, const 
     return 0;
 }
 
+/* Encrypted inner product with the ModDown hoisted (Sec. 5.1, the consequence
+ * of Algorithm 7): sum over i < n of NewMult(ct1_i, ct2_i).  Each pair's lifted
+ * (u_hat_i + PModUp(b3_i), v_hat_i + PModUp(c3_i)) over C_ell U P is summed
+ * first, and one merged ModDown by P*q_{ell-1} per polynomial ends the sum.
+ * a1s..b2s: n pointers to [ell][N]; outputs [ell-1][N].  Needs ell >= 2. */
+int or_newmult_sum(const or_params *P, int ell, int n, const u64 *const *a1s, const u64 *const *b1s,
+                   const u64 *const *a2s, const u64 *const *b2s, const u64 *key, u64 *oa, u64 *ob) {
+    if (ell < 2 || n < 1) return -1;
+    size_t N = N_of(P), sz = (size_t)ell * N;
+    int beta = p_beta(P, ell), ext = ell + P->k;
+    u64 *su = (u64 *)calloc((size_t)ext * N, sizeof(u64)), *sv = (u64 *)calloc((size_t)ext * N, sizeof(u64));
+    u64 *a3 = (u64 *)malloc(sizeof(u64) * sz), *b3 = (u64 *)malloc(sizeof(u64) * sz);
+    u64 *c3 = (u64 *)malloc(sizeof(u64) * sz);
+    u64 *digits = (u64 *)malloc(sizeof(u64) * beta * ext * N);
+    u64 *uh = (u64 *)malloc(sizeof(u64) * ext * N), *vh = (u64 *)malloc(sizeof(u64) * ext * N);
+    u64 *bh = (u64 *)malloc(sizeof(u64) * ext * N), *ch = (u64 *)malloc(sizeof(u64) * ext * N);
+    for (int p = 0; p < n; p++) {
+        for (int i = 0; i < ell; i++) {
+            u64 q = P->primes[i];
+            for (size_t m = 0; m < N; m++) {
+                size_t o = (size_t)i * N + m;
+                a3[o] = mulmod(a1s[p][o], a2s[p][o], q);
+                b3[o] = addmod(mulmod(a1s[p][o], b2s[p][o], q), mulmod(a2s[p][o], b1s[p][o], q), q);
+                c3[o] = mulmod(b1s[p][o], b2s[p][o], q);
+            }
+        }
+        for (int j = 0; j < beta; j++) or_modup(P, ell, j, a3, digits + (size_t)j * ext * N);
+        or_ksk_inner_prod(P, ell, digits, key, uh, vh);
+        or_pmodup(P, ell, b3, bh);
+        or_pmodup(P, ell, c3, ch);
+        for (int t = 0; t < ext; t++) {
+            u64 pt = prime_at(P, ell, t);
+            for (size_t m = 0; m < N; m++) {
+                size_t o = (size_t)t * N + m;
+                su[o] = addmod(su[o], addmod(uh[o], bh[o], pt), pt);
+                sv[o] = addmod(sv[o], addmod(vh[o], ch[o], pt), pt);
+            }
+        }
+    }
+    or_moddown_merged(P, ell, su, oa);
+    or_moddown_merged(P, ell, sv, ob);
+    free(su); free(sv); free(a3); free(b3); free(c3); free(digits); free(uh); free(vh); free(bh); free(ch);
+    return 0;
+}
+
 /* Algorithm 3: automorph (a, b) first, key-switch a_rot, return (u, v + b_rot). */
 int or_rotate(const or_params *P, int ell, const u64 *a, const u64 *b, u64 g, const u64 *key, u64 *oa, u64 *ob) {
     size_t N = N_of(P);

@@ -231,3 +231,39 @@ def test_newmult_decrypts_to_rescaled_product(oracle_lib, logN, L, k, dnum, ell)
     # the same product as Algorithm 2 up to the two methods' error terms, but other bits
     ra, rb = oracle_lib.mult(P, ell, a1, b1, a2, b2, rlk)
     assert not (np.array_equal(ra, oa) and np.array_equal(rb, ob))
+
+
+@pytest.mark.parametrize("n,ell", [(3, 6), (2, 2)])
+def test_newmult_sum_decrypts_to_the_inner_product(oracle_lib, n, ell):
+    """The ModDown-hoisted encrypted inner product: one merged ModDown after the
+    sum of the n lifted products, so Dec(out) ~ sum_i m1_i*m2_i / q_{ell-1}
+    within n*E/(P q_{ell-1}) + (h_s+1)/2 + (k+1)(h_s+1) + 1; for n = 1 it is
+    NewMult bit for bit."""
+    P = params(oracle_lib, 6, 6, 3, 2)
+    s = synth.ternary(P.N, "pin/nmsum/s")
+    rlk = make_key(oracle_lib, P, s, oracle_lib.sq_secret(P, s), "pin/nmsum/rlk")
+    ql = int(P.primes[ell - 1])
+    delta = 1 << (ql.bit_length() // 2 + 4)
+    cts1, cts2, ms1, ms2 = [], [], [], []
+    for i in range(n):
+        for cts, ms, tag in ((cts1, ms1, "x"), (cts2, ms2, "y")):
+            m = delta * synth.small_uniform(P.N, f"pin/nmsum/{tag}{i}", 8) + synth.gaussian(P.N, f"pin/nmsum/e{tag}{i}")
+            a = synth.uniform_residues(P.primes[:ell], P.N, f"pin/nmsum/a{tag}{i}")
+            cts.append((a, oracle_lib.encrypt(P, ell, s, m, a)))
+            ms.append([int(v) for v in m])
+    oa, ob = oracle_lib.newmult_sum(P, ell, cts1, cts2, rlk)
+    got = decrypt_int(oracle_lib, P, ell - 1, s, oa, ob)
+    want = [0] * P.N
+    for m1, m2 in zip(ms1, ms2):
+        want = [w + v for w, v in zip(want, negacyclic_mul(m1, m2))]
+    hs = int(np.count_nonzero(s))
+    alpha, beta = P.alpha, P.beta(ell)
+    Pp = prod(int(x) for x in P.primes[P.L:])
+    qmax = max(prod(int(x) for x in P.primes[j * alpha:min((j + 1) * alpha, ell)]) for j in range(beta))
+    bound = n * beta * alpha * P.N * 19 * qmax / (Pp * ql) + (hs + 1) / 2 + (P.k + 1) * (hs + 1) + 1
+    assert max(abs(g * ql - t) for g, t in zip(got, want)) / ql <= bound
+    assert max(abs(t) for t in want) / ql > 100 * bound
+    one = oracle_lib.newmult_sum(P, ell, cts1[:1], cts2[:1], rlk)
+    ref = oracle_lib.newmult(P, ell, *cts1[0], *cts2[0], rlk)
+    np.testing.assert_array_equal(one[0], ref[0])
+    np.testing.assert_array_equal(one[1], ref[1])
