@@ -233,6 +233,20 @@ int ckks_newmult_batch(ckks_ctx *ctx, int n, const uint64_t *const *d_a1, const 
                        const uint64_t *const *d_keys, uint64_t *const *d_oa, uint64_t *const *d_ob, void *ws,
                        ckks_stream_t stream);
 
+/* Encrypted inner product with the ModDown hoisted (Sec. 5.1, a consequence of
+ * Algorithm 7): out = sum over i < n of NewMult((a1[i], b1[i]), (a2[i], b2[i]))
+ * computed with one merged ModDown for the whole sum: each pair's tensor step,
+ * ModUp and KSKInnerProd with PModUp(b3), PModUp(c3) added run as one batch,
+ * the n lifted (u, v) are summed over the extended basis, and one ModDown by
+ * P*q_{ell-1} per polynomial gives d_oa, d_ob [ell-1][N].  All pairs at
+ * `level` (>= 2) with one relinearisation key; 1 <= n <= 64.  For n = 1 the
+ * bits are those of ckks_newmult.  Workspace: ckks_newmult_batch_workspace_bytes
+ * with n copies of the level.  CKKS_EUNSUPPORTED for contexts without the split
+ * basis conversion or with k + 1 > 32. */
+int ckks_newmult_sum(ckks_ctx *ctx, int n, const uint64_t *const *d_a1, const uint64_t *const *d_b1,
+                     const uint64_t *const *d_a2, const uint64_t *const *d_b2, int level, const uint64_t *d_key,
+                     uint64_t *d_oa, uint64_t *d_ob, void *ws, ckks_stream_t stream);
+
 /* PtMatVecMult with hoisted ModUp and ModDown (Algorithm 8) in baby-step /
  * giant-step form (Sec. 5.2): nb baby steps, ng giant steps, diagonal (t, i) =
  * d_diag[t*nb + i], an [ell+k][N] evaluation-form plaintext over the extended

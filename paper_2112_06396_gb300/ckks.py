@@ -82,6 +82,8 @@ _SIGS = {
     "ckks_mult": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _vp, _vp, _vp, _vp, _vp]),
     "ckks_mult_batch_workspace_bytes": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_size_t)]),
     "ckks_newmult": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _vp, _vp, _vp, _vp, _vp]),
+    "ckks_newmult_sum": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                              ctypes.POINTER(_vp), _i, _vp, _vp, _vp, _vp, _vp]),
     "ckks_newmult_batch_workspace_bytes": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_size_t)]),
     "ckks_newmult_batch": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                 ctypes.POINTER(_vp), ctypes.POINTER(_i), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
@@ -424,6 +426,18 @@ class Context:
                   arr([c[1] for c in cts2]), lv, arr(keys), arr([o[0] for o in outs]), arr([o[1] for o in outs]),
                   _p(ws), _stream(stream)), self._h)
         return outs
+
+    def newmult_sum(self, cts1, cts2, level, key, oa=None, ob=None, ws=None, stream=None):
+        """Sum of NewMult products with one merged ModDown; cts: lists of (a, b) at one level."""
+        n = len(cts1)
+        oa = self.empty(level - 1) if oa is None else oa
+        ob = self.empty(level - 1) if ob is None else ob
+        ws = self.mult_batch_workspace([level] * n, new=True) if ws is None else ws
+        arr = lambda xs: (_vp * n)(*[x.data_ptr() for x in xs])
+        _check(lib().ckks_newmult_sum(self._h, n, arr([c[0] for c in cts1]), arr([c[1] for c in cts1]),
+                                      arr([c[0] for c in cts2]), arr([c[1] for c in cts2]), level, _p(key), _p(oa),
+                                      _p(ob), _p(ws), _stream(stream)), self._h)
+        return oa, ob
 
     def ptmatvecmult(self, a, b, level, nb, ng, g_baby, g_giant, key_baby, key_giant, diags, rescale=True,
                      oa=None, ob=None, ws=None, stream=None):

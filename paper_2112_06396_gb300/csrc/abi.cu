@@ -973,6 +973,30 @@ static int entry_one(ckks_ctx *ctx, const CtDesc &c, const TensorEntry *te, cuda
     return CKKS_OK;
 }
 
+// The steps of a batch up to the inner product: tensor step of the Mult
+// entries, iNTT of the inputs, ModUp conversion, NTT of the new limbs, KSKInnerProd.
+static int batch_front(ckks_ctx *ctx, const KsBatchDesc &d, const TensorBatch &T, cudaStream_t st) {
+    CK(launch_tensor(ctx, T, st));
+    CK(launch_ntt_batch(ctx, d, PH_INTT_A, st));
+    CK(launch_bconv_batch(ctx, d, GM_MODUP, st));
+    CK(launch_ntt_batch(ctx, d, PH_NTT_UP, st));
+    CK(launch_inner_prod_batch(ctx, d, st));
+    return CKKS_OK;
+}
+
+// The ModDown steps (and the Rescale of Mult entries).
+static int batch_back(ckks_ctx *ctx, const KsBatchDesc &d, bool rescale, cudaStream_t st) {
+    CK(launch_ntt_batch(ctx, d, PH_INTT_P, st));
+    CK(launch_bconv_batch(ctx, d, GM_MODDOWN, st));
+    CK(launch_ntt_batch(ctx, d, PH_NTT_DOWN, st));
+    if (rescale) {
+        CK(launch_ntt_batch(ctx, d, PH_RS_INTT, st));
+        CK(launch_bconv_batch(ctx, d, GM_RESCALE, st));
+        CK(launch_ntt_batch(ctx, d, PH_RS_NTT, st));
+    }
+    return CKKS_OK;
+}
+
 // Runs a batch in groups of kMaxCts entries.  An entry's workspace is its ws
 // when set, else the next entry_ws_words region of w (batch order).
 int ckks::run_batch(ckks_ctx *ctx, int n, const BatchEntry *e, u64 *w, cudaStream_t st) {
@@ -1004,19 +1028,8 @@ int ckks::run_batch(ckks_ctx *ctx, int n, const BatchEntry *e, u64 *w, cudaStrea
             continue;
         }
         // one launch per step over the whole batch
-        CK(launch_tensor(ctx, T, st));
-        CK(launch_ntt_batch(ctx, d, PH_INTT_A, st));
-        CK(launch_bconv_batch(ctx, d, GM_MODUP, st));
-        CK(launch_ntt_batch(ctx, d, PH_NTT_UP, st));
-        CK(launch_inner_prod_batch(ctx, d, st));
-        CK(launch_ntt_batch(ctx, d, PH_INTT_P, st));
-        CK(launch_bconv_batch(ctx, d, GM_MODDOWN, st));
-        CK(launch_ntt_batch(ctx, d, PH_NTT_DOWN, st));
-        if (T.n > 0) {
-            CK(launch_ntt_batch(ctx, d, PH_RS_INTT, st));
-            CK(launch_bconv_batch(ctx, d, GM_RESCALE, st));
-            CK(launch_ntt_batch(ctx, d, PH_RS_NTT, st));
-        }
+        RC(batch_front(ctx, d, T, st));
+        RC(batch_back(ctx, d, T.n > 0, st));
     }
     return CKKS_OK;
 }
@@ -1099,6 +1112,44 @@ extern "C" int ckks_newmult(ckks_ctx *ctx, const uint64_t *a1, const uint64_t *b
                             const uint64_t *b2, int level, const uint64_t *key, uint64_t *oa, uint64_t *ob, void *ws,
                             ckks_stream_t stream) {
     return ckks_newmult_batch(ctx, 1, &a1, &b1, &a2, &b2, &level, &key, &oa, &ob, ws, stream);
+}
+
+// Encrypted inner product with the ModDown hoisted (Sec. 5.1): the n NewMult
+// products are lifted and summed over the extended basis, then one merged
+// ModDown per polynomial.  All pairs at one level; workspace: n NewMult entries.
+extern "C" int ckks_newmult_sum(ckks_ctx *ctx, int n, const uint64_t *const *a1, const uint64_t *const *b1,
+                                const uint64_t *const *a2, const uint64_t *const *b2, int level,
+                                const uint64_t *key, uint64_t *oa, uint64_t *ob, void *ws, ckks_stream_t stream) {
+    if (ctx == nullptr || n < 1 || n > kMaxCts || !a1 || !b1 || !a2 || !b2 || !level_ok(ctx, level) || level < 2 ||
+        !al16(key) || !al16(oa) || !al16(ob) || !al16(ws))
+        return CKKS_EINVAL;
+    if (ctx->k + 1 > kMaxSrc || !ctx->split_bits) return CKKS_EUNSUPPORTED;
+    for (int i = 0; i < n; ++i)
+        if (!al16(a1[i]) || !al16(b1[i]) || !al16(a2[i]) || !al16(b2[i])) return CKKS_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    KsBatchDesc d{};
+    d.n = n;
+    d.L = ctx->L;
+    d.k = ctx->k;
+    d.alpha = ctx->alpha;
+    d.dnum = ctx->dnum;
+    d.logN = ctx->logN;
+    TensorBatch T;
+    T.n = 0;
+    T.logN = ctx->logN;
+    u64 *w = static_cast<u64 *>(ws);
+    for (int i = 0; i < n; ++i) {
+        const BatchEntry e{BE_NEWMULT, a1[i], b1[i], a2[i], b2[i], key, oa, ob, level, 1u, nullptr, 0, 0};
+        TensorEntry te{};
+        d.ct[i] = entry_desc(ctx, e, w, &te);
+        T.e[T.n++] = te;
+        w += entry_ws_words(ctx, BE_NEWMULT, level);
+    }
+    RC(batch_front(ctx, d, T, st));
+    if (n > 1) CK(launch_sum_uv(ctx, d, st));
+    KsBatchDesc d1 = d;
+    d1.n = 1;
+    return batch_back(ctx, d1, false, st);
 }
 
 extern "C" int ckks_mult(ckks_ctx *ctx, const uint64_t *a1, const uint64_t *b1, const uint64_t *a2,

@@ -109,6 +109,7 @@ cudaError_t launch_inner_prod(const ckks_ctx *ctx, const InnerArgs &a, cudaStrea
 cudaError_t launch_inner_prod_batch(const ckks_ctx *ctx, const KsBatchDesc &d, cudaStream_t st);
 cudaError_t launch_tensor(const ckks_ctx *ctx, const TensorBatch &T, cudaStream_t st);
 cudaError_t launch_key_a_fill(const ckks_ctx *ctx, u64 seed, int j0, int ndig, u64 *dst, cudaStream_t st);
+cudaError_t launch_sum_uv(const ckks_ctx *ctx, const KsBatchDesc &d, cudaStream_t st);
 
 // ---- batch executor (abi.cu), shared with the serving loop (serve.cu)
 enum { BE_KEYSWITCH = 0, BE_HROTATE = 1, BE_MULT = 2, BE_NEWMULT = 3 };

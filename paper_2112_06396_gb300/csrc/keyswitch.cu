@@ -290,6 +290,38 @@ cudaError_t launch_tensor(const ckks_ctx *ctx, const TensorBatch &T, cudaStream_
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ hoisted inner product
+// The lifted (u, v) of every entry of a batch summed into entry 0's, slot-wise
+// mod each prime of the extended basis (all entries at one level).  Grid
+// (coefficient tile, position of the 2(ell+k) limbs of u and v).
+__global__ void __launch_bounds__(256) sum_uv_kernel(const __grid_constant__ KsBatchDesc d,
+                                                     const PrimeInfo *__restrict__ pinfo) {
+    const size_t N = size_t(1) << d.logN;
+    const size_t n0 = (size_t(blockIdx.x) * blockDim.x + threadIdx.x) * 2;
+    if (n0 >= N) return;
+    const int ell = d.ct[0].ell, ext = ell + d.k;
+    const int y = blockIdx.y;  // poly * ext + t
+    const int t = y % ext;
+    const PrimeInfo P = pinfo[t < ell ? t : d.L + (t - ell)];
+    u64 s0 = 0, s1 = 0;  // n < 2^9 values below 2^55 each: no overflow
+    for (int c = 0; c < d.n; ++c) {
+        const CtLayout lo = ct_layout(d, d.ct[c]);
+        const ulonglong2 v = ld2(lo.uv + size_t(y) * N + n0);
+        s0 += v.x;
+        s1 += v.y;
+    }
+    const CtLayout l0 = ct_layout(d, d.ct[0]);
+    st2(l0.uv + size_t(y) * N + n0, make_ulonglong2(reduce128(s0, 0, P), reduce128(s1, 0, P)));
+}
+
+cudaError_t launch_sum_uv(const ckks_ctx *ctx, const KsBatchDesc &d, cudaStream_t st) {
+    const int threads = 256;
+    dim3 grid(unsigned((ctx->N / 2 + threads - 1) / threads), unsigned(2 * (d.ct[0].ell + ctx->k)));
+    ProfScope ps(ctx, K_ELEMWISE, 2.0 * (d.ct[0].ell + ctx->k) * d.n, st);
+    sum_uv_kernel<<<grid, threads, 0, st>>>(d, ctx->d_pinfo);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ compressed keys
 // a[(j*(L+k) + l)*N + n] for digits j0 .. j0+gridDim.z-1, written at
 // dst + ((j - j0)*(L+k) + l)*N + n: the key half regenerated from the seed.

@@ -100,3 +100,17 @@ def test_mult_headline_shape(oracle_lib):
         ra, rb = ref(S.P, 24, *cts, key)
         np.testing.assert_array_equal(host(oa), ra)
         np.testing.assert_array_equal(host(ob), rb)
+
+
+@pytest.mark.parametrize("n,ell", [(5, 7), (1, 4), (3, 2)])
+def test_newmult_sum_parity(cfg_odd, n, ell):
+    """Sum of n NewMult products with one merged ModDown against the oracle."""
+    S = cfg_odd
+    key = S.key(0, "gpu/nmsum/rlk")[0]
+    pairs = [_pair(S, ell, f"gpu/nmsum/{n}/{ell}/{i}") for i in range(n)]
+    c1 = [(dev(p[0]), dev(p[1])) for p in pairs]
+    c2 = [(dev(p[2]), dev(p[3])) for p in pairs]
+    oa, ob = S.ctx.newmult_sum(c1, c2, ell, dev(key))
+    ra, rb = S.o.newmult_sum(S.P, ell, [(p[0], p[1]) for p in pairs], [(p[2], p[3]) for p in pairs], key)
+    np.testing.assert_array_equal(host(oa), ra)
+    np.testing.assert_array_equal(host(ob), rb)
