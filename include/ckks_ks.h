@@ -282,12 +282,20 @@ int ckks_keygen_ksk(ckks_ctx *ctx, const int64_t *d_s, const int64_t *d_e, const
  *   key_b [dnum][L+k][N].  Workspace CKKS_OP_KEYGEN_SEEDED.
  * ckks_ksk_expand: the full key [dnum][2][L+k][N] of a compressed key.
  * ckks_keyswitch_batch_seeded: ckks_keyswitch_batch with compressed keys
- *   keys_b[i] and seeds[i]; same bits as the full keys (ckks_ksk_expand);
- *   contexts whose primes are too wide for the split basis conversion return
- *   CKKS_EUNSUPPORTED. */
+ *   keys_b[i] and seeds[i]; same bits as the full keys (ckks_ksk_expand). */
 int ckks_keygen_ksk_seeded(ckks_ctx *ctx, const int64_t *d_s, const int64_t *d_e, uint64_t seed, uint32_t galois,
                            uint64_t *d_key_b, void *ws, ckks_stream_t stream);
 int ckks_ksk_expand(ckks_ctx *ctx, const uint64_t *d_key_b, uint64_t seed, uint64_t *d_key, ckks_stream_t stream);
+/* ckks_key_register_seed records in the context that d_key_b is a compressed
+ * key with this seed; from then on every call of the context that takes a key
+ * (ckks_keyswitch, ckks_rotate, ckks_hrotate, ckks_ksk_inner_prod,
+ * ckks_ptmatvecmult, the batched calls, ckks_mult / ckks_newmult /
+ * ckks_newmult_sum, ckks_server_add_key) treats that pointer as a compressed key
+ * and regenerates its rows a_j on chip.  ckks_key_unregister forgets it.
+ * Host-side only (no device work); not thread-safe against concurrent calls on
+ * the same context. */
+int ckks_key_register_seed(ckks_ctx *ctx, const uint64_t *d_key_b, uint64_t seed);
+int ckks_key_unregister(ckks_ctx *ctx, const uint64_t *d_key_b);
 int ckks_keyswitch_batch_seeded(ckks_ctx *ctx, int n, const uint64_t *const *d_a, const uint64_t *const *d_b,
                                 const int *levels, const uint32_t *galois, const uint64_t *const *d_keys_b,
                                 const uint64_t *seeds, uint64_t *const *d_oa, uint64_t *const *d_ob, void *ws,

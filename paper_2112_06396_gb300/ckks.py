@@ -100,6 +100,8 @@ _SIGS = {
     "ckks_server_add_key_seeded": (_i, [_vp, _i, _vp, ctypes.c_uint64, ctypes.POINTER(_i)]),
     "ckks_keygen_ksk_seeded": (_i, [_vp, _vp, _vp, ctypes.c_uint64, ctypes.c_uint32, _vp, _vp, _vp]),
     "ckks_ksk_expand": (_i, [_vp, _vp, ctypes.c_uint64, _vp, _vp]),
+    "ckks_key_register_seed": (_i, [_vp, _vp, ctypes.c_uint64]),
+    "ckks_key_unregister": (_i, [_vp, _vp]),
     "ckks_keyswitch_batch_seeded": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_i),
                                          ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(_vp),
                                          ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
@@ -382,6 +384,13 @@ class Context:
         _check(lib().ckks_keygen_ksk_seeded(self._h, _p(s), _p(e), int(seed) & 0xFFFFFFFFFFFFFFFF, int(galois),
                                             _p(key_b), _p(ws), _stream(stream)), self._h)
         return key_b
+
+    def register_compressed_key(self, key_b, seed):
+        """Every call of this context that receives key_b treats it as a compressed key."""
+        _check(lib().ckks_key_register_seed(self._h, _p(key_b), int(seed) & 0xFFFFFFFFFFFFFFFF))
+
+    def unregister_compressed_key(self, key_b):
+        _check(lib().ckks_key_unregister(self._h, _p(key_b)))
 
     def ksk_expand(self, key_b, seed, key=None, stream=None):
         key = torch.empty((self.dnum, 2, self.L + self.k, self.N), dtype=torch.uint64,

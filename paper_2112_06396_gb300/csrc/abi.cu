@@ -426,6 +426,13 @@ extern "C" size_t ckks_ctx_table_bytes(const ckks_ctx *c) { return c ? c->table_
 static bool al16(const void *p) { return p != nullptr && (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 static bool level_ok(const ckks_ctx *c, int ell) { return c != nullptr && ell >= 1 && ell <= c->L; }
 static bool galois_ok(const ckks_ctx *c, uint32_t g) { return (g & 1u) && g < uint32_t(2 * c->N); }
+// A key pointer registered with ckks_key_register_seed is a compressed key.
+static bool key_seed(const ckks_ctx *c, const u64 *key, u64 *seed) {
+    const auto it = c->comp_keys.find(key);
+    if (it == c->comp_keys.end()) return false;
+    *seed = it->second;
+    return true;
+}
 
 // Launch forward (or inverse) NTTs over a list of limbs, in chunks of kMaxBatch.
 struct LimbList {
@@ -658,6 +665,7 @@ static int keyswitch_core(ckks_ctx *ctx, const u64 *a, int ell, const u64 *key, 
     u64 *u = ws + lo.uv, *v = u + size_t(ell + ctx->k) * N;
     RC(modup_all(ctx, a, ell, ws + lo.ext, ws + lo.acoeff, st));
     InnerArgs ia{ws + lo.ext, a, key, u, v, ell, gin};
+    ia.compressed = key_seed(ctx, key, &ia.seed);
     CK(launch_inner_prod(ctx, ia, st));
     const u64 *in[2] = {u, v};
     u64 *out[2] = {out0, out1};
@@ -794,6 +802,7 @@ extern "C" int ckks_ksk_inner_prod(ckks_ctx *ctx, const uint64_t *digits, int el
                                    uint64_t *v, ckks_stream_t stream) {
     if (!level_ok(ctx, ell) || !al16(digits) || !al16(key) || !al16(u) || !al16(v)) return CKKS_EINVAL;
     InnerArgs ia{digits, nullptr, key, u, v, ell, 1};
+    ia.compressed = key_seed(ctx, key, &ia.seed);
     CK(launch_inner_prod(ctx, ia, (cudaStream_t)stream));
     return CKKS_OK;
 }
@@ -853,6 +862,7 @@ extern "C" int ckks_hrotate(ckks_ctx *ctx, const uint64_t *a, const uint64_t *b,
     u64 *u = w + lo.uv, *v = u + size_t(ell + ctx->k) * N;
     for (int i = 0; i < r; ++i) {
         InnerArgs ia{w + lo.ext, a, keys[i], u, v, ell, galois[i]};
+        ia.compressed = key_seed(ctx, keys[i], &ia.seed);
         CK(launch_inner_prod(ctx, ia, st));
         const u64 *in[2] = {u, v};
         u64 *out[2] = {oa[i], ob[i]};
@@ -937,7 +947,6 @@ static CtDesc entry_desc(const ckks_ctx *ctx, const BatchEntry &e, u64 *ws, Tens
 // primes are too wide for the split basis conversion).
 static int entry_one(ckks_ctx *ctx, const CtDesc &c, const TensorEntry *te, cudaStream_t st) {
     const size_t N = ctx->N;
-    if (c.compressed) return CKKS_EUNSUPPORTED;  // compressed keys need the batched inner product
     if (te != nullptr) {
         TensorBatch T;
         T.n = 1;
@@ -948,7 +957,7 @@ static int entry_one(ckks_ctx *ctx, const CtDesc &c, const TensorEntry *te, cuda
     const HrLayout lo = hr_layout(ctx, c.ell);
     RC(modup_all(ctx, c.a, c.ell, c.ws + lo.ext, c.ws + lo.tmp, st));
     u64 *u = c.ws + lo.uv, *v = u + size_t(c.ell + ctx->k) * N;
-    InnerArgs ia{c.ws + lo.ext, c.a, c.key, u, v, c.ell, c.galois, {nullptr, nullptr}};
+    InnerArgs ia{c.ws + lo.ext, c.a, c.key, u, v, c.ell, c.galois, {nullptr, nullptr}, c.compressed, c.seed};
     if (c.merged) {
         ia.padd[0] = c.add[0];
         ia.padd[1] = c.add[1];
@@ -1050,6 +1059,7 @@ static int keyswitch_batch_any(ckks_ctx *ctx, int n, const uint64_t *const *a, c
         e[i] = BatchEntry{rot ? BE_HROTATE : BE_KEYSWITCH, a[i], rot ? b[i] : nullptr, nullptr, nullptr, keys[i],
                           oa[i], ob[i], levels[i], rot ? galois[i] : 1u, nullptr, seeds != nullptr,
                           seeds != nullptr ? seeds[i] : 0};
+        if (seeds == nullptr) e[i].compressed = key_seed(ctx, keys[i], &e[i].seed);
     }
     return run_batch(ctx, n, e.data(), static_cast<u64 *>(ws), (cudaStream_t)stream);
 }
@@ -1082,6 +1092,7 @@ static int mult_like_batch(ckks_ctx *ctx, int kind, int n, const uint64_t *const
             !al16(b2[i]) || !al16(keys[i]) || !al16(oa[i]) || !al16(ob[i]))
             return CKKS_EINVAL;
         e[i] = BatchEntry{kind, a1[i], b1[i], a2[i], b2[i], keys[i], oa[i], ob[i], levels[i], 1u, nullptr, 0, 0};
+        e[i].compressed = key_seed(ctx, keys[i], &e[i].seed);
     }
     return run_batch(ctx, n, e.data(), static_cast<u64 *>(ws), (cudaStream_t)stream);
 }
@@ -1139,7 +1150,8 @@ extern "C" int ckks_newmult_sum(ckks_ctx *ctx, int n, const uint64_t *const *a1,
     T.logN = ctx->logN;
     u64 *w = static_cast<u64 *>(ws);
     for (int i = 0; i < n; ++i) {
-        const BatchEntry e{BE_NEWMULT, a1[i], b1[i], a2[i], b2[i], key, oa, ob, level, 1u, nullptr, 0, 0};
+        BatchEntry e{BE_NEWMULT, a1[i], b1[i], a2[i], b2[i], key, oa, ob, level, 1u, nullptr, 0, 0};
+        e.compressed = key_seed(ctx, key, &e.seed);
         TensorEntry te{};
         d.ct[i] = entry_desc(ctx, e, w, &te);
         T.e[T.n++] = te;
@@ -1194,6 +1206,7 @@ extern "C" int ckks_ptmatvecmult(ckks_ctx *ctx, const uint64_t *a, const uint64_
         for (int i = 0; i < nb; ++i) {
             pa.galois[i] = i == 0 ? 1u : g_baby[i];
             pa.key[i] = i == 0 ? nullptr : key_baby[i];
+            pa.compressed[i] = i == 0 ? 0 : uint8_t(key_seed(ctx, key_baby[i], &pa.seed[i]));
             pa.diag[i] = diag[size_t(t) * nb + i];
         }
         CK(launch_pmv_accum(ctx, pa, st));
@@ -1280,6 +1293,18 @@ extern "C" int ckks_ksk_expand(ckks_ctx *ctx, const uint64_t *key_b, uint64_t se
                            cudaMemcpyDeviceToDevice, st));
     }
     return CKKS_OK;
+}
+
+// ------------------------------------------------------------------ compressed-key registry
+extern "C" int ckks_key_register_seed(ckks_ctx *ctx, const uint64_t *key_b, uint64_t seed) {
+    if (ctx == nullptr || !al16(key_b)) return CKKS_EINVAL;
+    ctx->comp_keys[key_b] = seed;
+    return CKKS_OK;
+}
+
+extern "C" int ckks_key_unregister(ckks_ctx *ctx, const uint64_t *key_b) {
+    if (ctx == nullptr || key_b == nullptr) return CKKS_EINVAL;
+    return ctx->comp_keys.erase(key_b) ? CKKS_OK : CKKS_EINVAL;
 }
 
 // ------------------------------------------------------------------ autotuner

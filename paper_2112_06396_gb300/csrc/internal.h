@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstddef>
+#include <unordered_map>
 #include <vector>
 
 #include "batch.cuh"
@@ -32,6 +33,9 @@ struct ckks_ctx {
     // NTT tile shape per pass (0 column, 1 block) and batch class (count <=
     // kTuneSmallBatch, larger): 0 default width, 1 half, 2 double (ntt_autotune)
     int ntt_csel[2][2] = {{0, 0}, {0, 0}};
+    // compressed keys registered with ckks_key_register_seed: device pointer of
+    // the rows b_j -> seed of the rows a_j
+    std::unordered_map<const u64 *, u64> comp_keys;
     // measurement hook (ckks_profile_*): event pairs around every launch
     struct ProfRec {
         cudaEvent_t a, b;
@@ -104,6 +108,8 @@ struct InnerArgs {
     int ell;
     uint32_t galois;     // 1 = no automorphism
     const u64 *padd[2];  // optional [ell][N]: u += P*padd[0], v += P*padd[1] on the chain positions (NewMult)
+    int compressed;      // key = rows b_j only [dnum][L+k][N]; a_j regenerated from seed
+    u64 seed;
 };
 cudaError_t launch_inner_prod(const ckks_ctx *ctx, const InnerArgs &a, cudaStream_t st);
 cudaError_t launch_inner_prod_batch(const ckks_ctx *ctx, const KsBatchDesc &d, cudaStream_t st);
@@ -136,6 +142,8 @@ struct PmvArgs {
     uint32_t galois[kMaxRot];
     const u64 *key[kMaxRot];
     const u64 *diag[kMaxRot];
+    u64 seed[kMaxRot];            // compressed keys: seed of the rows a_j
+    uint8_t compressed[kMaxRot];  // key[i] holds the rows b_j only
 };
 cudaError_t launch_pmv_accum(const ckks_ctx *ctx, const PmvArgs &a, cudaStream_t st);
 

@@ -50,7 +50,9 @@ __device__ __forceinline__ void add_pmodup(const InnerArgs &A, int t, uint32_t n
     mac128(vl1, vh1, c.y, pm.x);
 }
 
-template <int BETA>
+// COMP: the key is compressed (rows b_j only); a_j is drawn from A.seed while
+// the loads are in flight.
+template <int BETA, bool COMP>
 __global__ void __launch_bounds__(256) inner_prod_kernel(InnerArgs A, const PrimeInfo *__restrict__ pinfo, int logN,
                                                          int L, int k, int alpha, const ulonglong2 *__restrict__ Pmod) {
     const size_t N = size_t(1) << logN;
@@ -66,10 +68,22 @@ __global__ void __launch_bounds__(256) inner_prod_kernel(InnerArgs A, const Prim
         const bool own = (A.own != nullptr) && t < ell && (t / alpha) == j;
         const u64 *d = own ? A.own + size_t(t) * N : A.ext + (size_t(j) * ext + t) * N;
         dv[j] = ld2_perm(d, n0, A.galois, logN);
-        ka[j] = ld2_stream(A.key + ((size_t(j) * 2 + 0) * LK + prime) * N + n0);
-        kb[j] = ld2_stream(A.key + ((size_t(j) * 2 + 1) * LK + prime) * N + n0);
+        if (COMP) {
+            kb[j] = ld2_stream(A.key + (size_t(j) * LK + prime) * N + n0);
+        } else {
+            ka[j] = ld2_stream(A.key + ((size_t(j) * 2 + 0) * LK + prime) * N + n0);
+            kb[j] = ld2_stream(A.key + ((size_t(j) * 2 + 1) * LK + prime) * N + n0);
+        }
     }
     const PrimeInfo P = pinfo[prime];
+    if (COMP) {
+        const int shift = __clzll(P.p);
+#pragma unroll
+        for (int j = 0; j < BETA; j++) {
+            const u64 e = (u64(j) * LK + prime) * N + n0;
+            ka[j] = make_ulonglong2(key_a_element(A.seed, e, P.p, shift), key_a_element(A.seed, e + 1, P.p, shift));
+        }
+    }
     u64 ul0 = 0, uh0 = 0, ul1 = 0, uh1 = 0, vl0 = 0, vh0 = 0, vl1 = 0, vh1 = 0;
 #pragma unroll
     for (int j = 0; j < BETA; j++) {
@@ -84,6 +98,7 @@ __global__ void __launch_bounds__(256) inner_prod_kernel(InnerArgs A, const Prim
 }
 
 // beta > 4: loop over digits
+template <bool COMP>
 __global__ void __launch_bounds__(256) inner_prod_kernel_any(InnerArgs A, const PrimeInfo *__restrict__ pinfo, int logN,
                                                              int L, int k, int alpha,
                                                              const ulonglong2 *__restrict__ Pmod) {
@@ -100,8 +115,16 @@ __global__ void __launch_bounds__(256) inner_prod_kernel_any(InnerArgs A, const 
         const bool own = (A.own != nullptr) && t < ell && (t / alpha) == j;
         const u64 *d = own ? A.own + size_t(t) * N : A.ext + (size_t(j) * ext + t) * N;
         const ulonglong2 dv = ld2_perm(d, n0, A.galois, logN);
-        const ulonglong2 ka = ld2_stream(A.key + ((size_t(j) * 2 + 0) * LK + prime) * N + n0);
-        const ulonglong2 kb = ld2_stream(A.key + ((size_t(j) * 2 + 1) * LK + prime) * N + n0);
+        ulonglong2 ka, kb;
+        if (COMP) {
+            const u64 e = (u64(j) * LK + prime) * N + n0;
+            const int shift = __clzll(P.p);
+            ka = make_ulonglong2(key_a_element(A.seed, e, P.p, shift), key_a_element(A.seed, e + 1, P.p, shift));
+            kb = ld2_stream(A.key + (size_t(j) * LK + prime) * N + n0);
+        } else {
+            ka = ld2_stream(A.key + ((size_t(j) * 2 + 0) * LK + prime) * N + n0);
+            kb = ld2_stream(A.key + ((size_t(j) * 2 + 1) * LK + prime) * N + n0);
+        }
         mac128(ul0, uh0, dv.x, ka.x);
         mac128(ul1, uh1, dv.y, ka.y);
         mac128(vl0, vh0, dv.x, kb.x);
@@ -117,14 +140,26 @@ cudaError_t launch_inner_prod(const ckks_ctx *ctx, const InnerArgs &a, cudaStrea
     dim3 grid(unsigned((ctx->N / 2 + threads - 1) / threads), unsigned(a.ell + ctx->k));
     ProfScope ps(ctx, K_INNER, a.ell + ctx->k, st);
     const int beta = beta_of(ctx, a.ell);
-    switch (beta) {
-    case 1: inner_prod_kernel<1><<<grid, threads, 0, st>>>(a, ctx->d_pinfo, ctx->logN, ctx->L, ctx->k, ctx->alpha, ctx->d_Pmod); break;
-    case 2: inner_prod_kernel<2><<<grid, threads, 0, st>>>(a, ctx->d_pinfo, ctx->logN, ctx->L, ctx->k, ctx->alpha, ctx->d_Pmod); break;
-    case 3: inner_prod_kernel<3><<<grid, threads, 0, st>>>(a, ctx->d_pinfo, ctx->logN, ctx->L, ctx->k, ctx->alpha, ctx->d_Pmod); break;
-    case 4: inner_prod_kernel<4><<<grid, threads, 0, st>>>(a, ctx->d_pinfo, ctx->logN, ctx->L, ctx->k, ctx->alpha, ctx->d_Pmod); break;
-    default:
-        inner_prod_kernel_any<<<grid, threads, 0, st>>>(a, ctx->d_pinfo, ctx->logN, ctx->L, ctx->k, ctx->alpha, ctx->d_Pmod);
+#define CKKS_IP(B, CMP)                                                                                            \
+    inner_prod_kernel<B, CMP><<<grid, threads, 0, st>>>(a, ctx->d_pinfo, ctx->logN, ctx->L, ctx->k, ctx->alpha,    \
+                                                        ctx->d_Pmod)
+#define CKKS_IP_BETA(CMP)                                                                                          \
+    switch (beta) {                                                                                                \
+    case 1: CKKS_IP(1, CMP); break;                                                                                \
+    case 2: CKKS_IP(2, CMP); break;                                                                                \
+    case 3: CKKS_IP(3, CMP); break;                                                                                \
+    case 4: CKKS_IP(4, CMP); break;                                                                                \
+    default:                                                                                                       \
+        inner_prod_kernel_any<CMP><<<grid, threads, 0, st>>>(a, ctx->d_pinfo, ctx->logN, ctx->L, ctx->k,           \
+                                                             ctx->alpha, ctx->d_Pmod);                             \
     }
+    if (a.compressed) {
+        CKKS_IP_BETA(true)
+    } else {
+        CKKS_IP_BETA(false)
+    }
+#undef CKKS_IP_BETA
+#undef CKKS_IP
     return cudaGetLastError();
 }
 
@@ -349,6 +384,7 @@ cudaError_t launch_key_a_fill(const ckks_ctx *ctx, u64 seed, int j0, int ndig, u
 // where (u_i, v_i) is the inner product of the hoisted digits automorphed by
 // g_i with key_i, and baby step i = 0 (no key) contributes M_0 * (P*a, P*b).
 // u_i and v_i never leave registers (the beta-limb caching of Sec. 4.2).
+template <bool COMP>
 __global__ void __launch_bounds__(256) pmv_accum_kernel(PmvArgs A, const PrimeInfo *__restrict__ pinfo,
                                                         const ulonglong2 *__restrict__ Pmod, int logN, int L, int k,
                                                         int alpha) {
@@ -384,8 +420,17 @@ __global__ void __launch_bounds__(256) pmv_accum_kernel(PmvArgs A, const PrimeIn
                 const bool own = t < ell && (t / alpha) == j;
                 const u64 *d = own ? A.a + size_t(t) * N : A.ext + (size_t(j) * ext + t) * N;
                 const ulonglong2 dv = ld2_perm(d, n0, g, logN);
-                const ulonglong2 ka = ld2_stream(key + ((size_t(j) * 2 + 0) * LK + prime) * N + n0);
-                const ulonglong2 kb = ld2_stream(key + ((size_t(j) * 2 + 1) * LK + prime) * N + n0);
+                ulonglong2 ka, kb;
+                if (COMP && A.compressed[i]) {
+                    const u64 e = (u64(j) * LK + prime) * N + n0;
+                    const int shift = __clzll(P.p);
+                    kb = ld2_stream(key + (size_t(j) * LK + prime) * N + n0);
+                    ka = make_ulonglong2(key_a_element(A.seed[i], e, P.p, shift),
+                                         key_a_element(A.seed[i], e + 1, P.p, shift));
+                } else {
+                    ka = ld2_stream(key + ((size_t(j) * 2 + 0) * LK + prime) * N + n0);
+                    kb = ld2_stream(key + ((size_t(j) * 2 + 1) * LK + prime) * N + n0);
+                }
                 mac128(ul0, uh0, dv.x, ka.x);
                 mac128(ul1, uh1, dv.y, ka.y);
                 mac128(vl0, vh0, dv.x, kb.x);
@@ -414,7 +459,14 @@ cudaError_t launch_pmv_accum(const ckks_ctx *ctx, const PmvArgs &a, cudaStream_t
     const int threads = 256;
     dim3 grid(unsigned((ctx->N / 2 + threads - 1) / threads), unsigned(a.ell + ctx->k));
     ProfScope ps(ctx, K_PMV, double(a.ell + ctx->k) * a.nb, st);
-    pmv_accum_kernel<<<grid, threads, 0, st>>>(a, ctx->d_pinfo, ctx->d_Pmod, ctx->logN, ctx->L, ctx->k, ctx->alpha);
+    bool comp = false;
+    for (int i = 0; i < a.nb; ++i) comp = comp || a.compressed[i];
+    if (comp)
+        pmv_accum_kernel<true><<<grid, threads, 0, st>>>(a, ctx->d_pinfo, ctx->d_Pmod, ctx->logN, ctx->L, ctx->k,
+                                                          ctx->alpha);
+    else
+        pmv_accum_kernel<false><<<grid, threads, 0, st>>>(a, ctx->d_pinfo, ctx->d_Pmod, ctx->logN, ctx->L, ctx->k,
+                                                           ctx->alpha);
     return cudaGetLastError();
 }
 

@@ -131,7 +131,6 @@ static int add_key(ckks_server *s, int ctx, const uint64_t *d_key, int compresse
     if (s == nullptr || handle == nullptr || ctx < 0 || ctx >= int(s->ctxs.size()) || !al16(d_key))
         return CKKS_EINVAL;
     const ckks_ctx *c = s->ctxs[size_t(ctx)];
-    if (compressed && !c->split_bits) return CKKS_EUNSUPPORTED;
     const size_t bytes = size_t(c->dnum) * (compressed ? 1 : 2) * (c->L + c->k) * c->N * sizeof(u64);
     if (!s->sched->add_resident(bytes)) return CKKS_ENOMEM;
     s->keys.push_back({ctx, d_key, compressed, seed});
@@ -140,6 +139,12 @@ static int add_key(ckks_server *s, int ctx, const uint64_t *d_key, int compresse
 }
 
 extern "C" int ckks_server_add_key(ckks_server *s, int ctx, const uint64_t *d_key, int *handle) {
+    if (s != nullptr && ctx >= 0 && ctx < int(s->ctxs.size())) {
+        // a key registered as compressed with its context
+        const auto &m = s->ctxs[size_t(ctx)]->comp_keys;
+        const auto it = m.find(d_key);
+        if (it != m.end()) return add_key(s, ctx, d_key, 1, it->second, handle);
+    }
     return add_key(s, ctx, d_key, 0, 0, handle);
 }
 

@@ -115,3 +115,64 @@ def test_compressed_keys_headline_shape(oracle_lib):
     for l in (0, 23, 24, 31):
         for n in (0, 1, 4097, S.P.N - 1):
             assert int(a0[l, n]) == S.o.prng_key_a_element(S.P, seed, 0, l, n)
+
+
+def test_registered_compressed_keys_in_every_call(cfg):
+    """A compressed key registered with its context works in the single calls
+    (KeySwitch, Rotate, HRotate, PtMatVecMult with compressed baby and giant
+    keys) with the bits of the expanded key."""
+    S = cfg
+    P, ctx = S.P, S.ctx
+    twoN = 2 * P.N
+    ell = P.L
+    a, b = S.ct(ell, "gpu/prng/reg/ct")
+    da, db = dev(a), dev(b)
+    relin_seed = synth.stream_seed("gpu/prng/reg/relin")
+    kr, _ = _seeded_key(S, 0, relin_seed, "gpu/prng/reg/relin")
+    ctx.register_compressed_key(kr, relin_seed)
+    full_r = ctx.ksk_expand(kr, relin_seed)
+    u1, v1 = ctx.keyswitch(da, ell, kr)
+    u2, v2 = ctx.keyswitch(da, ell, full_r)
+    assert torch.equal(u1, u2) and torch.equal(v1, v2)
+    nb, ng = 3, 2
+    g_baby = [1] + [pow(5, i, twoN) for i in range(1, nb)]
+    g_giant = [1] + [pow(5, nb, twoN)]
+    comp, full = {}, {}
+    for g in g_baby[1:] + g_giant[1:]:
+        sd = synth.stream_seed(f"gpu/prng/reg/{g}")
+        kb, _ = _seeded_key(S, g, sd, f"gpu/prng/reg/{g}")
+        ctx.register_compressed_key(kb, sd)
+        comp[g], full[g] = kb, ctx.ksk_expand(kb, sd)
+    g = g_baby[1]
+    (ra, rb), = ctx.hrotate(da, db, ell, [g], [comp[g]])
+    (fa, fb), = ctx.hrotate(da, db, ell, [g], [full[g]])
+    assert torch.equal(ra, fa) and torch.equal(rb, fb)
+    ra, rb = ctx.rotate(da, db, ell, g, comp[g])
+    fa, fb = ctx.rotate(da, db, ell, g, full[g])
+    assert torch.equal(ra, fa) and torch.equal(rb, fb)
+    diags = [dev(synth.uniform_residues(P.ext_primes(ell), P.N, f"gpu/prng/reg/M{d}")) for d in range(nb * ng)]
+    kbc = [None] + [comp[g] for g in g_baby[1:]]
+    kgc = [None] + [comp[g] for g in g_giant[1:]]
+    kbf = [None] + [full[g] for g in g_baby[1:]]
+    kgf = [None] + [full[g] for g in g_giant[1:]]
+    ca, cb = ctx.ptmatvecmult(da, db, ell, nb, ng, g_baby, g_giant, kbc, kgc, diags, rescale=True)
+    pa, pb = ctx.ptmatvecmult(da, db, ell, nb, ng, g_baby, g_giant, kbf, kgf, diags, rescale=True)
+    assert torch.equal(ca, pa) and torch.equal(cb, pb)
+    for k in [kr] + list(comp.values()):
+        ctx.unregister_compressed_key(k)
+
+
+def test_registered_compressed_key_wide_primes(oracle_lib):
+    """58-bit primes (single-operation launches): a registered compressed key
+    gives the bits of its expansion, and those of the oracle."""
+    S = Setup(oracle_lib, 11, 4, 2, 2, 58)
+    seed = synth.stream_seed("gpu/prng/wide")
+    kb, ref = _seeded_key(S, 0, seed, "gpu/prng/wide")
+    S.ctx.register_compressed_key(kb, seed)
+    for ell in (4, 1):
+        a, _ = S.ct(ell, f"gpu/prng/wide/{ell}")
+        u, v = S.ctx.keyswitch(dev(a), ell, kb)
+        ru, rv = S.o.keyswitch(S.P, ell, a, ref)
+        np.testing.assert_array_equal(host(u), ru)
+        np.testing.assert_array_equal(host(v), rv)
+    S.ctx.unregister_compressed_key(kb)
