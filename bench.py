@@ -365,6 +365,29 @@ def measure_other_rows(ctx, ckks, torch, reps=5):
 
     per_level = [_timed(torch, lambda i=i: level(i), reps) for i in range(3)]
     c2s_ms = _timed(torch, lambda: [level(i) for i in range(3)], reps)
+    # the same three levels with every rotation key compressed (Sec. 5.4): rows b_j
+    # only, a_j regenerated from a seed inside the kernels
+    full_levels = levels
+    levels = []
+    comp_key_bytes = 0
+    for lv, (ell, g_baby, g_giant, kb, kg, diags) in enumerate(full_levels):
+        def ckey(g, tag):
+            nonlocal comp_key_bytes
+            sd = synth.stream_seed(f"bench/rows/l{lv}/{tag}/seed")
+            e_key = np.stack([synth.gaussian(N, f"bench/rows/l{lv}/{tag}/e{j}") for j in range(DNUM)])
+            kbc = ctx.keygen_ksk_seeded(s, dev(e_key), sd, g)
+            ctx.register_compressed_key(kbc, sd)
+            comp_key_bytes += kbc.numel() * 8
+            return kbc
+        kbc = [None] + [ckey(g, f"kb{i}") for i, g in enumerate(g_baby) if i > 0]
+        kgc = [None] + [ckey(g, f"kg{t}") for t, g in enumerate(g_giant) if t > 0]
+        levels.append((ell, g_baby, g_giant, kbc, kgc, diags))
+    per_level_c = [_timed(torch, lambda i=i: level(i), reps) for i in range(3)]
+    c2s_ms_c = _timed(torch, lambda: [level(i) for i in range(3)], reps)
+    for (_e, _gb, _gg, kbc, kgc, _d) in levels:
+        for k in kbc[1:] + kgc[1:]:
+            ctx.unregister_compressed_key(k)
+    del full_levels
     comp = []
     for i, (ell, *_rest) in enumerate(levels):
         comp.append((2 * ell + (nb - 1 + ng - 1) * traffic.key_limbs(ell, K_SP, L, DNUM) + nb * ng * (ell + K_SP)
@@ -379,6 +402,9 @@ def measure_other_rows(ctx, ckks, torch, reps=5):
                                   "stride 32^level, 32 diagonals and 10 keys per level (30 keys), rescaled",
                          "ms_per_level": per_level, "ms_coeff_to_slot": c2s_ms,
                          "coeff_to_slot_per_s": 1e3 / c2s_ms,
+                         "compressed_keys": {"ms_per_level": per_level_c, "ms_coeff_to_slot": c2s_ms_c,
+                                             "coeff_to_slot_per_s": 1e3 / c2s_ms_c,
+                                             "resident_key_bytes": comp_key_bytes},
                          "compulsory_bytes_per_level": comp,
                          "hbm_frac_of_measured_per_level": [c / (t * 1e-3) / 1e9 / hbm for c, t in zip(comp, per_level)]},
     }
@@ -403,6 +429,24 @@ def ncu_traffic_per_limb():
     if d.get("source_hash") != ntt_source_hash():
         return None
     return float(d["dram_bytes_per_limb_transform"])
+
+
+# ------------------------------------------------------------------ multi-rank helpers
+def max_over_ranks(value, dist, device="cpu"):
+    """The slowest rank's time (the whole job ends with it); no-op on one rank."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, per_rank_units_per_step, steps, ms):
+    """Units per second of the whole job: every rank processes its own units
+    (weak scaling), the time is the max over ranks."""
+    return world * per_rank_units_per_step * steps / (ms / 1e3)
 
 
 # ------------------------------------------------------------------ oracle (CPU) legs
@@ -501,13 +545,9 @@ def run_gpu(args, rank, world, local_rank):
     t_wall = time.perf_counter() - t_wall0
     barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     ms_per_step = ms / args.steps
-    value = world * C * args.steps / (ms / 1e3)
+    value = job_throughput(world, C, args.steps, ms)
 
     # ---- per-kernel-class device time on the launch stream (measurement hook),
     # one stream so that every bracketed launch runs alone
@@ -555,11 +595,7 @@ def run_gpu(args, rank, world, local_rank):
         e2e_step()
     f1.record()
     torch.cuda.synchronize()
-    e2e_ms = f0.elapsed_time(f1)
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(f0.elapsed_time(f1), dist, "cuda")
     # the step's result is read back on the host: check it matches the device-only run
     ok = all(torch.equal(oa, it["oa"].cpu()) for (oa, _), it in zip(pin_out, items))
     bytes_io = C * 2 * L * N * 8
@@ -603,7 +639,7 @@ def run_gpu(args, rank, world, local_rank):
                          "avg_launch_us": avg_launch_ms * 1e3,
                          "share_of_kernel_time": ntt_ms / sum(v[0] for v in prof.values())},
             "kernels": by_class,
-            "e2e": {"value": world * C * e2e_steps / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": bytes_io,
+            "e2e": {"value": job_throughput(world, C, e2e_steps, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": bytes_io,
                     "d2h_bytes_per_step": bytes_io, "matches_device_result": ok},
         }
         if not args.no_rows:

@@ -80,10 +80,12 @@ ntt_pass_kernel(const __grid_constant__ MAP map, const PrimeInfo *__restrict__ p
     constexpr uint32_t N = 1u << LOGN;
     constexpr int logN = LOGN;
     // limbs sharing a prime are adjacent: co-resident CTAs reuse twiddles
-    const LimbIO io = map.get(blockIdx.x, N);
-    const int prime = io.prime;
-    const u64 *__restrict__ src = io.src;
-    u64 *dst = io.dst;
+    // The limb's pointers are derived twice (here for the source and the L2
+    // prefetch, again before the stores): nothing but the source and the prime
+    // stays live across the butterflies.
+    const LimbIO io0 = map.get(blockIdx.x, N);
+    const int prime = io0.prime;
+    const u64 *__restrict__ src = io0.src;
     const ulonglong2 *__restrict__ tw = tw_all + size_t(prime) * N;
     const u64 p = pinfo[prime].p;
     const u64 np = u64(0) - p;
@@ -121,13 +123,13 @@ ntt_pass_kernel(const __grid_constant__ MAP map, const PrimeInfo *__restrict__ p
             l2_prefetch(t0, uint32_t(C * sizeof(ulonglong2)) << sg);
         }
         if (EPI) {
-            l2_prefetch(io.ex + (col0 << L2), uint32_t(C * sizeof(u64)) << L2);
-            if (io.accumulate) l2_prefetch(io.eout + (col0 << L2), uint32_t(C * sizeof(u64)) << L2);
-            if (io.eadd != nullptr) {
+            l2_prefetch(io0.ex + (col0 << L2), uint32_t(C * sizeof(u64)) << L2);
+            if (io0.accumulate) l2_prefetch(io0.eout + (col0 << L2), uint32_t(C * sizeof(u64)) << L2);
+            if (io0.eadd != nullptr) {
                 for (int b = 0; b < C; b++) {
                     const uint32_t first = uint32_t((col0 + b) << L2);
-                    const uint32_t sblk = (io.galois == 1 ? first : automorph_src(first, io.galois, logN)) >> L2;
-                    l2_prefetch(io.eadd + (size_t(sblk) << L2), uint32_t(sizeof(u64)) << L2);
+                    const uint32_t sblk = (io0.galois == 1 ? first : automorph_src(first, io0.galois, logN)) >> L2;
+                    l2_prefetch(io0.eadd + (size_t(sblk) << L2), uint32_t(sizeof(u64)) << L2);
                 }
             }
         }
@@ -163,6 +165,8 @@ ntt_pass_kernel(const __grid_constant__ MAP map, const PrimeInfo *__restrict__ p
                 ct_bfly<SMALLP>(x[e], x[e + half], TW(sg, (g << A) + e), p, np);
             }
         }
+        const LimbIO io = map.get(blockIdx.x, N);
+        u64 *dst = io.dst;
         if (!CONTIG) {
             // pass S: store contiguous layout (lanes run over columns: coalesced)
 #pragma unroll
@@ -274,6 +278,7 @@ ntt_pass_kernel(const __grid_constant__ MAP map, const PrimeInfo *__restrict__ p
                 }
             }
         }
+        u64 *dst = map.get(blockIdx.x, N).dst;
 #pragma unroll
         for (int k = 0; k < E; k++) {
             u64 v = x[k];
