@@ -149,8 +149,8 @@ __global__ void __launch_bounds__(128) bconv_split_kernel(const __grid_constant_
         u64 v0 = B0 + shoup_approx(A0, d.rw, d.rw_s, np);
         u64 v1 = B1 + shoup_approx(A1, d.rw, d.rw_s, np);
         const u64 off = d.p - d.sub;
-        v0 = shoup_approx(v0, 1, d.one_s, np) + off;
-        v1 = shoup_approx(v1, 1, d.one_s, np) + off;
+        v0 = shoup_one(v0, d.one_s, np) + off;
+        v1 = shoup_one(v1, d.one_s, np) + off;
         *reinterpret_cast<ulonglong2 *>(G.dst + size_t(d.pos) * N + n0) = make_ulonglong2(v0, v1);
     }
 }

@@ -91,6 +91,40 @@ __device__ __forceinline__ u64 shoup_approx(u64 x, u64 w, u64 ws, u64 np) {
     return r;
 }
 __device__ __forceinline__ u64 shoup_mul(u64 x, u64 w, u64 ws, u64 p) { return csub(shoup_lazy(x, w, ws, p), p); }
+// shoup_approx with w = 1 (a reduction of any 64-bit x to [0, 3p) with
+// ones = floor(2^64 / p)): the same quotient, and x - q_hat*p = x + q_hat*np
+// needs one wide multiply-add with x as the addend and two low products.
+__device__ __forceinline__ u64 shoup_one(u64 x, u64 ones, u64 np) {
+    u64 r;
+    asm("{\n\t"
+        ".reg .u32 x0, x1, s0, s1, n0, n1, h1, h2, q0, q1, m, r0, r1;\n\t"
+        ".reg .u64 q, acc, t;\n\t"
+        "mov.b64 {x0, x1}, %1;\n\t"
+        "mov.b64 {s0, s1}, %2;\n\t"
+        "mov.b64 {n0, n1}, %3;\n\t"
+        "mul.wide.u32 t, x1, s0;\n\t"
+        "mov.b64 {h1, h2}, t;\n\t"
+        "cvt.u64.u32 acc, h1;\n\t"
+        "mad.wide.u32 acc, x0, s1, acc;\n\t"
+        "cvt.u64.u32 t, h2;\n\t"
+        "mad.wide.u32 q, x1, s1, t;\n\t"
+        "mov.b64 {h1, h2}, acc;\n\t"
+        "cvt.u64.u32 t, h2;\n\t"
+        "add.u64 q, q, t;\n\t"
+        "mov.b64 {q0, q1}, q;\n\t"
+        // x + q * (2^64 - p), low word
+        "mad.wide.u32 acc, q0, n0, %1;\n\t"
+        "mul.lo.u32 m, q0, n1;\n\t"
+        "mad.lo.u32 m, q1, n0, m;\n\t"
+        "mov.b64 {r0, r1}, acc;\n\t"
+        "add.u32 r1, r1, m;\n\t"
+        "mov.b64 %0, {r0, r1};\n\t"
+        "}"
+        : "=l"(r)
+        : "l"(x), "l"(ones), "l"(np));
+    return r;
+}
+
 __device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 p) { return csub(a + b, p); }
 __device__ __forceinline__ u64 sub_mod(u64 a, u64 b, u64 p) { return a >= b ? a - b : a + p - b; }
 

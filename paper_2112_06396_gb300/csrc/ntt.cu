@@ -181,7 +181,7 @@ ntt_pass_kernel(const __grid_constant__ MAP map, const PrimeInfo *__restrict__ p
             const u64 one_s = pinfo[prime].one_s;
 #pragma unroll
             for (int k = 0; k < E; k++) {
-                u64 v = SMALLP ? shoup_approx(x[k], 1, one_s, np) : x[k];
+                u64 v = SMALLP ? shoup_one(x[k], one_s, np) : x[k];
                 x[k] = csub(csub(v, 2 * p), p);
             }
             if (!EPI) {
