@@ -195,6 +195,20 @@ int ckks_keyswitch_batch(ckks_ctx *ctx, int n, const uint64_t *const *d_a, const
                          const int *levels, const uint32_t *galois, const uint64_t *const *d_keys,
                          uint64_t *const *d_oa, uint64_t *const *d_ob, void *ws, ckks_stream_t stream);
 
+/* Batched HRotate with hoisted rotations (Algorithm 4 over many ciphertexts):
+ * ciphertext c (d_a[c], d_b[c] at levels[c]) is rotated by nrot[c] >= 1 Galois
+ * elements; the rotations are listed ciphertext by ciphertext in galois,
+ * d_keys, d_oa, d_ob (sum of nrot entries; d_oa/d_ob [levels[c]][N]).  The
+ * ModUp of every ciphertext runs once (one launch per step for all of them),
+ * then the inner product and ModDown of every rotation (one launch per step
+ * for all rotations, 64 per launch).  Bits: those of ckks_hrotate with the
+ * same rotations.  Workspace: ckks_hrotate_batch_workspace_bytes. */
+int ckks_hrotate_batch_workspace_bytes(const ckks_ctx *ctx, int n, const int *levels, const int *nrot,
+                                       size_t *bytes);
+int ckks_hrotate_batch(ckks_ctx *ctx, int n, const uint64_t *const *d_a, const uint64_t *const *d_b,
+                       const int *levels, const int *nrot, const uint32_t *galois, const uint64_t *const *d_keys,
+                       uint64_t *const *d_oa, uint64_t *const *d_ob, void *ws, ckks_stream_t stream);
+
 /* Mult with relinearisation and Rescale (Algorithm 2): for ciphertexts
  * (d_a1, d_b1), (d_a2, d_b2) at level ell >= 2 (evaluation form, [ell][N]):
  * (a3, b3, c3) = (a1 a2, a1 b2 + a2 b1, b1 b2) slot-wise, (u, v) = KeySwitch

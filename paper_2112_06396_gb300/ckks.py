@@ -82,6 +82,11 @@ _SIGS = {
     "ckks_mult": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _vp, _vp, _vp, _vp, _vp]),
     "ckks_mult_batch_workspace_bytes": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_size_t)]),
     "ckks_newmult": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _vp, _vp, _vp, _vp, _vp]),
+    "ckks_hrotate_batch_workspace_bytes": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i),
+                                                ctypes.POINTER(ctypes.c_size_t)]),
+    "ckks_hrotate_batch": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_i),
+                                ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(_vp),
+                                ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp, _vp]),
     "ckks_newmult_sum": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                               ctypes.POINTER(_vp), _i, _vp, _vp, _vp, _vp, _vp]),
     "ckks_newmult_batch_workspace_bytes": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_size_t)]),
@@ -374,6 +379,30 @@ class Context:
             sd = (ctypes.c_uint64 * m)(*[int(x) & 0xFFFFFFFFFFFFFFFF for x in seeds])
             _check(lib().ckks_keyswitch_batch_seeded(self._h, n, ap, bp, lv, gp, kp, sd, oa, ob, _p(ws),
                                                      _stream(stream)), self._h)
+        return outs
+
+    def hrotate_batch(self, cts, levels, rotations, outs=None, ws=None, stream=None):
+        """cts: list of (a, b); rotations: per ciphertext a list of (galois, key).
+        Returns per ciphertext a list of (oa, ob), one per rotation."""
+        n = len(cts)
+        nrot = [len(r) for r in rotations]
+        flat = [gk for r in rotations for gk in r]
+        if outs is None:
+            outs = [[(self.empty(levels[c]), self.empty(levels[c])) for _ in rotations[c]] for c in range(n)]
+        flat_out = [o for oc in outs for o in oc]
+        m = max(len(flat), 1)
+        lv = (_i * max(n, 1))(*[int(x) for x in levels])
+        nr = (_i * max(n, 1))(*nrot)
+        if ws is None:
+            nbytes = ctypes.c_size_t()
+            _check(lib().ckks_hrotate_batch_workspace_bytes(self._h, n, lv, nr, ctypes.byref(nbytes)))
+            ws = torch.empty(max(nbytes.value // 8, 2), dtype=torch.uint64, device=self.device)
+        arr = lambda xs, k: (_vp * k)(*[x.data_ptr() for x in xs])
+        _check(lib().ckks_hrotate_batch(self._h, n, arr([c[0] for c in cts], max(n, 1)),
+                                        arr([c[1] for c in cts], max(n, 1)), lv, nr,
+                                        (ctypes.c_uint32 * m)(*[int(g) for g, _ in flat]),
+                                        arr([k for _, k in flat], m), arr([o[0] for o in flat_out], m),
+                                        arr([o[1] for o in flat_out], m), _p(ws), _stream(stream)), self._h)
         return outs
 
     def keygen_ksk_seeded(self, s, e, seed, galois, key_b=None, ws=None, stream=None):

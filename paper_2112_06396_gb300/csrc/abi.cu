@@ -1070,6 +1070,95 @@ extern "C" int ckks_keyswitch_batch(ckks_ctx *ctx, int n, const uint64_t *const 
     return keyswitch_batch_any(ctx, n, a, b, levels, galois, keys, nullptr, oa, ob, ws, stream);
 }
 
+// ---- batched HRotate with hoisted rotations (Algorithm 4 over many ciphertexts)
+// Ciphertext c has nrot[c] rotations; its first rotation owns the full HRotate
+// workspace (ModUp digits, uv, scratch), every further rotation only uv and
+// scratch and reads the owner's digits.
+static size_t rot_extra_words(const ckks_ctx *c, int ell) {
+    const HrLayout lo = hr_layout(c, ell);
+    return lo.total - lo.uv;  // uv | tmp
+}
+
+extern "C" int ckks_hrotate_batch_workspace_bytes(const ckks_ctx *ctx, int n, const int *levels, const int *nrot,
+                                                  size_t *bytes) {
+    if (ctx == nullptr || bytes == nullptr || n < 0 || (n > 0 && (levels == nullptr || nrot == nullptr)))
+        return CKKS_EINVAL;
+    size_t w = 0;
+    for (int i = 0; i < n; ++i) {
+        if (!level_ok(ctx, levels[i]) || nrot[i] < 1) return CKKS_EINVAL;
+        w += hr_layout(ctx, levels[i]).total + size_t(nrot[i] - 1) * rot_extra_words(ctx, levels[i]);
+    }
+    *bytes = w * sizeof(u64);
+    return CKKS_OK;
+}
+
+extern "C" int ckks_hrotate_batch(ckks_ctx *ctx, int n, const uint64_t *const *a, const uint64_t *const *b,
+                                  const int *levels, const int *nrot, const uint32_t *galois,
+                                  const uint64_t *const *keys, uint64_t *const *oa, uint64_t *const *ob, void *ws,
+                                  ckks_stream_t stream) {
+    if (ctx == nullptr || n < 0) return CKKS_EINVAL;
+    if (n == 0) return CKKS_OK;
+    if (!a || !b || !levels || !nrot || !galois || !keys || !oa || !ob || !al16(ws)) return CKKS_EINVAL;
+    int m = 0;
+    for (int c = 0; c < n; ++c) {
+        if (!level_ok(ctx, levels[c]) || nrot[c] < 1 || !al16(a[c]) || !al16(b[c])) return CKKS_EINVAL;
+        for (int r = 0; r < nrot[c]; ++r, ++m)
+            if (!galois_ok(ctx, galois[m]) || !al16(keys[m]) || !al16(oa[m]) || !al16(ob[m])) return CKKS_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    u64 *w = static_cast<u64 *>(ws);
+    if (!ctx->split_bits) {
+        // one ciphertext at a time: ModUp once, then every rotation (the single-call path)
+        for (int c = 0, i = 0; c < n; i += nrot[c], ++c) {
+            RC(ckks_hrotate(ctx, a[c], b[c], levels[c], nrot[c], galois + i, keys + i, oa + i, ob + i, w, stream));
+            w += hr_layout(ctx, levels[c]).total + size_t(nrot[c] - 1) * rot_extra_words(ctx, levels[c]);
+        }
+        return CKKS_OK;
+    }
+    // descriptors of every rotation; the first of each ciphertext owns the digits
+    std::vector<CtDesc> all(m), owners(n);
+    for (int c = 0, i = 0; c < n; ++c) {
+        u64 *own = w;
+        for (int r = 0; r < nrot[c]; ++r, ++i) {
+            BatchEntry e{BE_HROTATE, a[c], b[c], nullptr, nullptr, keys[i], oa[i], ob[i], levels[c], galois[i],
+                         nullptr, 0, 0};
+            e.compressed = key_seed(ctx, keys[i], &e.seed);
+            TensorEntry te{};
+            all[i] = entry_desc(ctx, e, w, &te);
+            if (r == 0) {
+                owners[c] = all[i];
+                w += hr_layout(ctx, levels[c]).total;
+            } else {
+                all[i].ext_shared = own;
+                w += rot_extra_words(ctx, levels[c]);
+            }
+        }
+    }
+    auto desc = [&](const CtDesc *v, int cnt) {
+        KsBatchDesc d{};
+        d.n = cnt;
+        d.L = ctx->L;
+        d.k = ctx->k;
+        d.alpha = ctx->alpha;
+        d.dnum = ctx->dnum;
+        d.logN = ctx->logN;
+        for (int i = 0; i < cnt; ++i) d.ct[i] = v[i];
+        return d;
+    };
+    for (int c0 = 0; c0 < n; c0 += kMaxCts) {  // ModUp of every ciphertext, once
+        const KsBatchDesc d = desc(owners.data() + c0, std::min(n - c0, kMaxCts));
+        CK(launch_ntt_batch(ctx, d, PH_INTT_A, st));
+        CK(launch_bconv_batch(ctx, d, GM_MODUP, st));
+        CK(launch_ntt_batch(ctx, d, PH_NTT_UP, st));
+    }
+    for (int i0 = 0; i0 < m; i0 += kMaxCts) {  // every rotation: inner product and ModDown
+        const KsBatchDesc d = desc(all.data() + i0, std::min(m - i0, kMaxCts));
+        CK(launch_inner_prod_batch(ctx, d, st));
+        RC(batch_back(ctx, d, false, st));
+    }
+    return CKKS_OK;
+}
+
 extern "C" int ckks_keyswitch_batch_seeded(ckks_ctx *ctx, int n, const uint64_t *const *a, const uint64_t *const *b,
                                            const int *levels, const uint32_t *galois,
                                            const uint64_t *const *keys_b, const uint64_t *seeds, uint64_t *const *oa,

@@ -85,6 +85,8 @@ struct CtDesc {
     int merged;      // NewMult entry
     int compressed;  // key holds only the b rows [dnum][L+k][N]; a is regenerated from seed
     u64 seed;
+    u64 *ext_shared; // hoisted rotations: the ModUp digits of another entry of the same
+                     // ciphertext; ws then holds only uv | tmp
 };
 
 struct KsBatchDesc {
@@ -104,8 +106,8 @@ __host__ __device__ __forceinline__ CtLayout ct_layout(const KsBatchDesc &d, con
     const size_t N = size_t(1) << d.logN;
     o.beta = (c.ell + d.alpha - 1) / d.alpha;
     o.ext = c.ell + d.k;
-    o.extp = c.ws;
-    o.uv = c.ws + size_t(o.beta) * o.ext * N;
+    o.extp = c.ext_shared != nullptr ? c.ext_shared : c.ws;
+    o.uv = c.ext_shared != nullptr ? c.ws : c.ws + size_t(o.beta) * o.ext * N;
     o.acoeff = o.uv + size_t(2) * o.ext * N;
     o.pcoeff = o.acoeff;
     o.w = o.pcoeff + size_t(2) * (d.k + c.merged) * N;

@@ -172,3 +172,53 @@ def test_batch_captured_in_a_cuda_graph(cfg1):
     torch.cuda.synchronize()
     for (ga, gb), (wa, wb) in zip(outs, want):
         assert torch.equal(ga, wa) and torch.equal(gb, wb)
+
+
+@pytest.mark.parametrize("which", ["cfg1", "cfg_odd"])
+def test_hrotate_batch_hoisted_rotations(request, which):
+    """Several ciphertexts at uneven levels, each rotated by several Galois
+    elements with one ModUp per ciphertext: every output equals ckks_hrotate of
+    that ciphertext with the same rotations, and the oracle."""
+    S = request.getfixturevalue(which)
+    P = S.P
+    twoN = 2 * P.N
+    gs = [5, pow(5, 3, twoN), twoN - 1, pow(5, 9, twoN)]
+    keys = {g: S.key(g, f"gpu/hrb/{which}/{g}")[0] for g in gs}
+    dkeys = {g: dev(k) for g, k in keys.items()}
+    levels = [P.L, 2, P.L - 1, 1]
+    nrots = [3, 1, 4, 2]
+    cts, rots = [], []
+    for c, (ell, r) in enumerate(zip(levels, nrots)):
+        a, b = S.ct(ell, f"gpu/hrb/{which}/{c}")
+        cts.append((a, b))
+        rots.append([gs[(c + j) % len(gs)] for j in range(r)])
+    dcts = [(dev(a), dev(b)) for a, b in cts]
+    outs = S.ctx.hrotate_batch(dcts, levels, [[(g, dkeys[g]) for g in r] for r in rots])
+    for c, ell in enumerate(levels):
+        single = S.ctx.hrotate(*dcts[c], ell, rots[c], [dkeys[g] for g in rots[c]])
+        ref = S.o.hrotate(P, ell, *cts[c], rots[c], [keys[g] for g in rots[c]])
+        for (ga, gb), (sa, sb), (ra, rb) in zip(outs[c], single, ref):
+            np.testing.assert_array_equal(host(ga), host(sa))
+            np.testing.assert_array_equal(host(gb), host(sb))
+            np.testing.assert_array_equal(host(ga), ra)
+            np.testing.assert_array_equal(host(gb), rb)
+
+
+def test_hrotate_batch_many_rotations_headline_shape(cfgB):
+    """Two ciphertexts at N=2^16, ell=24 and 20, 40 rotations each (80 rotation
+    entries: two launches of the inner-product and ModDown steps): equal to
+    the single hoisted calls."""
+    S = cfgB
+    P = S.P
+    twoN = 2 * P.N
+    gs = [pow(5, i + 1, twoN) for i in range(4)]
+    keys = {g: dev(S.key(g, f"gpu/hrbB/{g}")[0]) for g in gs}
+    levels = [24, 20]
+    dcts = [tuple(dev(x) for x in S.ct(ell, f"gpu/hrbB/{c}")) for c, ell in enumerate(levels)]
+    rots = [[gs[j % 4] for j in range(40)] for _ in levels]
+    outs = S.ctx.hrotate_batch(dcts, levels, [[(g, keys[g]) for g in r] for r in rots])
+    for c, ell in enumerate(levels):
+        single = S.ctx.hrotate(*dcts[c], ell, rots[c][:4], [keys[g] for g in rots[c][:4]])
+        for j in range(40):
+            sa, sb = single[j % 4]
+            assert torch.equal(outs[c][j][0], sa) and torch.equal(outs[c][j][1], sb)
