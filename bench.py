@@ -325,6 +325,47 @@ def measure_serving(ctx16, ckks, torch, n_req=400, rates=(2000, 4000, 8000, 1600
             "max_ops_per_s_within_slo": best}
 
 
+def measure_hoisted(ctx, ckks, torch, reps=5, n_ct=4, r=8):
+    """Hoisted rotations (Algorithm 4 with r = 8): 4 ciphertexts at N=2^16, ell=24,
+    each rotated by 5^1..5^8 with its own 8 keys: one batched call (ModUp once per
+    ciphertext, every rotation's inner product and ModDown in one launch per
+    step) against ckks_hrotate per ciphertext on 4 streams."""
+    N = ctx.N
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(ctx.device)
+    s = dev(synth.ternary(N, "bench/hoist/s"))
+    gs = [pow(5, j + 1, 2 * N) for j in range(r)]
+    keys = [_keygen(ctx, torch, s, g, f"bench/hoist/k{j}") for j, g in enumerate(gs)]
+    cts = [(dev(synth.uniform_residues(ctx.q, N, f"bench/hoist/a{c}")),
+            dev(synth.uniform_residues(ctx.q, N, f"bench/hoist/b{c}"))) for c in range(n_ct)]
+    rots = [[(g, k) for g, k in zip(gs, keys)] for _ in range(n_ct)]
+    outs = [[(ctx.empty(L), ctx.empty(L)) for _ in range(r)] for _ in range(n_ct)]
+    t_batch = _timed(torch, lambda: ctx.hrotate_batch(cts, [L] * n_ct, rots, outs=outs), reps)
+    streams = [torch.cuda.Stream() for _ in range(4)]
+    wss = [ctx.workspace(ckks.OP_HROTATE, L, r) for _ in range(4)]
+
+    def four():
+        ev = torch.cuda.current_stream().record_event()
+        for st in streams:
+            st.wait_event(ev)
+        for c in range(n_ct):
+            j = c % 4
+            ctx.hrotate(cts[c][0], cts[c][1], L, gs, keys, outs=outs[c], ws=wss[j], stream=streams[j])
+        for st in streams:
+            torch.cuda.current_stream().wait_stream(st)
+
+    t_four = _timed(torch, four, reps)
+    nrot = n_ct * r
+    comp = (2 * L * n_ct + nrot * 2 * L) * traffic.limb_bytes(N) + r * traffic.key_limbs(L, K_SP, L, DNUM) * \
+        traffic.limb_bytes(N)
+    del keys, cts, outs, wss
+    torch.cuda.empty_cache()
+    return {"shape": f"{n_ct} ciphertexts x {r} hoisted rotations (5^1..5^{r}), N=2^16, ell=24, k=8, dnum=3",
+            "batched": {"ms": t_batch, "rotations_per_s": nrot / t_batch * 1e3},
+            "single_calls_4_streams": {"ms": t_four, "rotations_per_s": nrot / t_four * 1e3},
+            "compulsory_bytes": comp,
+            "hbm_frac_of_measured": comp / (min(t_batch, t_four) * 1e-3) / 1e9 / load_peaks()["hbm_gbs"]}
+
+
 def measure_other_rows(ctx, ckks, torch, reps=5):
     """Rescale (Alg. 1's ModDown_{B,1}) of one ciphertext, and a CoeffToSlot-shaped
     PtMatVecMult: fftIter = 3 levels at ell = 24, 23, 22 (Alg. 8 with 8 baby x 4
@@ -648,6 +689,7 @@ def run_gpu(args, rank, world, local_rank):
             line["other_rows"] = measure_other_rows(ctx, ckks, torch)
             line["other_rows"]["batched_keyswitch"] = measure_batched(ctx, ckks, torch)
             line["other_rows"]["small_keyswitch"] = measure_small_keyswitch(ckks, torch)
+            line["other_rows"]["hoisted_rotations"] = measure_hoisted(ctx, ckks, torch)
             line["other_rows"]["serving"] = measure_serving(ctx, ckks, torch)
         if world == 1 and not args.no_cpu_baseline:
             times = oracle_keyswitch_seconds(1)

@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(256) bconv_kernel(BConvLaunch L, const PrimeIn
 // targets of its group for 256 coefficients; the constants of the group sit
 // in shared memory and every source word is read and scaled exactly once.
 template <int NS, class GMAP>
-__global__ void __launch_bounds__(128) bconv_split_kernel(const __grid_constant__ GMAP gm, int chunks, int chunk,
+__global__ void __launch_bounds__(128, 7) bconv_split_kernel(const __grid_constant__ GMAP gm, int chunks, int chunk,
                                                           const PrimeInfo *__restrict__ pinfo, int logN, int W) {
     extern __shared__ uint4 smat[];  // [n_dst][NS] then the per-target constants
     const BConvGroup G = gm.get(blockIdx.y / chunks);
