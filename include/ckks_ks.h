@@ -390,6 +390,16 @@ int ckks_server_step(ckks_server *srv, int *n_launched);
 int ckks_server_poll(ckks_server *srv, int max, uint64_t *ids, double *latency_ms, double *done_ms, int *n);
 int ckks_server_stats(const ckks_server *srv, ckks_server_stats_t *stats);
 
+/* Asynchronous errors: every call returns after enqueueing its kernels, so a
+ * failure during execution (a CUDA error of an earlier launch) surfaces on a
+ * later call or here.  ckks_poll_status does not block: it returns CKKS_OK
+ * while the stream's work is pending or finished without error (*done, when
+ * given, is 1 once everything enqueued on the stream has finished) and
+ * CKKS_ECUDA with the CUDA error in ckks_last_cuda_error otherwise.  No kernel
+ * of this library waits on a flag, a peer or a queue, so there is no device-side
+ * timeout status to report. */
+int ckks_poll_status(ckks_ctx *ctx, ckks_stream_t stream, int *done);
+
 /* ------------------------------------------------------------------------
  * Measurement hook (no counterpart in the paper).  While enabled, every
  * kernel the context launches is bracketed by a pair of CUDA events recorded

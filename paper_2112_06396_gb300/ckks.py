@@ -100,6 +100,7 @@ _SIGS = {
     "ckks_server_create": (_i, [ctypes.POINTER(_vp), _i, ctypes.c_size_t, _i, _i, ctypes.POINTER(_vp)]),
     "ckks_server_destroy": (_i, [_vp]),
     "ckks_server_add_key": (_i, [_vp, _i, _vp, ctypes.POINTER(_i)]),
+    "ckks_poll_status": (_i, [_vp, _vp, ctypes.POINTER(_i)]),
     "ckks_autotune": (_i, [_vp, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_float)]),
     "ckks_tune_set": (_i, [_vp, ctypes.POINTER(_i)]),
     "ckks_server_add_key_seeded": (_i, [_vp, _i, _vp, ctypes.c_uint64, ctypes.POINTER(_i)]),
@@ -237,14 +238,40 @@ class Context:
             out[name] = (ms.value, int(n.value), u.value)
         return out
 
-    def autotune(self, limbs=128, stream=None):
+    def poll_status(self, stream=None):
+        """True once the stream's work has finished; raises on an asynchronous CUDA error."""
+        done = _i()
+        _check(lib().ckks_poll_status(self._h, _stream(stream), ctypes.byref(done)), self._h)
+        return bool(done.value)
+
+    def autotune(self, limbs=128, stream=None, cache=None):
         """Time the NTT tile shapes and keep the fastest (ckks_autotune).
-        Returns (choice[4], times_ms[12])."""
+        Returns (choice[4], times_ms[12]).  With cache (a JSON file path), a
+        choice stored for this GPU model and parameter shape is applied without
+        timing, and a new one is stored."""
+        import json
+
+        key = None
+        if cache is not None:
+            key = f"{torch.cuda.get_device_name(self.device)}|logN={self.logN}|L={self.L}|k={self.k}|dnum={self.dnum}"
+            try:
+                with open(cache) as f:
+                    saved = json.load(f)
+            except (OSError, ValueError):
+                saved = {}
+            if key in saved:
+                self.tune_set(saved[key]["choice"])
+                return list(saved[key]["choice"]), list(saved[key]["times_ms"])
         ws = torch.empty((limbs, self.N), dtype=torch.uint64, device=self.device)
         ch = (_i * 4)()
         tm = (ctypes.c_float * 12)()
         _check(lib().ckks_autotune(self._h, _p(ws), limbs * self.N * 8, _stream(stream), ch, tm), self._h)
-        return list(ch), list(tm)
+        choice, times = list(ch), list(tm)
+        if cache is not None:
+            saved[key] = {"choice": choice, "times_ms": times}
+            with open(cache, "w") as f:
+                json.dump(saved, f, indent=1)
+        return choice, times
 
     def tune_set(self, choice):
         ch = (_i * 4)(*[int(x) for x in choice])

@@ -11,6 +11,8 @@
 #include "common.cuh"
 #include "internal.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 using namespace ckks;
 
 typedef unsigned __int128 u128;
@@ -343,6 +345,7 @@ extern "C" int ckks_ctx_create(const ckks_params *prm, int device, ckks_ctx **ou
     cudaError_t err = cudaSetDevice(device);
     if (err == cudaSuccess) err = cudaMalloc(&c->d_block, off);
     if (err != cudaSuccess) {
+        cudaGetLastError();  // not sticky: leave no error behind for the caller
         cudaSetDevice(prev);
         delete c;
         return err == cudaErrorMemoryAllocation ? CKKS_ENOMEM : CKKS_ECUDA;
@@ -422,6 +425,15 @@ extern "C" size_t ckks_ctx_table_bytes(const ckks_ctx *c) { return c ? c->table_
         int r_ = (call);                                                                                          \
         if (r_ != CKKS_OK) return r_;                                                                             \
     } while (0)
+
+// An NVTX range per C-ABI operation (visible in Nsight timelines; a no-op when
+// no tool is attached).
+struct OpRange {
+    explicit OpRange(const char *name) { nvtxRangePushA(name); }
+    ~OpRange() { nvtxRangePop(); }
+    OpRange(const OpRange &) = delete;
+    OpRange &operator=(const OpRange &) = delete;
+};
 
 static bool al16(const void *p) { return p != nullptr && (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 static bool level_ok(const ckks_ctx *c, int ell) { return c != nullptr && ell >= 1 && ell <= c->L; }
@@ -750,6 +762,7 @@ extern "C" int ckks_workspace_bytes(const ckks_ctx *c, int op, int ell, int r, s
 
 // ------------------------------------------------------------------ API
 extern "C" int ckks_ntt(ckks_ctx *ctx, uint64_t *d, int ell, int first, int count, ckks_stream_t stream) {
+    OpRange r_("ckks_ntt");
     if (!level_ok(ctx, ell) || !al16(d) || first < 0 || count < 0 || first + count > ell + ctx->k) return CKKS_EINVAL;
     LimbList ll;
     for (int t = first; t < first + count; ++t) ll.add(d + size_t(t) * ctx->N, d + size_t(t) * ctx->N, ext_prime(ctx, ell, t));
@@ -757,6 +770,7 @@ extern "C" int ckks_ntt(ckks_ctx *ctx, uint64_t *d, int ell, int first, int coun
 }
 
 extern "C" int ckks_intt(ckks_ctx *ctx, uint64_t *d, int ell, int first, int count, ckks_stream_t stream) {
+    OpRange r_("ckks_intt");
     if (!level_ok(ctx, ell) || !al16(d) || first < 0 || count < 0 || first + count > ell + ctx->k) return CKKS_EINVAL;
     LimbList ll;
     for (int t = first; t < first + count; ++t) ll.add(d + size_t(t) * ctx->N, d + size_t(t) * ctx->N, ext_prime(ctx, ell, t));
@@ -765,6 +779,7 @@ extern "C" int ckks_intt(ckks_ctx *ctx, uint64_t *d, int ell, int first, int cou
 
 extern "C" int ckks_automorph(ckks_ctx *ctx, const uint64_t *in, uint64_t *out, int nlimbs, uint32_t g,
                               ckks_stream_t stream) {
+    OpRange r_("ckks_automorph");
     if (ctx == nullptr || !al16(in) || !al16(out) || in == out || nlimbs < 0 || nlimbs > 65535 || !galois_ok(ctx, g))
         return CKKS_EINVAL;
     CK(launch_automorph(ctx, in, out, nlimbs, g, (cudaStream_t)stream));
@@ -773,6 +788,7 @@ extern "C" int ckks_automorph(ckks_ctx *ctx, const uint64_t *in, uint64_t *out, 
 
 extern "C" int ckks_modup(ckks_ctx *ctx, const uint64_t *a, int ell, int digit, uint64_t *out, void *ws,
                           ckks_stream_t stream) {
+    OpRange r_("ckks_modup");
     if (!level_ok(ctx, ell) || !al16(a) || !al16(out) || !al16(ws) || digit < 0 || digit >= beta_of(ctx, ell))
         return CKKS_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
@@ -800,6 +816,7 @@ extern "C" int ckks_modup(ckks_ctx *ctx, const uint64_t *a, int ell, int digit, 
 
 extern "C" int ckks_ksk_inner_prod(ckks_ctx *ctx, const uint64_t *digits, int ell, const uint64_t *key, uint64_t *u,
                                    uint64_t *v, ckks_stream_t stream) {
+    OpRange r_("ckks_ksk_inner_prod");
     if (!level_ok(ctx, ell) || !al16(digits) || !al16(key) || !al16(u) || !al16(v)) return CKKS_EINVAL;
     InnerArgs ia{digits, nullptr, key, u, v, ell, 1};
     ia.compressed = key_seed(ctx, key, &ia.seed);
@@ -809,6 +826,7 @@ extern "C" int ckks_ksk_inner_prod(ckks_ctx *ctx, const uint64_t *digits, int el
 
 extern "C" int ckks_moddown(ckks_ctx *ctx, const uint64_t *in, int ell, uint64_t *out, void *ws,
                             ckks_stream_t stream) {
+    OpRange r_("ckks_moddown");
     if (!level_ok(ctx, ell) || !al16(in) || !al16(out) || !al16(ws)) return CKKS_EINVAL;
     u64 *w = static_cast<u64 *>(ws);
     const u64 *ins[2] = {in, nullptr};
@@ -818,6 +836,7 @@ extern "C" int ckks_moddown(ckks_ctx *ctx, const uint64_t *in, int ell, uint64_t
 }
 
 extern "C" int ckks_pmodup(ckks_ctx *ctx, const uint64_t *in, int ell, uint64_t *out, ckks_stream_t stream) {
+    OpRange r_("ckks_pmodup");
     if (!level_ok(ctx, ell) || !al16(in) || !al16(out)) return CKKS_EINVAL;
     CK(launch_pmodup(ctx, in, out, ell, (cudaStream_t)stream));
     return CKKS_OK;
@@ -825,6 +844,7 @@ extern "C" int ckks_pmodup(ckks_ctx *ctx, const uint64_t *in, int ell, uint64_t 
 
 extern "C" int ckks_rescale(ckks_ctx *ctx, const uint64_t *in, int ell, uint64_t *out, void *ws,
                             ckks_stream_t stream) {
+    OpRange r_("ckks_rescale");
     if (!level_ok(ctx, ell) || ell < 2 || !al16(in) || !al16(out) || !al16(ws)) return CKKS_EINVAL;
     u64 *w = static_cast<u64 *>(ws);
     const u64 *ins[2] = {in, nullptr};
@@ -834,12 +854,14 @@ extern "C" int ckks_rescale(ckks_ctx *ctx, const uint64_t *in, int ell, uint64_t
 
 extern "C" int ckks_keyswitch(ckks_ctx *ctx, const uint64_t *a, int ell, const uint64_t *key, uint64_t *u,
                               uint64_t *v, void *ws, ckks_stream_t stream) {
+    OpRange r_("ckks_keyswitch");
     if (!level_ok(ctx, ell) || !al16(a) || !al16(key) || !al16(u) || !al16(v) || !al16(ws)) return CKKS_EINVAL;
     return keyswitch_core(ctx, a, ell, key, 1, u, v, nullptr, 1, 0, static_cast<u64 *>(ws), (cudaStream_t)stream);
 }
 
 extern "C" int ckks_rotate(ckks_ctx *ctx, const uint64_t *a, const uint64_t *b, int ell, uint32_t g,
                            const uint64_t *key, uint64_t *oa, uint64_t *ob, void *ws, ckks_stream_t stream) {
+    OpRange r_("ckks_rotate");
     if (!level_ok(ctx, ell) || !al16(a) || !al16(b) || !al16(key) || !al16(oa) || !al16(ob) || !al16(ws) ||
         !galois_ok(ctx, g))
         return CKKS_EINVAL;
@@ -849,6 +871,7 @@ extern "C" int ckks_rotate(ckks_ctx *ctx, const uint64_t *a, const uint64_t *b, 
 extern "C" int ckks_hrotate(ckks_ctx *ctx, const uint64_t *a, const uint64_t *b, int ell, int r,
                             const uint32_t *galois, const uint64_t *const *keys, uint64_t *const *oa,
                             uint64_t *const *ob, void *ws, ckks_stream_t stream) {
+    OpRange r_("ckks_hrotate");
     if (!level_ok(ctx, ell) || !al16(a) || !al16(b) || !al16(ws) || r < 0 || (r > 0 && (!galois || !keys || !oa || !ob)))
         return CKKS_EINVAL;
     for (int i = 0; i < r; ++i)
@@ -1067,6 +1090,7 @@ static int keyswitch_batch_any(ckks_ctx *ctx, int n, const uint64_t *const *a, c
 extern "C" int ckks_keyswitch_batch(ckks_ctx *ctx, int n, const uint64_t *const *a, const uint64_t *const *b,
                                     const int *levels, const uint32_t *galois, const uint64_t *const *keys,
                                     uint64_t *const *oa, uint64_t *const *ob, void *ws, ckks_stream_t stream) {
+    OpRange r_("ckks_keyswitch_batch");
     return keyswitch_batch_any(ctx, n, a, b, levels, galois, keys, nullptr, oa, ob, ws, stream);
 }
 
@@ -1096,6 +1120,7 @@ extern "C" int ckks_hrotate_batch(ckks_ctx *ctx, int n, const uint64_t *const *a
                                   const int *levels, const int *nrot, const uint32_t *galois,
                                   const uint64_t *const *keys, uint64_t *const *oa, uint64_t *const *ob, void *ws,
                                   ckks_stream_t stream) {
+    OpRange r_("ckks_hrotate_batch");
     if (ctx == nullptr || n < 0) return CKKS_EINVAL;
     if (n == 0) return CKKS_OK;
     if (!a || !b || !levels || !nrot || !galois || !keys || !oa || !ob || !al16(ws)) return CKKS_EINVAL;
@@ -1163,6 +1188,7 @@ extern "C" int ckks_keyswitch_batch_seeded(ckks_ctx *ctx, int n, const uint64_t 
                                            const int *levels, const uint32_t *galois,
                                            const uint64_t *const *keys_b, const uint64_t *seeds, uint64_t *const *oa,
                                            uint64_t *const *ob, void *ws, ckks_stream_t stream) {
+    OpRange r_("ckks_keyswitch_batch_seeded");
     if (seeds == nullptr && n > 0) return CKKS_EINVAL;
     return keyswitch_batch_any(ctx, n, a, b, levels, galois, keys_b, seeds, oa, ob, ws, stream);
 }
@@ -1190,6 +1216,7 @@ extern "C" int ckks_mult_batch(ckks_ctx *ctx, int n, const uint64_t *const *a1, 
                                const uint64_t *const *a2, const uint64_t *const *b2, const int *levels,
                                const uint64_t *const *keys, uint64_t *const *oa, uint64_t *const *ob, void *ws,
                                ckks_stream_t stream) {
+    OpRange r_("ckks_mult_batch");
     return mult_like_batch(ctx, BE_MULT, n, a1, b1, a2, b2, levels, keys, oa, ob, ws, stream);
 }
 
@@ -1205,6 +1232,7 @@ extern "C" int ckks_newmult_batch(ckks_ctx *ctx, int n, const uint64_t *const *a
                                   const uint64_t *const *a2, const uint64_t *const *b2, const int *levels,
                                   const uint64_t *const *keys, uint64_t *const *oa, uint64_t *const *ob, void *ws,
                                   ckks_stream_t stream) {
+    OpRange r_("ckks_newmult_batch");
     return mult_like_batch(ctx, BE_NEWMULT, n, a1, b1, a2, b2, levels, keys, oa, ob, ws, stream);
 }
 
@@ -1220,6 +1248,7 @@ extern "C" int ckks_newmult(ckks_ctx *ctx, const uint64_t *a1, const uint64_t *b
 extern "C" int ckks_newmult_sum(ckks_ctx *ctx, int n, const uint64_t *const *a1, const uint64_t *const *b1,
                                 const uint64_t *const *a2, const uint64_t *const *b2, int level,
                                 const uint64_t *key, uint64_t *oa, uint64_t *ob, void *ws, ckks_stream_t stream) {
+    OpRange r_("ckks_newmult_sum");
     if (ctx == nullptr || n < 1 || n > kMaxCts || !a1 || !b1 || !a2 || !b2 || !level_ok(ctx, level) || level < 2 ||
         !al16(key) || !al16(oa) || !al16(ob) || !al16(ws))
         return CKKS_EINVAL;
@@ -1263,6 +1292,7 @@ extern "C" int ckks_ptmatvecmult(ckks_ctx *ctx, const uint64_t *a, const uint64_
                                  const uint32_t *g_baby, const uint32_t *g_giant, const uint64_t *const *key_baby,
                                  const uint64_t *const *key_giant, const uint64_t *const *diag, int rescale,
                                  uint64_t *oa, uint64_t *ob, void *ws, ckks_stream_t stream) {
+    OpRange r_("ckks_ptmatvecmult");
     if (!level_ok(ctx, ell) || !al16(a) || !al16(b) || !al16(oa) || !al16(ob) || !al16(ws) || nb < 1 ||
         nb > kMaxRot || ng < 1 || diag == nullptr || (rescale && ell < 2))
         return CKKS_EINVAL;
@@ -1320,6 +1350,7 @@ extern "C" int ckks_ptmatvecmult(ckks_ctx *ctx, const uint64_t *a, const uint64_
 
 extern "C" int ckks_keygen_ksk(ckks_ctx *ctx, const int64_t *s, const int64_t *e, const uint64_t *a, uint32_t g,
                                uint64_t *key, void *ws, ckks_stream_t stream) {
+    OpRange r_("ckks_keygen_ksk");
     if (ctx == nullptr || !al16(s) || !al16(e) || !al16(a) || !al16(key) || !al16(ws) || (g != 0 && !galois_ok(ctx, g)))
         return CKKS_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
@@ -1347,6 +1378,7 @@ extern "C" int ckks_keygen_ksk(ckks_ctx *ctx, const int64_t *s, const int64_t *e
 // Compressed keys (Sec. 5.4): only the rows b_j are stored; a_j comes from the seed.
 extern "C" int ckks_keygen_ksk_seeded(ckks_ctx *ctx, const int64_t *s, const int64_t *e, uint64_t seed, uint32_t g,
                                       uint64_t *key_b, void *ws, ckks_stream_t stream) {
+    OpRange r_("ckks_keygen_ksk_seeded");
     if (ctx == nullptr || !al16(s) || !al16(e) || !al16(key_b) || !al16(ws) || (g != 0 && !galois_ok(ctx, g)))
         return CKKS_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
@@ -1373,6 +1405,7 @@ extern "C" int ckks_keygen_ksk_seeded(ckks_ctx *ctx, const int64_t *s, const int
 
 extern "C" int ckks_ksk_expand(ckks_ctx *ctx, const uint64_t *key_b, uint64_t seed, uint64_t *key,
                                ckks_stream_t stream) {
+    OpRange r_("ckks_ksk_expand");
     if (ctx == nullptr || !al16(key_b) || !al16(key) || key_b == key) return CKKS_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t row = size_t(ctx->L + ctx->k) * ctx->N;
@@ -1382,6 +1415,16 @@ extern "C" int ckks_ksk_expand(ckks_ctx *ctx, const uint64_t *key_b, uint64_t se
                            cudaMemcpyDeviceToDevice, st));
     }
     return CKKS_OK;
+}
+
+// ------------------------------------------------------------------ asynchronous errors
+extern "C" int ckks_poll_status(ckks_ctx *ctx, ckks_stream_t stream, int *done) {
+    if (ctx == nullptr) return CKKS_EINVAL;
+    const cudaError_t q = cudaStreamQuery((cudaStream_t)stream);
+    if (done) *done = q == cudaSuccess;
+    if (q == cudaSuccess || q == cudaErrorNotReady) return CKKS_OK;
+    ctx->last_cuda_error = int(q);
+    return CKKS_ECUDA;
 }
 
 // ------------------------------------------------------------------ compressed-key registry
@@ -1399,6 +1442,7 @@ extern "C" int ckks_key_unregister(ckks_ctx *ctx, const uint64_t *key_b) {
 // ------------------------------------------------------------------ autotuner
 extern "C" int ckks_autotune(ckks_ctx *ctx, void *ws, size_t ws_bytes, ckks_stream_t stream, int *choice,
                              float *times) {
+    OpRange r_("ckks_autotune");
     if (ctx == nullptr || !al16(ws)) return CKKS_EINVAL;
     const size_t limb = size_t(ctx->N) * sizeof(u64);
     const int large = int(std::min<size_t>(kMaxBatch, ws_bytes / limb));

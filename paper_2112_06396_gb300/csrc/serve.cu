@@ -92,6 +92,7 @@ extern "C" int ckks_server_create(ckks_ctx *const *ctxs, int nctx, size_t mem_bu
     int prev = 0;
     cudaGetDevice(&prev);
     auto fail = [&](cudaError_t e) {
+        cudaGetLastError();  // an allocation failure is not sticky: clear it for the caller
         cudaSetDevice(prev);
         destroy(s);
         return e == cudaErrorMemoryAllocation ? CKKS_ENOMEM : CKKS_ECUDA;

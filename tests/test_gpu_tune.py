@@ -49,3 +49,23 @@ def test_autotune_picks_a_timed_shape(cfg14):
     with pytest.raises(ckks.CkksError):
         cfg14.ctx.tune_set([0, 3, 0, 0])
     cfg14.ctx.tune_set([0, 0, 0, 0])
+
+
+def test_autotune_cache_round_trip(cfg14, tmp_path):
+    cache = str(tmp_path / "tune.json")
+    ch1, _ = cfg14.ctx.autotune(limbs=32, cache=cache)
+    cfg14.ctx.tune_set([0, 0, 0, 0])
+    ch2, _ = cfg14.ctx.autotune(limbs=32, cache=cache)  # from the cache, no timing
+    assert ch1 == ch2
+    cfg14.ctx.tune_set([0, 0, 0, 0])
+
+
+def test_poll_status_and_allocation_failure(cfg14):
+    ckks = _gpu()
+    st = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    assert cfg14.ctx.poll_status(st) is True
+    # a budget no GPU has: the server's arena allocation fails cleanly
+    with pytest.raises(ckks.CkksError):
+        ckks.Server([cfg14.ctx], 1 << 50, max_batch=4, streams=1)
+    assert cfg14.ctx.poll_status(st) is True  # the context is still usable
