@@ -36,7 +36,7 @@ LOGN, L, K_SP, DNUM, BITS = 16, 24, 8, 3, 54
 METRIC = "KeySwitch ops/s at N=2^16, ell=24, dnum=3"
 UNIT = "KeySwitch/s"
 WORKLOAD = "HRotate(5^r)+KeySwitch N=2^16 ell=24 k=8 dnum=3 54-bit primes"
-STREAMS = 4
+STREAMS = 8
 
 
 def load_peaks():
@@ -707,8 +707,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--batch", type=int, default=8, help="ciphertexts (each with its own key) per step")
-    ap.add_argument("--streams", type=int, default=4, help="CUDA streams the independent ciphertexts are spread over")
+    ap.add_argument("--batch", type=int, default=16, help="ciphertexts (each with its own key) per step")
+    ap.add_argument("--streams", type=int, default=8, help="CUDA streams the independent ciphertexts are spread over")
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-rows", action="store_true", help="skip the Rescale / PtMatVecMult side measurements")
