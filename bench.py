@@ -702,6 +702,31 @@ def run_gpu(args, rank, world, local_rank):
     return 0
 
 
+def run_profile_batch(args):
+    """A small case for ncu: `--profile-batch n` batched KeySwitches at levels
+    uniform in {4..24} (the first n of the 64-entry workload), one shared key,
+    `--warmup` + `--steps` calls; nothing is printed but a completion line."""
+    import torch
+
+    from paper_2112_06396_gb300 import ckks
+
+    primes = ckks.ckks_gen_primes(BITS, LOGN, L + K_SP)
+    ctx = ckks.Context(LOGN, primes[:L], primes[L:], DNUM)
+    N = ctx.N
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(ctx.device)
+    levels = synth.uniform_ints(64, 4, 24, "batch/levels")[:args.profile_batch]
+    s = dev(synth.ternary(N, "bench/batch/s"))
+    key = _keygen(ctx, torch, s, 0, "bench/batch/key")
+    a = [dev(synth.uniform_residues(ctx.q[:ell], N, f"bench/batch/ct{i}")) for i, ell in enumerate(levels)]
+    outs = [(ctx.empty(ell), ctx.empty(ell)) for ell in levels]
+    ws = ctx.batch_workspace(levels)
+    for _ in range(args.warmup + args.steps):
+        ctx.keyswitch_batch(a, None, levels, None, [key] * len(levels), outs=outs, ws=ws)
+    torch.cuda.synchronize()
+    print(f"profile case done: {len(levels)} batched KeySwitches, levels {levels}", flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -713,6 +738,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-rows", action="store_true", help="skip the Rescale / PtMatVecMult side measurements")
     ap.add_argument("--no-tune", action="store_true", help="keep the default NTT tile shapes (no autotuning)")
+    ap.add_argument("--profile-batch", type=int, default=0,
+                    help="profiling case: only run this many batched KeySwitches at uneven levels (no JSON line)")
     args = ap.parse_args()
     global STREAMS
     STREAMS = args.streams
@@ -723,6 +750,8 @@ def main():
         return run_reference(args, rank, world)
     if args.warmup < 3:
         args.warmup = 3
+    if args.profile_batch:
+        return run_profile_batch(args)
     return run_gpu(args, rank, world, local_rank)
 
 
