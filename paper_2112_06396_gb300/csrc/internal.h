@@ -107,9 +107,10 @@ struct InnerArgs {
     u64 *u, *v;          // [ell+k][N]
     int ell;
     uint32_t galois;     // 1 = no automorphism
-    const u64 *padd[2];  // optional [ell][N]: u += P*padd[0], v += P*padd[1] on the chain positions (NewMult)
-    int compressed;      // key = rows b_j only [dnum][L+k][N]; a_j regenerated from seed
-    u64 seed;
+    const u64 *padd[2] = {nullptr, nullptr};  // optional [ell][N]: u += P*padd[0], v += P*padd[1] on the
+                                               // chain positions (NewMult)
+    int compressed = 0;  // key = rows b_j only [dnum][L+k][N]; a_j regenerated from seed
+    u64 seed = 0;
 };
 cudaError_t launch_inner_prod(const ckks_ctx *ctx, const InnerArgs &a, cudaStream_t st);
 cudaError_t launch_inner_prod_batch(const ckks_ctx *ctx, const KsBatchDesc &d, cudaStream_t st);
