@@ -614,16 +614,35 @@ def run_gpu(args, rank, world, local_rank):
         hb.copy_(it["b"].cpu())
     dev_in = [(ctx.empty(L), ctx.empty(L)) for _ in range(C)]
 
+    # copies run on their own streams, in ciphertext order, so the copy engines
+    # stream continuously: ciphertext i's HRotate waits only for its own inputs,
+    # and its outputs leave as soon as it is done
+    h2d, d2h = torch.cuda.Stream(), torch.cuda.Stream()
+
     def e2e_step():
+        cur = torch.cuda.current_stream()
+        ev0 = cur.record_event()
+        h2d.wait_event(ev0)
+        d2h.wait_event(ev0)
         lanes.fork()
-        for i, ((ha, hb), (da, db), it, (oa, ob)) in enumerate(zip(pin_in, dev_in, items, pin_out)):
-            j = i % len(lanes.streams)
-            with torch.cuda.stream(lanes.streams[j]):
+        loaded, done = [], []
+        with torch.cuda.stream(h2d):
+            for (ha, hb), (da, db) in zip(pin_in, dev_in):
                 da.copy_(ha, non_blocking=True)
                 db.copy_(hb, non_blocking=True)
-                ctx.hrotate(da, db, L, [it["g"]], [it["key"]], outs=[(it["oa"], it["ob"])], ws=lanes.ws[j])
+                loaded.append(h2d.record_event())
+        for i, ((da, db), it) in enumerate(zip(dev_in, items)):
+            j = i % len(lanes.streams)
+            st = lanes.streams[j]
+            st.wait_event(loaded[i])
+            ctx.hrotate(da, db, L, [it["g"]], [it["key"]], outs=[(it["oa"], it["ob"])], ws=lanes.ws[j], stream=st)
+            done.append(st.record_event())
+        with torch.cuda.stream(d2h):
+            for i, ((oa, ob), it) in enumerate(zip(pin_out, items)):
+                d2h.wait_event(done[i])
                 oa.copy_(it["oa"], non_blocking=True)
                 ob.copy_(it["ob"], non_blocking=True)
+        cur.wait_stream(d2h)
         lanes.join()
 
     e2e_steps = max(1, min(args.steps, 10))
