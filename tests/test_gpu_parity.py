@@ -291,3 +291,59 @@ def test_keyswitch_repeatable_headline_shape(cfgB):
     ou, ov = S.o.keyswitch(P, P.L, a, key)
     np.testing.assert_array_equal(host(u1), ou)
     np.testing.assert_array_equal(host(v1), ov)
+
+
+# ------------------------------------------------------------------ other ring degrees of the configurations
+def test_serving_ring_degree_n15(oracle_lib):
+    """N=2^15 (the serving loop's second ring degree), 54-bit primes: batched
+    KeySwitch / HRotate entries and Mult against the oracle."""
+    S = Setup(oracle_lib, 15, 9, 3, 3, 54)
+    P = S.P
+    key = S.key(0, "gpu/n15/relin")[0]
+    rot = S.key(5, "gpu/n15/rot5")[0]
+    dk, dr = dev(key), dev(rot)
+    levels = [9, 4, 6]
+    cts = [S.ct(ell, f"gpu/n15/{i}") for i, ell in enumerate(levels)]
+    outs = S.ctx.keyswitch_batch([dev(a) for a, _ in cts], [None, dev(cts[1][1]), None], levels, [1, 5, 1],
+                                 [dk, dr, dk])
+    for i, ell in enumerate(levels):
+        a, b = cts[i]
+        if i == 1:
+            ((ra, rb),) = S.o.hrotate(P, ell, a, b, [5], [rot])
+        else:
+            ra, rb = S.o.keyswitch(P, ell, a, key)
+        np.testing.assert_array_equal(host(outs[i][0]), ra)
+        np.testing.assert_array_equal(host(outs[i][1]), rb)
+    a2, b2 = S.ct(6, "gpu/n15/m2")
+    ma, mb = S.ctx.mult(dev(cts[2][0]), dev(cts[2][1]), dev(a2), dev(b2), 6, dk)
+    ra, rb = S.o.mult(P, 6, cts[2][0], cts[2][1], a2, b2, key)
+    np.testing.assert_array_equal(host(ma), ra)
+    np.testing.assert_array_equal(host(mb), rb)
+
+
+def test_keyswitch_ring_degree_n17(oracle_lib):
+    """N=2^17 (the paper's bootstrapping ring degree), 54-bit primes, small level."""
+    S = Setup(oracle_lib, 17, 4, 2, 2, 54)
+    key = S.key(0, "gpu/n17/relin")[0]
+    a, _ = S.ct(4, "gpu/n17/ct")
+    u, v = S.ctx.keyswitch(dev(a), 4, dev(key))
+    ru, rv = S.o.keyswitch(S.P, 4, a, key)
+    np.testing.assert_array_equal(host(u), ru)
+    np.testing.assert_array_equal(host(v), rv)
+
+
+def test_ptmatvec_headline_shape(cfgB):
+    """PtMatVecMult (2 baby x 2 giant steps, rescaled) at N=2^16, ell=24, k=8, dnum=3."""
+    S = cfgB
+    P = S.P
+    twoN = 2 * P.N
+    g_baby, g_giant = [1, 5], [1, pow(5, 2, twoN)]
+    kb = [None, S.key(5, "gpu/B/pmv/kb")[0]]
+    kg = [None, S.key(g_giant[1], "gpu/B/pmv/kg")[0]]
+    a, b = S.ct(P.L, "gpu/B/pmv/ct")
+    diags = [synth.uniform_residues(P.ext_primes(P.L), P.N, f"gpu/B/pmv/M{d}") for d in range(4)]
+    oa, ob = S.ctx.ptmatvecmult(dev(a), dev(b), P.L, 2, 2, g_baby, g_giant, [None, dev(kb[1])], [None, dev(kg[1])],
+                                [dev(d) for d in diags], rescale=True)
+    ra, rb = S.o.ptmatvec(P, P.L, a, b, 2, 2, g_baby, g_giant, kb, kg, diags, rescale_out=True)
+    np.testing.assert_array_equal(host(oa), ra)
+    np.testing.assert_array_equal(host(ob), rb)
