@@ -366,6 +366,47 @@ def measure_hoisted(ctx, ckks, torch, reps=5, n_ct=4, r=8):
             "hbm_frac_of_measured": comp / (min(t_batch, t_four) * 1e-3) / 1e9 / load_peaks()["hbm_gbs"]}
 
 
+def measure_steps(ctx, ckks, torch, reps=10):
+    """Each step of the path on its own at N=2^16, ell=24, k=8, dnum=3, with its
+    roofline: the transforms in butterflies/s (integer-issue bound), the data
+    movers in GB/s of their compulsory bytes against the measured HBM copy rate."""
+    N = ctx.N
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(ctx.device)
+    hbm = load_peaks()["hbm_gbs"]
+    limb = traffic.limb_bytes(N)
+    ext = L + K_SP
+    x = dev(synth.uniform_residues(ctx.ext_primes(L) * 4, N, "bench/steps/x"))  # 128 limbs
+    out = torch.empty_like(x)
+    rows = {}
+    t = _timed(torch, lambda: (ctx.ntt(x[:ext], L), ctx.intt(x[:ext], L)), reps)
+    bf = 2 * ext * traffic.ntt_butterflies_per_limb(N)
+    rows["ntt_intt"] = {"shape": f"forward + inverse of {ext} limbs", "us": t * 1e3, "gbutterfly_per_s": bf / t / 1e6}
+    t = _timed(torch, lambda: ctx.automorph(x[:2 * L], 5, out=out[:2 * L]), reps)
+    rows["automorph"] = {"shape": f"{2 * L} limbs (a ciphertext), g = 5", "us": t * 1e3,
+                         "hbm_frac_of_measured": 2 * 2 * L * limb / (t * 1e-3) / 1e9 / hbm}
+    a = x[:L]
+    ws_m = ctx.workspace(ckks.OP_MODUP, L)
+    dig = ctx.empty(ext)
+    t = _timed(torch, lambda: ctx.modup(a, L, 0, out=dig, ws=ws_m), reps)
+    rows["modup_one_digit"] = {"shape": f"digit 0 of {L} limbs -> {ext} limbs (8 iNTT, 24 new limbs, 24 NTT)",
+                               "us": t * 1e3}
+    digits = dev(synth.uniform_residues(ctx.ext_primes(L) * DNUM, N, "bench/steps/d"))
+    s = dev(synth.ternary(N, "bench/steps/s"))
+    key = _keygen(ctx, torch, s, 0, "bench/steps/key")
+    u, v = ctx.empty(ext), ctx.empty(ext)
+    t = _timed(torch, lambda: ctx.ksk_inner_prod(digits, L, key, u, v), reps)
+    ip_bytes = (DNUM * ext + traffic.key_limbs(L, K_SP, L, DNUM) + 2 * ext) * limb
+    rows["ksk_inner_prod"] = {"shape": f"beta=3 digits x {ext} positions, key {traffic.key_limbs(L, K_SP, L, DNUM)} limbs",
+                              "us": t * 1e3, "hbm_frac_of_measured": ip_bytes / (t * 1e-3) / 1e9 / hbm}
+    ws_d = ctx.workspace(ckks.OP_MODDOWN, L)
+    md = ctx.empty(L)
+    t = _timed(torch, lambda: ctx.moddown(u, L, out=md, ws=ws_d), reps)
+    rows["moddown"] = {"shape": f"{ext} -> {L} limbs (8 iNTT, conversion, 24 NTT + scale)", "us": t * 1e3}
+    del x, out, digits, key
+    torch.cuda.empty_cache()
+    return rows
+
+
 def measure_other_rows(ctx, ckks, torch, reps=5):
     """Rescale (Alg. 1's ModDown_{B,1}) of one ciphertext, and a CoeffToSlot-shaped
     PtMatVecMult: fftIter = 3 levels at ell = 24, 23, 22 (Alg. 8 with 8 baby x 4
@@ -709,6 +750,7 @@ def run_gpu(args, rank, world, local_rank):
             line["other_rows"]["batched_keyswitch"] = measure_batched(ctx, ckks, torch)
             line["other_rows"]["small_keyswitch"] = measure_small_keyswitch(ckks, torch)
             line["other_rows"]["hoisted_rotations"] = measure_hoisted(ctx, ckks, torch)
+            line["other_rows"]["steps"] = measure_steps(ctx, ckks, torch)
             line["other_rows"]["serving"] = measure_serving(ctx, ckks, torch)
         if world == 1 and not args.no_cpu_baseline:
             times = oracle_keyswitch_seconds(1)
