@@ -447,7 +447,7 @@ def measure_other_rows(ctx, ckks, torch, reps=5):
 
     per_level = [_timed(torch, lambda i=i: level(i), reps) for i in range(3)]
     c2s_ms = _timed(torch, lambda: [level(i) for i in range(3)], reps)
-    # the same three levels with every rotation key compressed (Sec. 5.4): rows b_j
+    # the same three levels with every rotation key compressed (Sec. 5.3): rows b_j
     # only, a_j regenerated from a seed inside the kernels
     full_levels = levels
     levels = []

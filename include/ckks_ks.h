@@ -284,7 +284,7 @@ int ckks_ptmatvecmult(ckks_ctx *ctx, const uint64_t *d_a, const uint64_t *d_b, i
 int ckks_keygen_ksk(ckks_ctx *ctx, const int64_t *d_s, const int64_t *d_e, const uint64_t *d_a, uint32_t galois,
                     uint64_t *d_key, void *ws, ckks_stream_t stream);
 
-/* Compressed keys (Sec. 5.4): the rows a_j of a key are uniformly random, so
+/* Compressed keys (Sec. 5.3): the rows a_j of a key are uniformly random, so
  * they are regenerated from a 64-bit seed where they are used instead of being
  * stored and read; a compressed key is the rows b_j only, [dnum][L+k][N]
  * (half the bytes of a full key).  Element (j, l, n) of a_j is drawn from

@@ -395,7 +395,7 @@ def keygen(P: Params, a, s, sp_eval, e):
 
 
 def prng_key_a(P: Params, seed: int):
-    """The uniform half a of a compressed key: [dnum][L+k][N] from the seed (Sec. 5.4)."""
+    """The uniform half a of a compressed key: [dnum][L+k][N] from the seed (Sec. 5.3)."""
     a = np.zeros((P.dnum, P.L + P.k, P.N), dtype=np.uint64)
     _load().or_prng_key_a_fill(P.c, seed & 0xFFFFFFFFFFFFFFFF, _u(a))
     return a

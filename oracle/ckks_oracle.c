@@ -809,7 +809,7 @@ int or_keygen(const or_params *P, const u64 *a, const int64_t *s, const u64 *sp,
     return 0;
 }
 
-/* Key compression (Sec. 5.4): the uniform half a_j of a key-switching key is
+/* Key compression (Sec. 5.3): the uniform half a_j of a key-switching key is
  * regenerated from a 64-bit seed instead of being stored.  The generator is
  * SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number
  * generators", OOPSLA 2014): draw c of seed s is mix(s + (c + 1) * gamma) with

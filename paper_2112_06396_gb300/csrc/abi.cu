@@ -1375,7 +1375,7 @@ extern "C" int ckks_keygen_ksk(ckks_ctx *ctx, const int64_t *s, const int64_t *e
     return CKKS_OK;
 }
 
-// Compressed keys (Sec. 5.4): only the rows b_j are stored; a_j comes from the seed.
+// Compressed keys (Sec. 5.3): only the rows b_j are stored; a_j comes from the seed.
 extern "C" int ckks_keygen_ksk_seeded(ckks_ctx *ctx, const int64_t *s, const int64_t *e, uint64_t seed, uint32_t g,
                                       uint64_t *key_b, void *ws, ckks_stream_t stream) {
     OpRange r_("ckks_keygen_ksk_seeded");

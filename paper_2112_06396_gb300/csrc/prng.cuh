@@ -1,4 +1,4 @@
-// prng.cuh -- the generator of compressed key-switching keys (Sec. 5.4:
+// prng.cuh -- the generator of compressed key-switching keys (Sec. 5.3:
 // half of a key is uniformly random, so it is regenerated from a short seed
 // instead of being read from HBM).
 //

@@ -1,4 +1,4 @@
-"""Compressed key-switching keys (Sec. 5.4) through the C ABI: the GPU key
+"""Compressed key-switching keys (Sec. 5.3) through the C ABI: the GPU key
 generator, the expansion of a compressed key, and key switching that
 regenerates the uniform key half on chip must give the bits of the oracle's
 full key and of key switching with that full key (tolerance 0)."""

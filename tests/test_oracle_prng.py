@@ -1,4 +1,4 @@
-"""Pins of the key-compression generator (Sec. 5.4): the oracle regenerates
+"""Pins of the key-compression generator (Sec. 5.3): the oracle regenerates
 the uniform half a_j of a key-switching key from a 64-bit seed with SplitMix64
 (Steele, Lea and Flood, OOPSLA 2014) and per-element rejection to [0, q).
 
