@@ -57,7 +57,8 @@ enum {
     CKKS_EINVAL = 1,
     CKKS_ENOMEM = 2,
     CKKS_ECUDA = 3,
-    CKKS_EUNSUPPORTED = 4
+    CKKS_EUNSUPPORTED = 4,
+    CKKS_ETIMEOUT = 5
 };
 
 /* Operation ids for ckks_workspace_bytes(). */
@@ -331,6 +332,16 @@ int ckks_keyswitch_batch_seeded(ckks_ctx *ctx, int n, const uint64_t *const *d_a
 int ckks_autotune(ckks_ctx *ctx, void *ws, size_t ws_bytes, ckks_stream_t stream, int *choice, float *times);
 int ckks_tune_set(ckks_ctx *ctx, const int *choice);
 
+/* Fast basis conversion path (Algorithm 6 and the table "CKKS Subroutines"):
+ * with every prime below 2^56 and at most 16 source limbs (max(alpha, k + 1)),
+ * the conversions of ModUp, ModDown and Rescale run on the tensor cores
+ * (tcgen05 f16 MMA on 8-bit pieces of the residues, exact f32 sums, one
+ * modular reduction per output); otherwise, or after tensor_cores = 0, on the
+ * integer units (32-bit split multiply-adds).  Both give the same residues
+ * bit for bit.  *available (optional) = 1 when the tensor-core form exists
+ * for this context.  Takes effect for later calls. */
+int ckks_bconv_select(ckks_ctx *ctx, int tensor_cores, int *available);
+
 /* ------------------------------------------------------------------------
  * Serving loop (no counterpart in the paper; it serves the paper's operations).
  * A server owns one device arena for request workspace and nstreams CUDA
@@ -395,9 +406,13 @@ int ckks_server_stats(const ckks_server *srv, ckks_server_stats_t *stats);
  * later call or here.  ckks_poll_status does not block: it returns CKKS_OK
  * while the stream's work is pending or finished without error (*done, when
  * given, is 1 once everything enqueued on the stream has finished) and
- * CKKS_ECUDA with the CUDA error in ckks_last_cuda_error otherwise.  No kernel
- * of this library waits on a flag, a peer or a queue, so there is no device-side
- * timeout status to report. */
+ * CKKS_ECUDA with the CUDA error in ckks_last_cuda_error otherwise.  The one
+ * device-side wait of this library, the tensor-core basis conversion waiting
+ * for its own matrix multiplies (an mbarrier), gives up after a bounded number
+ * of polls (about a second), skips its outputs and records the fact in the
+ * context: once the stream's work has finished, ckks_poll_status returns
+ * CKKS_ETIMEOUT for it (once; the record is cleared) and the outputs of that
+ * work are not valid. */
 int ckks_poll_status(ckks_ctx *ctx, ckks_stream_t stream, int *done);
 
 /* ------------------------------------------------------------------------

@@ -24,7 +24,7 @@ _vp = ctypes.c_void_p
 _i = ctypes.c_int
 _lib = None
 
-CKKS_OK, CKKS_EINVAL, CKKS_ENOMEM, CKKS_ECUDA, CKKS_EUNSUPPORTED = 0, 1, 2, 3, 4
+CKKS_OK, CKKS_EINVAL, CKKS_ENOMEM, CKKS_ECUDA, CKKS_EUNSUPPORTED, CKKS_ETIMEOUT = 0, 1, 2, 3, 4, 5
 (OP_MODUP, OP_MODDOWN, OP_KEYSWITCH, OP_ROTATE, OP_HROTATE, OP_RESCALE, OP_PTMATVEC, OP_KEYGEN, OP_MULT,
  OP_NEWMULT, OP_KEYGEN_SEEDED) = range(1, 12)
 
@@ -103,6 +103,7 @@ _SIGS = {
     "ckks_poll_status": (_i, [_vp, _vp, ctypes.POINTER(_i)]),
     "ckks_autotune": (_i, [_vp, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_float)]),
     "ckks_tune_set": (_i, [_vp, ctypes.POINTER(_i)]),
+    "ckks_bconv_select": (_i, [_vp, _i, ctypes.POINTER(_i)]),
     "ckks_server_add_key_seeded": (_i, [_vp, _i, _vp, ctypes.c_uint64, ctypes.POINTER(_i)]),
     "ckks_keygen_ksk_seeded": (_i, [_vp, _vp, _vp, ctypes.c_uint64, ctypes.c_uint32, _vp, _vp, _vp]),
     "ckks_ksk_expand": (_i, [_vp, _vp, ctypes.c_uint64, _vp, _vp]),
@@ -276,6 +277,14 @@ class Context:
     def tune_set(self, choice):
         ch = (_i * 4)(*[int(x) for x in choice])
         _check(lib().ckks_tune_set(self._h, ch))
+
+    def bconv_tensor_cores(self, on=True):
+        """Run the basis conversions on the tensor cores (on) or the integer
+        units (ckks_bconv_select); returns whether the tensor-core form exists
+        for this context."""
+        avail = _i()
+        _check(lib().ckks_bconv_select(self._h, 1 if on else 0, ctypes.byref(avail)))
+        return bool(avail.value)
 
     # ------------------------------------------------------------ memory
     def empty(self, nlimbs):

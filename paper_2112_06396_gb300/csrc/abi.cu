@@ -92,6 +92,7 @@ extern "C" const char *ckks_strerror(int s) {
     case CKKS_ENOMEM: return "out of device memory";
     case CKKS_ECUDA: return "CUDA error (see ckks_last_cuda_error)";
     case CKKS_EUNSUPPORTED: return "unsupported parameters";
+    case CKKS_ETIMEOUT: return "a bounded device-side wait ran out";
     default: return "unknown status";
     }
 }
@@ -305,6 +306,53 @@ extern "C" int ckks_ctx_create(const ckks_params *prm, int device, ckks_ctx **ou
         for (auto &pl : resc) split(pl);
         for (auto &pl : mdrs) split(pl);
     }
+    // tensor-core form of every plan (basis.cu, bconv_tc_kernel): 7-byte
+    // residues (primes below 2^56) and at most 16 sources keep every f32 sum
+    // of byte products below 2^23
+    {
+        const u64 maxp = *std::max_element(primes.begin(), primes.end());
+        const int nsrc = std::max(alpha, k + 1);
+        c->tc_kg = (c->split_bits && maxp < (u64(1) << 56) && nsrc <= 16) ? ((nsrc + 2) & ~1) : 0;
+    }
+    std::vector<uint16_t> tc_img;  // f16 bit patterns
+    std::vector<size_t> tc_off[4];
+    if (c->tc_kg) {
+        const int KG = c->tc_kg;
+        auto f16 = [](unsigned v) -> uint16_t {  // exact below 2048 and for powers of two up to 2^15
+            if (v == 0) return 0;
+            const int e = 31 - __builtin_clz(v);
+            const unsigned mant = e <= 10 ? (v << (10 - e)) : (v >> (e - 10));
+            return uint16_t(((e + 15) << 10) | (mant & 0x3FFu));
+        };
+        // sum of the 2^23 biases of the seven byte columns, as read from the f32 bits
+        const u128 b32 = 0x4B000000u;
+        const u128 bias = b32 * (1 + (1u << 8) + (1u << 16) + (1u << 24)) +
+                          ((b32 * (1 + (1u << 8) + (1u << 16))) << 32);
+        auto prep = [&](BConvPlan &pl) -> size_t {
+            const size_t off0 = tc_img.size() / 8;  // in 16-byte units
+            const int ntp = (pl.n_dst + 1) & ~1;
+            tc_img.resize(tc_img.size() + size_t(ntp) * KG * 64, 0);
+            uint16_t *base = tc_img.data() + off0 * 8;
+            for (int d = 0; d < ntp; ++d) {
+                uint16_t *blk = base + size_t(d) * KG * 64;
+                for (int r = 0; r < 8; ++r) blk[(KG - 1) * 64 + r * 8] = f16(4096);
+                if (d >= pl.n_dst) continue;
+                const u64 t = primes[pl.dst_prime[d]];
+                for (int i = 0; i < pl.n_src; ++i)
+                    for (int j = 0; j < 7; ++j) {
+                        const u64 mj = hmul(pl.mat[d][i] % t, u64(((u128)1 << (8 * j)) % t), t);
+                        for (int r = 0; r < 7; ++r) blk[i * 64 + r * 8 + j] = f16(unsigned(mj >> (8 * r)) & 0xFFu);
+                    }
+                pl.dst_r32[d] = u64(((u128)1 << 32) % t);
+                pl.dst_r32_s[d] = shoup_of(pl.dst_r32[d], t);
+                pl.dst_off[d] = (t - u64((bias + pl.dst_sub[d]) % t)) % t;
+            }
+            return off0;
+        };
+        std::vector<BConvPlan> *kinds[4] = {&modup, &mdown, &resc, &mdrs};
+        for (int kd = 0; kd < 4; ++kd)
+            for (auto &pl : *kinds[kd]) tc_off[kd].push_back(prep(pl));
+    }
     std::vector<ulonglong2> Pinv(LK), Pmod(LK), qlinv(size_t(L + 1) * LK);
     for (int i = 0; i < LK; ++i) {
         const u64 q = primes[i];
@@ -340,6 +388,8 @@ extern "C" int ckks_ctx_create(const ckks_params *prm, int device, ckks_ctx **ou
     const size_t o_qlinv = take(sizeof(ulonglong2) * qlinv.size());
     const size_t o_mdrs = take(sizeof(BConvPlan) * mdrs.size());
     const size_t o_dinv = take(sizeof(ulonglong2) * Dinv.size());
+    const size_t o_tcimg = take(sizeof(uint16_t) * tc_img.size());
+    const size_t o_status = take(sizeof(int));
     int prev = 0;
     cudaGetDevice(&prev);
     cudaError_t err = cudaSetDevice(device);
@@ -363,6 +413,13 @@ extern "C" int ckks_ctx_create(const ckks_params *prm, int device, ckks_ctx **ou
     c->d_qlinv = reinterpret_cast<ulonglong2 *>(base + o_qlinv);
     c->d_mdmerged = reinterpret_cast<BConvPlan *>(base + o_mdrs);
     c->d_Dinv = reinterpret_cast<ulonglong2 *>(base + o_dinv);
+    c->d_tc_img = reinterpret_cast<uint4 *>(base + o_tcimg);
+    c->d_status = reinterpret_cast<int *>(base + o_status);
+    if (c->tc_kg) {
+        std::vector<BConvPlan> *kinds[4] = {&modup, &mdown, &resc, &mdrs};
+        for (int kd = 0; kd < 4; ++kd)
+            for (size_t i = 0; i < kinds[kd]->size(); ++i) (*kinds[kd])[i].tc_img = c->d_tc_img + tc_off[kd][i];
+    }
     struct Up {
         void *dst;
         const void *src;
@@ -377,9 +434,11 @@ extern "C" int ckks_ctx_create(const ckks_params *prm, int device, ckks_ctx **ou
                {c->d_Pmod, Pmod.data(), sizeof(ulonglong2) * LK},
                {c->d_qlinv, qlinv.data(), sizeof(ulonglong2) * qlinv.size()},
                {c->d_mdmerged, mdrs.data(), sizeof(BConvPlan) * mdrs.size()},
-               {c->d_Dinv, Dinv.data(), sizeof(ulonglong2) * Dinv.size()}};
+               {c->d_Dinv, Dinv.data(), sizeof(ulonglong2) * Dinv.size()},
+               {c->d_tc_img, tc_img.data(), sizeof(uint16_t) * tc_img.size()}};
     for (auto &u : ups)
-        if (err == cudaSuccess) err = cudaMemcpy(u.dst, u.src, u.n, cudaMemcpyHostToDevice);
+        if (err == cudaSuccess && u.n) err = cudaMemcpy(u.dst, u.src, u.n, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemset(c->d_status, 0, sizeof(int));
     if (err == cudaSuccess) err = ntt_set_attributes(c);
     cudaSetDevice(prev);
     if (err != cudaSuccess) {
@@ -1422,7 +1481,18 @@ extern "C" int ckks_poll_status(ckks_ctx *ctx, ckks_stream_t stream, int *done) 
     if (ctx == nullptr) return CKKS_EINVAL;
     const cudaError_t q = cudaStreamQuery((cudaStream_t)stream);
     if (done) *done = q == cudaSuccess;
-    if (q == cudaSuccess || q == cudaErrorNotReady) return CKKS_OK;
+    if (q == cudaSuccess) {
+        // a bounded wait that ran out in a finished kernel (read and cleared)
+        int flag = 0;
+        cudaError_t e = cudaMemcpy(&flag, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && flag != 0) e = cudaMemset(ctx->d_status, 0, sizeof(int));
+        if (e != cudaSuccess) {
+            ctx->last_cuda_error = int(e);
+            return CKKS_ECUDA;
+        }
+        return flag ? CKKS_ETIMEOUT : CKKS_OK;
+    }
+    if (q == cudaErrorNotReady) return CKKS_OK;
     ctx->last_cuda_error = int(q);
     return CKKS_ECUDA;
 }
@@ -1461,6 +1531,13 @@ extern "C" int ckks_tune_set(ckks_ctx *ctx, const int *choice) {
     for (int i = 0; i < 4; ++i)
         if (choice[i] < 0 || choice[i] > 2) return CKKS_EINVAL;
     for (int i = 0; i < 4; ++i) ctx->ntt_csel[i / 2][i % 2] = choice[i];
+    return CKKS_OK;
+}
+
+extern "C" int ckks_bconv_select(ckks_ctx *ctx, int tensor_cores, int *available) {
+    if (ctx == nullptr) return CKKS_EINVAL;
+    if (available) *available = ctx->tc_kg != 0;
+    ctx->tc_on = tensor_cores != 0;
     return CKKS_OK;
 }
 

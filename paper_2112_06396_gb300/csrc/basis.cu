@@ -11,6 +11,7 @@
 #include "batch.cuh"
 #include "common.cuh"
 #include "internal.h"
+#include "tc.cuh"
 
 #include <algorithm>
 
@@ -155,12 +156,185 @@ __global__ void __launch_bounds__(128, 7) bconv_split_kernel(const __grid_consta
     }
 }
 
+// Tensor-core variant (tcgen05).  The conversion of 128 coefficients to a
+// chunk of targets is a matrix product over the integers: with the reduced
+// y_i cut into bytes y_ij (j = 0..6, y < 2^56) and M_tij = [2^(8j) C_ti]_t cut
+// into bytes m_tijc,
+//   sum_i y_i C_ti == sum_c 2^(8c) S_tc  (mod t),  S_tc = sum_ij y_ij m_tijc,
+// and every S_tc (at most 16 sources: below 112 * 255^2 < 2^23) is an exact
+// integer in f16 x f16 -> f32 arithmetic.  A (128 coefficients x 8 KG bytes,
+// f16) is built in shared memory from the sources; B (targets x 8 rows c, same
+// K) is the plan's precomputed image; the f32 sums land in tensor memory,
+// column 8t + c of the coefficient's lane.  A constant column (2048 in A, 4096
+// in B) adds 2^23 to every sum, so the bits of the f32 result read as the
+// integer 0x4B000000 + S_tc with no conversion; the epilogue combines the
+// seven columns of a target with wide multiply-adds into lo + hi * 2^32,
+// folds hi by [2^32]_t, adds the plan's dst_off (which removes the biases and
+// sub_t) and reduces once: the output is in [0, 3t) for the lazy forward NTT.
+constexpr uint32_t kTcWaitPolls = 1u << 24;  // about a second of 64 ns sleeps
+
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+// bytes 2k, 2k+1 of w as two f16 values: (0x6400 | byte) is the f16 1024 + byte,
+// and subtracting 1024 is exact
+__device__ __forceinline__ uint32_t byte_pair_f16(uint32_t w, uint32_t sel) {
+    uint32_t d;
+    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(prmt(w, 0x64646464u, sel)), "r"(0x64006400u));
+    return d;
+}
+
+template <int KG, class GMAP>
+__global__ void __launch_bounds__(256, 2) bconv_tc_kernel(const __grid_constant__ GMAP gm, int chunks, int chunk,
+                                                         const PrimeInfo *__restrict__ pinfo, int logN,
+                                                         int *__restrict__ status) {
+    extern __shared__ __align__(1024) uint4 tsm[];
+    __shared__ uint64_t mbar;
+    __shared__ uint32_t tslot;
+    struct Dst {
+        u64 p, one_s, r32, r32_s, off;
+        uint32_t pos, pad;
+    };
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const BConvGroup G = gm.get(blockIdx.y / chunks);
+    const BConvPlan *__restrict__ plan = G.plan;
+    const uint32_t N = 1u << logN;
+    const int t0 = (blockIdx.y % chunks) * chunk;
+    const int nd = min(plan->n_dst - t0, chunk);
+    if (nd <= 0) return;
+    const int ntp = (nd + 1) & ~1;  // N of the MMA = 8 * ntp, a multiple of 16
+    const int n_src = plan->n_src;
+    uint4 *As = tsm;                                        // [16 row groups][KG][8 rows]
+    uint4 *Bs = tsm + 128 * KG;                             // [ntp][KG][8 rows]
+    Dst *sd = reinterpret_cast<Dst *>(Bs + size_t(ntp) * KG * 8);  // [chunk]
+
+    if (warp == 0) tc::tmem_alloc(&tslot, 256);
+    if (tid == 32) tc::mbar_init(&mbar, 1);
+    const uint4 *__restrict__ img = plan->tc_img + size_t(t0) * KG * 8;
+    for (int i = tid; i < ntp * KG * 8; i += blockDim.x) Bs[i] = img[i];
+    for (int t = tid; t < nd; t += blockDim.x) {
+        const int tt = t0 + t;
+        const PrimeInfo &P = pinfo[plan->dst_prime[tt]];
+        sd[t] = Dst{P.p, P.one_s, plan->dst_r32[tt], plan->dst_r32_s[tt], plan->dst_off[tt], plan->dst_pos[tt], 0};
+    }
+    // A: row m is coefficient n0 + m; group g < n_src holds the bytes of the
+    // reduced y_g (see bconv_split_kernel: the representative matters), group
+    // KG-1 the bias entry, the rest zeros
+    const uint32_t n0 = blockIdx.x * 128u;
+    {
+        const int m = tid & 127;
+        uint4 *row = As + (m >> 3) * (KG * 8) + (m & 7);
+        for (int g = tid >> 7; g < KG; g += 2) {
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (g < n_src) {
+                const u64 q = pinfo[plan->src_prime[g]].p, nq = u64(0) - q;
+                const u64 x = G.src[size_t(g) * N + n0 + m];
+                const u64 y =
+                    csub(csub(shoup_approx(x + plan->src_add[g], plan->src_mul[g], plan->src_mul_s[g], nq), 2 * q), q);
+                const uint32_t w0 = uint32_t(y), w1 = uint32_t(y >> 32);
+                v = make_uint4(byte_pair_f16(w0, 0x4140u), byte_pair_f16(w0, 0x4342u), byte_pair_f16(w1, 0x4140u),
+                               byte_pair_f16(w1, 0x4342u));
+            } else if (g == KG - 1) {
+                v.x = 0x6800u;  // f16 2048
+            }
+            row[g * 8] = v;
+        }
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = tslot;
+    if (tid == 0) {
+        const uint32_t a0 = tc::smem_addr(As), b0 = tc::smem_addr(Bs);
+        const uint32_t idesc = tc::idesc_f16_f32(128, 8 * ntp);
+#pragma unroll
+        for (int s = 0; s < KG / 2; ++s)
+            tc::mma_f16(taddr, tc::desc_kmajor(a0 + 256u * s, 128u, 128u * KG),
+                        tc::desc_kmajor(b0 + 256u * s, 128u, 128u * KG), idesc, s > 0);
+        tc::mma_commit(&mbar);
+    }
+    bool ok = tc::mbar_wait(&mbar, 0, kTcWaitPolls);
+    tc::fence_after_sync();
+    if (ok) {
+        // warp w reads lanes 32*(w % 4) .. +31 (its coefficients) for half the targets
+        const int quarter = warp & 3, half = warp >> 2;
+        const int h0 = (nd + 1) >> 1;
+        const int tb = half ? h0 : 0, te = half ? nd : h0;
+        const uint32_t laddr = taddr + (uint32_t(quarter * 32) << 16);
+        const uint32_t n = n0 + uint32_t(quarter * 32 + lane);
+        for (int t = tb; t < te; t += 2) {
+            uint32_t r[16];
+            tc::tmem_ld16(laddr + uint32_t(t * 8), r);
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                if (t + j >= te) break;
+                const Dst &d = sd[t + j];
+                const uint32_t *b = r + 8 * j;
+                u64 lo = b[0], hi = b[4];
+                mad_wide(lo, b[1], 1u << 8);
+                mad_wide(lo, b[2], 1u << 16);
+                mad_wide(lo, b[3], 1u << 24);
+                mad_wide(hi, b[5], 1u << 8);
+                mad_wide(hi, b[6], 1u << 16);
+                const u64 np = u64(0) - d.p;
+                const u64 v = shoup_one(lo + shoup_approx(hi, d.r32, d.r32_s, np) + d.off, d.one_s, np);
+                G.dst[size_t(d.pos) * N + n] = v;
+            }
+        }
+    } else {
+        if (lane == 0) atomicOr(status, 1);
+        // the multiplies may still be running: wait once more before freeing their memory
+        tc::mbar_wait(&mbar, 0, kTcWaitPolls);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(taddr, 256);
+}
+
+template <int KG, class GMAP>
+static void launch_tc_kg(const ckks_ctx *ctx, const GMAP &gm, int ngroups, int chunks, int chunk, cudaStream_t st) {
+    const int ntp = (chunk + 1) & ~1;
+    // at least 80 KiB: no more than two CTAs share an SM, as many as fit their
+    // 256 tensor-memory columns (a third would wait inside tcgen05.alloc)
+    const size_t need = (size_t(128) * KG + size_t(ntp) * KG * 8) * sizeof(uint4) + size_t(chunk) * 48;
+    const size_t smem = std::max<size_t>(need, 80 * 1024);
+    auto kern = bconv_tc_kernel<KG, GMAP>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    dim3 grid(unsigned(ctx->N / 128), unsigned(ngroups * chunks));
+    kern<<<grid, 256, smem, st>>>(gm, chunks, chunk, ctx->d_pinfo, ctx->logN, ctx->d_status);
+}
+
+// Tensor-core conversion over `ngroups` groups of up to n_all targets each,
+// in chunks of at most 32 targets (256 tensor-memory columns).
+template <class GMAP>
+static cudaError_t launch_tc(const ckks_ctx *ctx, const GMAP &gm, int ngroups, int n_all, cudaStream_t st) {
+    const int chunks = (n_all + 31) / 32;
+    const int chunk = (n_all + chunks - 1) / chunks;
+    ProfScope ps(ctx, K_BCONV, double(ngroups) * n_all, st);
+    switch (ctx->tc_kg) {
+    case 4: launch_tc_kg<4>(ctx, gm, ngroups, chunks, chunk, st); break;
+    case 6: launch_tc_kg<6>(ctx, gm, ngroups, chunks, chunk, st); break;
+    case 8: launch_tc_kg<8>(ctx, gm, ngroups, chunks, chunk, st); break;
+    case 10: launch_tc_kg<10>(ctx, gm, ngroups, chunks, chunk, st); break;
+    case 12: launch_tc_kg<12>(ctx, gm, ngroups, chunks, chunk, st); break;
+    case 14: launch_tc_kg<14>(ctx, gm, ngroups, chunks, chunk, st); break;
+    case 16: launch_tc_kg<16>(ctx, gm, ngroups, chunks, chunk, st); break;
+    case 18: launch_tc_kg<18>(ctx, gm, ngroups, chunks, chunk, st); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 // Split conversion over `ngroups` groups of up to n_all targets each: targets
 // in chunks of at most 12 per CTA row (enough CTAs to fill the SMs while each
 // source word is still scaled once per 12 targets).
 template <class GMAP>
 static cudaError_t launch_split(const ckks_ctx *ctx, const GMAP &gm, int ngroups, int n_all, int max_src,
                                 cudaStream_t st) {
+    if (ctx->tc_kg && ctx->tc_on) return launch_tc(ctx, gm, ngroups, n_all, st);
     const int chunks = (n_all + 11) / 12;
     const int chunk = (n_all + chunks - 1) / chunks;
     const int tpb = 128;

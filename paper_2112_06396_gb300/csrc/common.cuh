@@ -227,6 +227,15 @@ struct BConvPlan {
     // Dh*2^W + Dl: matw = (Dh, Ch, Dl, Cl).
     uint4 matw[kMaxDst][kMaxSrc];
     u64 dst_rw[kMaxDst], dst_rw_s[kMaxDst];  // [2^W]_t, Shoup companion
+    // Tensor-core form (primes below 2^56, at most 16 sources): tc_img holds,
+    // per target t (n_dst rounded up to even), KG groups of an 8 x 8 f16 core
+    // matrix, row c and column j of group i < n_src being byte c of
+    // [2^(8j) * mat[t][i]]_t, group KG-1 holding 4096 in column 0 of every row
+    // (with the 2048 in the A operand: the bias 2^23 of every sum).  The
+    // epilogue adds dst_off = [-bias - sub_t]_t and folds the high word with
+    // dst_r32 = [2^32]_t.
+    const uint4 *tc_img;
+    u64 dst_r32[kMaxDst], dst_r32_s[kMaxDst], dst_off[kMaxDst];
 };
 
 struct BConvGroup {

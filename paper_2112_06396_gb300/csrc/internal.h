@@ -14,6 +14,8 @@ struct ckks_ctx {
     int logN, N, L, k, dnum, alpha;
     bool small_primes;                // every prime < 2^57: lazy NTT without conditional subtractions
     int split_bits;                   // W of the split basis conversion, 0 if primes are too large for it
+    int tc_kg;                        // K groups of the tensor-core basis conversion, 0 if not available
+    bool tc_on = true;                // use it when available (ckks_tune_set can switch it off)
     std::vector<u64> primes;          // L + k: q_0..q_{L-1}, p_0..p_{k-1}
     // device tables (one allocation)
     void *d_block;
@@ -30,6 +32,8 @@ struct ckks_ctx {
     ulonglong2 *d_qlinv;              // [(L+1)*(L+k)]: [q_{ell-1}^-1]_{q_i} at ell*(L+k) + i
     ulonglong2 *d_Dinv;               // [(L+1)*(L+k)]: [(P q_{ell-1})^-1]_{q_i} at ell*(L+k) + i
     int last_cuda_error;
+    int *d_status;                    // device word: bit 0 set when a kernel's bounded wait ran out
+    uint4 *d_tc_img;                  // tensor-core operand images of every plan
     // NTT tile shape per pass (0 column, 1 block) and batch class (count <=
     // kTuneSmallBatch, larger): 0 default width, 1 half, 2 double (ntt_autotune)
     int ntt_csel[2][2] = {{0, 0}, {0, 0}};

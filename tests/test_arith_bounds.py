@@ -90,3 +90,80 @@ def test_split_conversion_accumulator_bound():
         n_src = 32
         prod_max = ((1 << (W + 2)) - 1) * ((1 << W) - 1)  # yh < 2^(W+2) with y < 3q, constants < 2^W
         assert 2 * n_src * prod_max < (1 << 62)
+
+
+# ---------------------------------------------------------------- tensor-core basis conversion
+def _f16_bits(v):
+    """The host encoder of byte values in bconv_tc_kernel's operand images (exact below 2048)."""
+    if v == 0:
+        return 0
+    e = v.bit_length() - 1
+    mant = v << (10 - e) if e <= 10 else v >> (e - 10)
+    return ((e + 15) << 10) | (mant & 0x3FF)
+
+
+def test_tc_operand_encodings_are_exact():
+    np = pytest.importorskip("numpy")
+    for v in list(range(256)) + [2048, 4096]:
+        assert np.array([v], dtype=np.float16).view(np.uint16)[0] == _f16_bits(v)
+    # device side: (0x6400 | b) is the f16 1024 + b; subtracting 1024 leaves b exactly
+    for b in range(256):
+        h = np.array([0x6400 | b], dtype=np.uint16).view(np.float16)[0]
+        assert float(h) == 1024 + b and float(np.float16(h - np.float16(1024))) == b
+    assert 2048.0 * 4096.0 == 2.0 ** 23
+
+
+def _tc_convert(ys, Cs, t, sub):
+    """bconv_tc_kernel for one coefficient and one target t: byte products summed
+    as the tensor core does (integers, every partial sum exact in f32), the f32
+    bits read as integers, the epilogue's lo/hi combination, fold and reduction."""
+    import struct
+
+    S = [0] * 8
+    for y, C in zip(ys, Cs):
+        for j in range(7):
+            mj = ((1 << (8 * j)) * C) % t
+            yj = (y >> (8 * j)) & 0xFF
+            for c in range(7):
+                S[c] += yj * ((mj >> (8 * c)) & 0xFF)
+    bits = []
+    for c in range(7):
+        f = 2.0 ** 23 + S[c]
+        assert f < 2.0 ** 24  # every partial sum is an exact f32 integer
+        b = struct.unpack("<I", struct.pack("<f", f))[0]
+        assert b == 0x4B000000 + S[c]
+        bits.append(b)
+    lo = bits[0] + (bits[1] << 8) + (bits[2] << 16) + (bits[3] << 24)
+    hi = bits[4] + (bits[5] << 8) + (bits[6] << 16)
+    assert lo < 1 << 56 and hi < 1 << 48
+    bias = 0x4B000000 * (1 + (1 << 8) + (1 << 16) + (1 << 24)) + ((0x4B000000 * (1 + (1 << 8) + (1 << 16))) << 32)
+    off = (t - (bias + sub) % t) % t
+    r32 = (1 << 32) % t
+    _, _, fold = shoup_approx(hi, r32, t)
+    v = lo + fold + off
+    assert v < 1 << 64
+    _, out = shoup_one(v, t)
+    return out
+
+
+@pytest.mark.parametrize("bits,nsrc", [(54, 9), (54, 16), (55, 16), (50, 4)])
+def test_tc_conversion_arithmetic(bits, nsrc):
+    rng = random.Random(bits * 100 + nsrc)
+    for trial in range(60):
+        t = rng.randrange(1 << (bits - 1), 1 << bits) | 1
+        qs = [rng.randrange(1 << (bits - 1), 1 << bits) | 1 for _ in range(nsrc)]
+        if trial % 3 == 0:  # largest byte sums: every byte of y and of M' near 255
+            t = (1 << bits) - rng.randrange(1, 1000, 2)
+            ys = [q - 1 for q in qs]
+        else:
+            ys = [rng.randrange(q) for q in qs]
+        Cs = [rng.randrange(t) for _ in range(nsrc)]
+        sub = rng.randrange(t)
+        out = _tc_convert(ys, Cs, t, sub)
+        assert out < 3 * t
+        assert out % t == (sum(y * C for y, C in zip(ys, Cs)) - sub) % t
+
+
+def test_tc_byte_sums_stay_below_two_to_23_at_sixteen_sources():
+    # the bound the kernel relies on: 16 sources x 7 bytes x 255^2
+    assert 16 * 7 * 255 * 255 < 2 ** 23

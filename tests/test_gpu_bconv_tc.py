@@ -1,0 +1,125 @@
+"""The two paths of the fast basis conversion (Algorithm 6 and the table "CKKS
+Subroutines"): on the tensor cores (tcgen05 f16 MMA on byte pieces of the
+residues, exact f32 sums, one reduction per output) and on the integer units
+(32-bit split multiply-adds).  Both must give the oracle's residues bit for bit
+(tolerance 0) in every operation that converts: ModUp, ModDown, Rescale, the
+merged ModDown of NewMult and the batched KeySwitch."""
+import numpy as np
+import pytest
+
+import synth
+from tests.test_gpu_parity import Setup, _gpu, dev, host
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+# (logN, L, k, dnum, bits): tensor-core K groups 6, 6, 8 (54-bit primes, the
+# widest of the integer path too) and 18 (alpha = 16 sources, the largest supported)
+SHAPES = [(12, 6, 3, 2, 50), (11, 7, 3, 3, 50), (11, 10, 5, 2, 54), (11, 32, 8, 2, 50)]
+
+
+@pytest.fixture(scope="module", params=SHAPES, ids=lambda s: "n%d_L%d_k%d_d%d_b%d" % s)
+def S(request, oracle_lib):
+    return Setup(oracle_lib, *request.param)
+
+
+def _both(ctx, fn):
+    """fn() on the tensor cores, then on the integer units (host copies)."""
+    try:
+        assert ctx.bconv_tensor_cores(True)
+        a = fn()
+        ctx.bconv_tensor_cores(False)
+        b = fn()
+    finally:
+        ctx.bconv_tensor_cores(True)
+    return a, b
+
+
+def _h(x):
+    return [host(t) for t in x] if isinstance(x, (tuple, list)) else host(x)
+
+
+def test_modup_moddown_rescale(S):
+    P, ctx = S.P, S.ctx
+    for ell in sorted({P.L, P.L - 1, P.alpha + 1, 2}):
+        a = synth.uniform_residues(P.primes[:ell], P.N, f"gpu/tc/modup/{ell}")
+        da = dev(a)
+        for j in range(P.beta(ell)):
+            tc, sp = _both(ctx, lambda: host(ctx.modup(da, ell, j)))
+            np.testing.assert_array_equal(tc, sp, err_msg=f"modup ell={ell} j={j}")
+            np.testing.assert_array_equal(tc, S.o.modup(P, ell, j, a), err_msg=f"modup ell={ell} j={j}")
+        x = synth.uniform_residues(P.ext_primes(ell), P.N, f"gpu/tc/moddown/{ell}")
+        dx = dev(x)
+        tc, sp = _both(ctx, lambda: host(ctx.moddown(dx, ell)))
+        np.testing.assert_array_equal(tc, sp, err_msg=f"moddown ell={ell}")
+        np.testing.assert_array_equal(tc, S.o.moddown(P, ell, x), err_msg=f"moddown ell={ell}")
+        y = synth.uniform_residues(P.primes[:ell], P.N, f"gpu/tc/rescale/{ell}")
+        dy = dev(y)
+        tc, sp = _both(ctx, lambda: host(ctx.rescale(dy, ell)))
+        np.testing.assert_array_equal(tc, sp, err_msg=f"rescale ell={ell}")
+        np.testing.assert_array_equal(tc, S.o.rescale(P, ell, y), err_msg=f"rescale ell={ell}")
+    assert ctx.poll_status()
+
+
+def test_newmult_merged_moddown(S):
+    P, ctx = S.P, S.ctx
+    key = S.key(0, "gpu/tc/relin")[0]
+    dkey = dev(key)
+    ell = P.L
+    a1, b1 = S.ct(ell, "gpu/tc/m1")
+    a2, b2 = S.ct(ell, "gpu/tc/m2")
+    d = [dev(v) for v in (a1, b1, a2, b2)]
+    tc, sp = _both(ctx, lambda: _h(ctx.mult(*d, ell, dkey, new=True)))
+    ra, rb = S.o.newmult(P, ell, a1, b1, a2, b2, key)
+    for got in (tc, sp):
+        np.testing.assert_array_equal(got[0], ra)
+        np.testing.assert_array_equal(got[1], rb)
+
+
+def test_batched_keyswitch(S):
+    P, ctx = S.P, S.ctx
+    key = S.key(0, "gpu/tc/bks")[0]
+    dkey = dev(key)
+    levels = synth.uniform_ints(6, 1, P.L, f"gpu/tc/bks/{P.logN}/{P.L}")
+    a = [S.ct(ell, f"gpu/tc/bks/{i}")[0] for i, ell in enumerate(levels)]
+    da = [dev(x) for x in a]
+    tc, sp = _both(ctx, lambda: [_h(o) for o in ctx.keyswitch_batch(da, None, levels, None, [dkey] * len(levels))])
+    for i, ell in enumerate(levels):
+        np.testing.assert_array_equal(tc[i][0], sp[i][0], err_msg=f"entry {i}")
+        np.testing.assert_array_equal(tc[i][1], sp[i][1], err_msg=f"entry {i}")
+    i = levels.index(max(levels))
+    ru, rv = S.o.keyswitch(P, levels[i], a[i], key)
+    np.testing.assert_array_equal(tc[i][0], ru)
+    np.testing.assert_array_equal(tc[i][1], rv)
+
+
+def test_availability(oracle_lib):
+    ckks = _gpu()
+    wide = oracle_lib.gen_primes(58, 11, 6)
+    ctx = ckks.Context(11, wide[:4], wide[4:], 2)
+    assert not ctx.bconv_tensor_cores(True)  # 58-bit primes: integer path only
+    many = oracle_lib.gen_primes(50, 11, 40)
+    ctx = ckks.Context(11, many[:34], many[34:], 2)
+    assert not ctx.bconv_tensor_cores(True)  # alpha = 17 sources
+
+
+@pytest.fixture(scope="module")
+def cfgB(oracle_lib):
+    return Setup(oracle_lib, 16, 24, 8, 3, 54)
+
+
+def test_headline_shape(cfgB):
+    """HRotate at N=2^16, ell=24, k=8, dnum=3: both paths equal and the oracle."""
+    S = cfgB
+    P, ctx = S.P, S.ctx
+    g = 5
+    key = S.key(g, "gpu/tc/B/key5")[0]
+    a, b = S.ct(P.L, "gpu/tc/B/ct")
+    da, db, dk = dev(a), dev(b), dev(key)
+    tc, sp = _both(ctx, lambda: _h(ctx.hrotate(da, db, P.L, [g], [dk])[0]))
+    np.testing.assert_array_equal(tc[0], sp[0])
+    np.testing.assert_array_equal(tc[1], sp[1])
+    (ra, rb), = S.o.hrotate(P, P.L, a, b, [g], [key])
+    np.testing.assert_array_equal(tc[0], ra)
+    np.testing.assert_array_equal(tc[1], rb)
+    assert ctx.poll_status()
