@@ -402,6 +402,29 @@ def measure_steps(ctx, ckks, torch, reps=10):
     md = ctx.empty(L)
     t = _timed(torch, lambda: ctx.moddown(u, L, out=md, ws=ws_d), reps)
     rows["moddown"] = {"shape": f"{ext} -> {L} limbs (8 iNTT, conversion, 24 NTT + scale)", "us": t * 1e3}
+
+    # the basis conversion alone (measurement hook), on the tensor cores and on
+    # the integer units, inside ModUp (8 -> 24 limbs) and ModDown (8 -> 24)
+    def conv_us(fn):
+        ctx.profile(True)
+        ctx.profile_reset()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        ms, n, _ = ctx.profile_read()["bconv"]
+        ctx.profile(False)
+        return ms / max(n, 1) * 1e3
+
+    conv = {}
+    for name, on in (("tensor_cores", True), ("integer_units", False)):
+        ctx.bconv_tensor_cores(on)
+        conv[name] = {"modup_digit_us": conv_us(lambda: ctx.modup(a, L, 0, out=dig, ws=ws_m)),
+                      "moddown_us": conv_us(lambda: ctx.moddown(u, L, out=md, ws=ws_d)),
+                      "modup_one_digit_total_us": _timed(torch, lambda: ctx.modup(a, L, 0, out=dig, ws=ws_m), reps) * 1e3,
+                      "moddown_total_us": _timed(torch, lambda: ctx.moddown(u, L, out=md, ws=ws_d), reps) * 1e3}
+    ctx.bconv_tensor_cores(True)
+    rows["basis_conversion"] = {"shape": "8 source limbs -> 24 target limbs of N=2^16 (one ModUp digit; the P "
+                                         "limbs of one polynomial in ModDown)", **conv}
     del x, out, digits, key
     torch.cuda.empty_cache()
     return rows

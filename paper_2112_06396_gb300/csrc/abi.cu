@@ -324,13 +324,18 @@ extern "C" int ckks_ctx_create(const ckks_params *prm, int device, ckks_ctx **ou
             const unsigned mant = e <= 10 ? (v << (10 - e)) : (v >> (e - 10));
             return uint16_t(((e + 15) << 10) | (mant & 0x3FFu));
         };
-        // sum of the 2^23 biases of the seven byte columns, as read from the f32 bits
-        const u128 b32 = 0x4B000000u;
-        const u128 bias = b32 * (1 + (1u << 8) + (1u << 16) + (1u << 24)) +
-                          ((b32 * (1 + (1u << 8) + (1u << 16))) << 32);
+        // the epilogue's sum lo = sum_{c<5} 2^(8c) S_c + fold (< 2t) + off (< t)
+        // stays below 8t, the lazy forward NTT's input bound, when lo < 5t for
+        // the smallest prime; otherwise the epilogue reduces once more
+        {
+            const u128 smax = u128(std::max(alpha, k + 1)) * 7 * 255 * 255;
+            const u128 lo_max = smax * (u128(1) + (1u << 8) + (1u << 16) + (1u << 24) + (u128(1) << 32));
+            const u64 tmin = *std::min_element(primes.begin(), primes.end());
+            c->tc_lazy = lo_max < u128(5) * tmin;
+        }
         auto prep = [&](BConvPlan &pl) -> size_t {
             const size_t off0 = tc_img.size() / 8;  // in 16-byte units
-            const int ntp = (pl.n_dst + 1) & ~1;
+            const int ntp = (pl.n_dst + 3) & ~3;
             tc_img.resize(tc_img.size() + size_t(ntp) * KG * 64, 0);
             uint16_t *base = tc_img.data() + off0 * 8;
             for (int d = 0; d < ntp; ++d) {
@@ -343,9 +348,9 @@ extern "C" int ckks_ctx_create(const ckks_params *prm, int device, ckks_ctx **ou
                         const u64 mj = hmul(pl.mat[d][i] % t, u64(((u128)1 << (8 * j)) % t), t);
                         for (int r = 0; r < 7; ++r) blk[i * 64 + r * 8 + j] = f16(unsigned(mj >> (8 * r)) & 0xFFu);
                     }
-                pl.dst_r32[d] = u64(((u128)1 << 32) % t);
-                pl.dst_r32_s[d] = shoup_of(pl.dst_r32[d], t);
-                pl.dst_off[d] = (t - u64((bias + pl.dst_sub[d]) % t)) % t;
+                pl.dst_r40[d] = u64(((u128)1 << 40) % t);
+                pl.dst_r40_s[d] = shoup_of(pl.dst_r40[d], t);
+                pl.dst_off[d] = (t - pl.dst_sub[d] % t) % t;
             }
             return off0;
         };
@@ -393,6 +398,7 @@ extern "C" int ckks_ctx_create(const ckks_params *prm, int device, ckks_ctx **ou
     int prev = 0;
     cudaGetDevice(&prev);
     cudaError_t err = cudaSetDevice(device);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
     if (err == cudaSuccess) err = cudaMalloc(&c->d_block, off);
     if (err != cudaSuccess) {
         cudaGetLastError();  // not sticky: leave no error behind for the caller

@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(128, 7) bconv_split_kernel(const __grid_consta
 // seven columns of a target with wide multiply-adds into lo + hi * 2^32,
 // folds hi by [2^32]_t, adds the plan's dst_off (which removes the biases and
 // sub_t) and reduces once: the output is in [0, 3t) for the lazy forward NTT.
-constexpr uint32_t kTcWaitPolls = 1u << 24;  // about a second of 64 ns sleeps
+constexpr uint64_t kTcWaitNs = 1000000000ull;  // give up after a second (ns)
 
 __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
     uint32_t d;
@@ -186,17 +186,45 @@ __device__ __forceinline__ uint32_t byte_pair_f16(uint32_t w, uint32_t sel) {
     return d;
 }
 
+// Persistent, warp-specialised: a CTA owns one group and one target chunk
+// (its B image is loaded once) and walks over tiles of 128 coefficients
+// blockIdx.x, blockIdx.x + gridDim.x, ...  Lane 0 of warp 21 copies the B
+// image once and streams the source words of the coming tiles (1 KiB per
+// source limb) into a ring of kTcXStages shared-memory stages with bulk
+// copies; warps 12-19 turn a staged tile into the A operand (one of two
+// stages; two threads per row, alternate sources); lane 0 of warp 20 issues the
+// MMAs of a tile into one of two tensor-memory accumulators (columns 0 and
+// 256) and commits them to the stage's "A empty" and "D full" mbarriers;
+// warps 0-11 read a finished accumulator (warp w: lanes 32*(w % 4), every
+// third group of four targets), reduce and store, then free it.  Every wait is
+// bounded; a role that gives up raises the CTA's abort flag and the context's
+// status word.
+//
+// Epilogue arithmetic, with b_c = 0x4B000000 + S_c the f32 bits of column c:
+//   lo = sum_{c<5} 2^(8c) S_c  (< 2^55 for 16 sources),  hi = S_5 + 2^8 S_6 (< 2^32),
+//   out = lo + hi * [2^40]_t (an exact 32-bit Shoup product, < 2t) + [-sub]_t,
+// below 8t for the lazy forward NTT when the context's primes are large
+// enough (tc_lazy), else reduced once more to [0, 3t).
+constexpr int kTcEpiWarps = 12, kTcProdWarps = 8, kTcThreads = (kTcEpiWarps + kTcProdWarps + 2) * 32;
+constexpr int kTcXStages = 4;
+
 template <int KG, class GMAP>
-__global__ void __launch_bounds__(256, 2) bconv_tc_kernel(const __grid_constant__ GMAP gm, int chunks, int chunk,
-                                                         const PrimeInfo *__restrict__ pinfo, int logN,
-                                                         int *__restrict__ status) {
+__global__ void __launch_bounds__(kTcThreads, 1)
+    bconv_tc_kernel(const __grid_constant__ GMAP gm, int chunks, int chunk, const PrimeInfo *__restrict__ pinfo,
+                    int logN, int lazy, int *__restrict__ status) {
     extern __shared__ __align__(1024) uint4 tsm[];
-    __shared__ uint64_t mbar;
+    __shared__ uint64_t a_full[2], a_empty[2], d_full[2], d_empty[2], x_full[kTcXStages], x_empty[kTcXStages], b_full;
     __shared__ uint32_t tslot;
-    struct Dst {
-        u64 p, one_s, r32, r32_s, off;
-        uint32_t pos, pad;
+    __shared__ volatile int abort_flag;
+    struct Src {
+        u64 q, add, mul, mul_s;
     };
+    __shared__ Src ssrc[KG];
+    struct Dst {
+        u64 r40, r40_s, off, np, one_s;
+        u64 *out;
+    };
+    constexpr int kMmaWarp = kTcEpiWarps + kTcProdWarps, kLoadWarp = kMmaWarp + 1;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const BConvGroup G = gm.get(blockIdx.y / chunks);
     const BConvPlan *__restrict__ plan = G.plan;
@@ -204,115 +232,225 @@ __global__ void __launch_bounds__(256, 2) bconv_tc_kernel(const __grid_constant_
     const int t0 = (blockIdx.y % chunks) * chunk;
     const int nd = min(plan->n_dst - t0, chunk);
     if (nd <= 0) return;
-    const int ntp = (nd + 1) & ~1;  // N of the MMA = 8 * ntp, a multiple of 16
+    const int ntp = (nd + 3) & ~3;  // N of the MMA = 8 * ntp: whole groups of four targets
     const int n_src = plan->n_src;
-    uint4 *As = tsm;                                        // [16 row groups][KG][8 rows]
-    uint4 *Bs = tsm + 128 * KG;                             // [ntp][KG][8 rows]
+    const int ntiles = int(N >> 7);
+    uint4 *As = tsm;                                               // [2][16 row groups][KG][8 rows]
+    u64 *Xs = reinterpret_cast<u64 *>(tsm + 2 * 128 * KG);         // [kTcXStages][KG - 1][128]
+    uint4 *Bs = tsm + 2 * 128 * KG + kTcXStages * (KG - 1) * 64;   // [ntp][KG][8 rows]
     Dst *sd = reinterpret_cast<Dst *>(Bs + size_t(ntp) * KG * 8);  // [chunk]
 
-    if (warp == 0) tc::tmem_alloc(&tslot, 256);
-    if (tid == 32) tc::mbar_init(&mbar, 1);
-    const uint4 *__restrict__ img = plan->tc_img + size_t(t0) * KG * 8;
-    for (int i = tid; i < ntp * KG * 8; i += blockDim.x) Bs[i] = img[i];
-    for (int t = tid; t < nd; t += blockDim.x) {
+    if (warp == kMmaWarp) tc::tmem_alloc(&tslot, 512);
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s) {
+            tc::mbar_init(&a_full[s], kTcProdWarps * 32);
+            tc::mbar_init(&a_empty[s], 1);
+            tc::mbar_init(&d_full[s], 1);
+            tc::mbar_init(&d_empty[s], kTcEpiWarps);
+        }
+        for (int s = 0; s < kTcXStages; ++s) {
+            tc::mbar_init(&x_full[s], 1);
+            tc::mbar_init(&x_empty[s], kTcProdWarps * 32);
+        }
+        tc::mbar_init(&b_full, 1);
+        abort_flag = 0;
+    }
+    for (int t = tid; t < nd; t += kTcThreads) {
         const int tt = t0 + t;
         const PrimeInfo &P = pinfo[plan->dst_prime[tt]];
-        sd[t] = Dst{P.p, P.one_s, plan->dst_r32[tt], plan->dst_r32_s[tt], plan->dst_off[tt], plan->dst_pos[tt], 0};
+        sd[t] = Dst{plan->dst_r40[tt], plan->dst_r40_s[tt], plan->dst_off[tt], u64(0) - P.p, P.one_s,
+                    G.dst + size_t(plan->dst_pos[tt]) * N};
     }
-    // A: row m is coefficient n0 + m; group g < n_src holds the bytes of the
-    // reduced y_g (see bconv_split_kernel: the representative matters), group
-    // KG-1 the bias entry, the rest zeros
-    const uint32_t n0 = blockIdx.x * 128u;
-    {
-        const int m = tid & 127;
-        uint4 *row = As + (m >> 3) * (KG * 8) + (m & 7);
-        for (int g = tid >> 7; g < KG; g += 2) {
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (g < n_src) {
-                const u64 q = pinfo[plan->src_prime[g]].p, nq = u64(0) - q;
-                const u64 x = G.src[size_t(g) * N + n0 + m];
-                const u64 y =
-                    csub(csub(shoup_approx(x + plan->src_add[g], plan->src_mul[g], plan->src_mul_s[g], nq), 2 * q), q);
-                const uint32_t w0 = uint32_t(y), w1 = uint32_t(y >> 32);
-                v = make_uint4(byte_pair_f16(w0, 0x4140u), byte_pair_f16(w0, 0x4342u), byte_pair_f16(w1, 0x4140u),
-                               byte_pair_f16(w1, 0x4342u));
-            } else if (g == KG - 1) {
-                v.x = 0x6800u;  // f16 2048
-            }
-            row[g * 8] = v;
-        }
-    }
+    if (tid < n_src)
+        ssrc[tid] = Src{pinfo[plan->src_prime[tid]].p, plan->src_add[tid], plan->src_mul[tid], plan->src_mul_s[tid]};
     tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t taddr = tslot;
-    if (tid == 0) {
-        const uint32_t a0 = tc::smem_addr(As), b0 = tc::smem_addr(Bs);
-        const uint32_t idesc = tc::idesc_f16_f32(128, 8 * ntp);
-#pragma unroll
-        for (int s = 0; s < KG / 2; ++s)
-            tc::mma_f16(taddr, tc::desc_kmajor(a0 + 256u * s, 128u, 128u * KG),
-                        tc::desc_kmajor(b0 + 256u * s, 128u, 128u * KG), idesc, s > 0);
-        tc::mma_commit(&mbar);
-    }
-    bool ok = tc::mbar_wait(&mbar, 0, kTcWaitPolls);
-    tc::fence_after_sync();
-    if (ok) {
-        // warp w reads lanes 32*(w % 4) .. +31 (its coefficients) for half the targets
-        const int quarter = warp & 3, half = warp >> 2;
-        const int h0 = (nd + 1) >> 1;
-        const int tb = half ? h0 : 0, te = half ? nd : h0;
-        const uint32_t laddr = taddr + (uint32_t(quarter * 32) << 16);
-        const uint32_t n = n0 + uint32_t(quarter * 32 + lane);
-        for (int t = tb; t < te; t += 2) {
-            uint32_t r[16];
-            tc::tmem_ld16(laddr + uint32_t(t * 8), r);
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                if (t + j >= te) break;
-                const Dst &d = sd[t + j];
-                const uint32_t *b = r + 8 * j;
-                u64 lo = b[0], hi = b[4];
-                mad_wide(lo, b[1], 1u << 8);
-                mad_wide(lo, b[2], 1u << 16);
-                mad_wide(lo, b[3], 1u << 24);
-                mad_wide(hi, b[5], 1u << 8);
-                mad_wide(hi, b[6], 1u << 16);
-                const u64 np = u64(0) - d.p;
-                const u64 v = shoup_one(lo + shoup_approx(hi, d.r32, d.r32_s, np) + d.off, d.one_s, np);
-                G.dst[size_t(d.pos) * N + n] = v;
+    auto give_up = [&]() {
+        abort_flag = 1;
+        atomicOr(status, 1);
+    };
+
+    if (warp == kLoadWarp) {
+        // ---- loader: the B image, then the n_src source slices (1 KiB each) of every tile
+        if (lane == 0) {
+            const uint32_t bbytes = uint32_t(ntp) * KG * 128u;
+            tc::mbar_arrive_expect_tx(&b_full, bbytes);
+            tc::bulk_g2s(Bs, plan->tc_img + size_t(t0) * KG * 8, bbytes, &b_full);
+            int it = 0;
+            for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+                const int xs = it % kTcXStages;
+                if (it >= kTcXStages &&
+                    !tc::mbar_wait(&x_empty[xs], ((it / kTcXStages) - 1) & 1, kTcWaitNs, &abort_flag)) {
+                    give_up();
+                    break;
+                }
+                tc::mbar_arrive_expect_tx(&x_full[xs], uint32_t(n_src) * 1024u);
+                for (int g = 0; g < n_src; ++g)
+                    tc::bulk_g2s(Xs + (size_t(xs) * (KG - 1) + g) * 128, G.src + size_t(g) * N + size_t(tile) * 128,
+                                 1024u, &x_full[xs]);
             }
+            // no copy may still be in flight when the CTA ends (they all have
+            // landed unless another role gave up)
+            for (int j = it - 1; j >= 0 && j >= it - kTcXStages; --j)
+                tc::mbar_wait(&x_full[j % kTcXStages], (j / kTcXStages) & 1, kTcWaitNs);
+            tc::mbar_wait(&b_full, 0, kTcWaitNs);
         }
+        __syncwarp();
+    } else if (warp >= kTcEpiWarps && warp < kMmaWarp) {
+        // ---- producers: thread = row m of the A tile (coefficient n0 + m);
+        // group g < n_src holds the bytes of the reduced y_g (see
+        // bconv_split_kernel: the representative matters), group KG-1 the
+        // bias entry 2048, the rest zeros
+        const int pt = tid - kTcEpiWarps * 32;
+        const int m = pt & 127, par = pt >> 7;  // row m, groups g = 2i + par
+        int it = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+            const int s = it & 1, xs = it % kTcXStages;
+            if ((it >= 2 && !tc::mbar_wait(&a_empty[s], ((it >> 1) & 1) ^ 1, kTcWaitNs, &abort_flag)) ||
+                !tc::mbar_wait(&x_full[xs], (it / kTcXStages) & 1, kTcWaitNs, &abort_flag)) {
+                give_up();
+                break;
+            }
+            u64 x[KG / 2];
+            const u64 *xrow = Xs + size_t(xs) * (KG - 1) * 128 + m;
+#pragma unroll
+            for (int i = 0; i < KG / 2; ++i) {
+                const int g = 2 * i + par;
+                x[i] = g < n_src ? xrow[g * 128] : 0;
+            }
+            tc::mbar_arrive(&x_empty[xs]);
+            uint4 *row = As + s * (128 * KG) + (m >> 3) * (KG * 8) + (m & 7);
+#pragma unroll
+            for (int i = 0; i < KG / 2; ++i) {
+                const int g = 2 * i + par;
+                uint4 v = make_uint4(0, 0, 0, 0);
+                if (g < n_src) {
+                    const Src c = ssrc[g];
+                    const u64 y = csub(csub(shoup_approx(x[i] + c.add, c.mul, c.mul_s, u64(0) - c.q), 2 * c.q), c.q);
+                    const uint32_t w0 = uint32_t(y), w1 = uint32_t(y >> 32);
+                    v = make_uint4(byte_pair_f16(w0, 0x4140u), byte_pair_f16(w0, 0x4342u), byte_pair_f16(w1, 0x4140u),
+                                   byte_pair_f16(w1, 0x4342u));
+                } else if (g == KG - 1) {
+                    v.x = 0x6800u;  // f16 2048
+                }
+                row[g * 8] = v;
+            }
+            tc::fence_async_smem();
+            tc::mbar_arrive(&a_full[s]);
+        }
+    } else if (warp == kMmaWarp) {
+        // ---- one thread issues the MMAs of every tile
+        if (lane == 0) {
+            const uint32_t a0 = tc::smem_addr(As), b0 = tc::smem_addr(Bs);
+            const uint32_t idesc = tc::idesc_f16_f32(128, 8 * ntp);
+            int it = 0;
+            const bool have_b = tc::mbar_wait(&b_full, 0, kTcWaitNs, &abort_flag);
+            if (!have_b) give_up();
+            for (int tile = blockIdx.x; have_b && tile < ntiles; tile += gridDim.x, ++it) {
+                const int s = it & 1;
+                const uint32_t ph = (it >> 1) & 1;
+                if (!tc::mbar_wait(&a_full[s], ph, kTcWaitNs, &abort_flag) ||
+                    (it >= 2 && !tc::mbar_wait(&d_empty[s], ph ^ 1, kTcWaitNs, &abort_flag))) {
+                    give_up();
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t as = a0 + uint32_t(s) * (128u * KG * 16u);
+#pragma unroll
+                for (int k = 0; k < KG / 2; ++k)
+                    tc::mma_f16(taddr + uint32_t(s) * 256u, tc::desc_kmajor(as + 256u * k, 128u, 128u * KG),
+                                tc::desc_kmajor(b0 + 256u * k, 128u, 128u * KG), idesc, k > 0);
+                tc::mma_commit(&a_empty[s]);
+                tc::mma_commit(&d_full[s]);
+            }
+            // whatever happened, no MMA may still run when the memory is freed
+            if (it > 0) tc::mbar_wait(&d_full[(it - 1) & 1], ((it - 1) >> 1) & 1, kTcWaitNs);
+        }
+        __syncwarp();
     } else {
-        if (lane == 0) atomicOr(status, 1);
-        // the multiplies may still be running: wait once more before freeing their memory
-        tc::mbar_wait(&mbar, 0, kTcWaitPolls);
+        // ---- epilogue: warp w reads lanes 32*(w % 4) .. +31, groups of four
+        // targets part, part + 3, ... (part = w / 4)
+        constexpr int kParts = kTcEpiWarps / 4;
+        const int quarter = warp & 3, part = warp >> 2;
+        const int ngroups4 = ntp >> 2;
+        constexpr uint32_t kBias = 0x4B000000u;
+        constexpr u64 kLoBias = u64(kBias) * (1ull + (1ull << 8) + (1ull << 16) + (1ull << 24) + (1ull << 32));
+        int it = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+            const int s = it & 1;
+            if (!tc::mbar_wait(&d_full[s], (it >> 1) & 1, kTcWaitNs, &abort_flag)) {
+                give_up();
+                break;
+            }
+            tc::fence_after_sync();
+            const uint32_t laddr = taddr + uint32_t(s) * 256u + (uint32_t(quarter * 32) << 16);
+            const uint32_t n = uint32_t(tile) * 128u + uint32_t(quarter * 32 + lane);
+            for (int q4 = part; q4 < ngroups4; q4 += kParts) {
+                uint32_t r[32];
+                tc::tmem_ld32(laddr + uint32_t(q4 * 32), r);
+                tc::tmem_wait_ld();
+                tc::tmem_hold(r);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int t = q4 * 4 + j;
+                    if (t >= nd) break;
+                    const Dst &d = sd[t];
+                    const uint32_t *b = r + 8 * j;
+                    u64 lo = b[0];
+                    mad_wide(lo, b[1], 1u << 8);
+                    mad_wide(lo, b[2], 1u << 16);
+                    mad_wide(lo, b[3], 1u << 24);
+                    lo += u64(b[4]) << 32;
+                    lo -= kLoBias;
+                    const uint32_t hi = b[5] + (b[6] << 8) - kBias * 257u;  // exact: the true value is < 2^32
+                    u64 v = lo + shoup_u32(hi, d.r40, d.r40_s, d.np) + d.off;
+                    if (!lazy) v = shoup_one(v, d.one_s, d.np);
+                    d.out[n] = v;
+                }
+            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&d_empty[s]);
+        }
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(taddr, 256);
+    if (warp == kMmaWarp) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(taddr, 512);
+    }
 }
 
 template <int KG, class GMAP>
 static void launch_tc_kg(const ckks_ctx *ctx, const GMAP &gm, int ngroups, int chunks, int chunk, cudaStream_t st) {
-    const int ntp = (chunk + 1) & ~1;
-    // at least 80 KiB: no more than two CTAs share an SM, as many as fit their
-    // 256 tensor-memory columns (a third would wait inside tcgen05.alloc)
-    const size_t need = (size_t(128) * KG + size_t(ntp) * KG * 8) * sizeof(uint4) + size_t(chunk) * 48;
-    const size_t smem = std::max<size_t>(need, 80 * 1024);
+    // 512 tensor-memory columns: one CTA of this kernel per SM (the shared
+    // memory is sized so that a second cannot be placed beside it and wait in
+    // tcgen05.alloc; CTAs of other kernels still fit); as many CTAs per
+    // (group, chunk) as share the SMs, each walking over tiles
+    const size_t need = (size_t(2 * 128) * KG + size_t(kTcXStages) * (KG - 1) * 64 + size_t(chunk) * KG * 8) *
+                            sizeof(uint4) +
+                        size_t(chunk) * 48;
+    const size_t smem = std::max<size_t>(need, 116 * 1024);
     auto kern = bconv_tc_kernel<KG, GMAP>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    dim3 grid(unsigned(ctx->N / 128), unsigned(ngroups * chunks));
-    kern<<<grid, 256, smem, st>>>(gm, chunks, chunk, ctx->d_pinfo, ctx->logN, ctx->d_status);
+    const int tiles = ctx->N / 128;
+    const int rows = ngroups * chunks;
+    const int per = std::max(1, std::min(tiles, ctx->sms / rows));
+    const dim3 grid(static_cast<unsigned>(per), static_cast<unsigned>(rows));
+    kern<<<grid, kTcThreads, smem, st>>>(gm, chunks, chunk, ctx->d_pinfo, ctx->logN, ctx->tc_lazy ? 1 : 0,
+                                         ctx->d_status);
 }
 
 // Tensor-core conversion over `ngroups` groups of up to n_all targets each,
-// in chunks of at most 32 targets (256 tensor-memory columns).
+// in chunks of at most 32 targets (256 tensor-memory columns), each a
+// multiple of four targets.
 template <class GMAP>
 static cudaError_t launch_tc(const ckks_ctx *ctx, const GMAP &gm, int ngroups, int n_all, cudaStream_t st) {
     const int chunks = (n_all + 31) / 32;
-    const int chunk = (n_all + chunks - 1) / chunks;
+    const int chunk = ((n_all + chunks - 1) / chunks + 3) & ~3;
     ProfScope ps(ctx, K_BCONV, double(ngroups) * n_all, st);
     switch (ctx->tc_kg) {
     case 4: launch_tc_kg<4>(ctx, gm, ngroups, chunks, chunk, st); break;

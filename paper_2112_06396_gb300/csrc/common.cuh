@@ -125,6 +125,36 @@ __device__ __forceinline__ u64 shoup_one(u64 x, u64 ones, u64 np) {
     return r;
 }
 
+// Shoup product of a 32-bit x by the constant w (companion ws = floor(w 2^64 / p)):
+// with T = x*s0 and U = x*s1 + hi(T) (no overflow), floor(x*ws / 2^64) is
+// exactly hi(U), so x*w - q*p is in [0, 2p).  Six 32-bit multiply-adds.
+__device__ __forceinline__ u64 shoup_u32(uint32_t x, u64 w, u64 ws, u64 np) {
+    u64 r;
+    asm("{\n\t"
+        ".reg .u32 w0, w1, s0, s1, n0, n1, t0, t1, u0, q, m, r0, r1;\n\t"
+        ".reg .u64 t, u, acc;\n\t"
+        "mov.b64 {w0, w1}, %2;\n\t"
+        "mov.b64 {s0, s1}, %3;\n\t"
+        "mov.b64 {n0, n1}, %4;\n\t"
+        "mul.wide.u32 t, %1, s0;\n\t"
+        "mov.b64 {t0, t1}, t;\n\t"
+        "cvt.u64.u32 u, t1;\n\t"
+        "mad.wide.u32 u, %1, s1, u;\n\t"
+        "mov.b64 {u0, q}, u;\n\t"
+        // x*w + q*(2^64 - p), low word
+        "mul.wide.u32 acc, %1, w0;\n\t"
+        "mad.wide.u32 acc, q, n0, acc;\n\t"
+        "mul.lo.u32 m, %1, w1;\n\t"
+        "mad.lo.u32 m, q, n1, m;\n\t"
+        "mov.b64 {r0, r1}, acc;\n\t"
+        "add.u32 r1, r1, m;\n\t"
+        "mov.b64 %0, {r0, r1};\n\t"
+        "}"
+        : "=l"(r)
+        : "r"(x), "l"(w), "l"(ws), "l"(np));
+    return r;
+}
+
 __device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 p) { return csub(a + b, p); }
 __device__ __forceinline__ u64 sub_mod(u64 a, u64 b, u64 p) { return a >= b ? a - b : a + p - b; }
 
@@ -228,14 +258,14 @@ struct BConvPlan {
     uint4 matw[kMaxDst][kMaxSrc];
     u64 dst_rw[kMaxDst], dst_rw_s[kMaxDst];  // [2^W]_t, Shoup companion
     // Tensor-core form (primes below 2^56, at most 16 sources): tc_img holds,
-    // per target t (n_dst rounded up to even), KG groups of an 8 x 8 f16 core
-    // matrix, row c and column j of group i < n_src being byte c of
+    // per target t (n_dst rounded up to a multiple of 4), KG groups of an 8 x 8
+    // f16 core matrix, row c and column j of group i < n_src being byte c of
     // [2^(8j) * mat[t][i]]_t, group KG-1 holding 4096 in column 0 of every row
     // (with the 2048 in the A operand: the bias 2^23 of every sum).  The
-    // epilogue adds dst_off = [-bias - sub_t]_t and folds the high word with
-    // dst_r32 = [2^32]_t.
+    // epilogue folds the sums of rows 5 and 6 with dst_r40 = [2^40]_t and adds
+    // dst_off = [-sub_t]_t.
     const uint4 *tc_img;
-    u64 dst_r32[kMaxDst], dst_r32_s[kMaxDst], dst_off[kMaxDst];
+    u64 dst_r40[kMaxDst], dst_r40_s[kMaxDst], dst_off[kMaxDst];
 };
 
 struct BConvGroup {

@@ -11,11 +11,13 @@
 
 struct ckks_ctx {
     int device;
+    int sms;                          // streaming multiprocessors of the device
     int logN, N, L, k, dnum, alpha;
     bool small_primes;                // every prime < 2^57: lazy NTT without conditional subtractions
     int split_bits;                   // W of the split basis conversion, 0 if primes are too large for it
     int tc_kg;                        // K groups of the tensor-core basis conversion, 0 if not available
-    bool tc_on = true;                // use it when available (ckks_tune_set can switch it off)
+    bool tc_on = true;                // use it when available (ckks_bconv_select can switch it off)
+    bool tc_lazy;                     // its outputs stay below 8t without a final reduction
     std::vector<u64> primes;          // L + k: q_0..q_{L-1}, p_0..p_{k-1}
     // device tables (one allocation)
     void *d_block;

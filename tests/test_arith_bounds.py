@@ -113,10 +113,33 @@ def test_tc_operand_encodings_are_exact():
     assert 2048.0 * 4096.0 == 2.0 ** 23
 
 
-def _tc_convert(ys, Cs, t, sub):
+def shoup_u32(x, w, p):
+    """shoup_u32 (common.cuh): x < 2^32, exact quotient hi(x*s1 + hi(x*s0)), result in [0, 2p)."""
+    ws = (w << 64) // p
+    s0, s1 = ws & M32, ws >> 32
+    T = x * s0
+    U = x * s1 + (T >> 32)
+    assert U <= M64
+    q = U >> 32
+    assert q == (x * ws) >> 64
+    n = (1 << 64) - p
+    acc = (x * (w & M32) + q * (n & M32)) & M64
+    m = (x * (w >> 32) + q * (n >> 32)) & M32
+    r = (acc + (m << 32)) & M64
+    assert r == x * w - q * p and r < 2 * p
+    return r
+
+
+def _tc_lazy(nsrc, tmin):
+    """The host's tc_lazy: the epilogue's low word stays below 5t for the smallest prime."""
+    lo_max = nsrc * 7 * 255 * 255 * (1 + (1 << 8) + (1 << 16) + (1 << 24) + (1 << 32))
+    return lo_max < 5 * tmin
+
+
+def _tc_convert(ys, Cs, t, sub, lazy):
     """bconv_tc_kernel for one coefficient and one target t: byte products summed
     as the tensor core does (integers, every partial sum exact in f32), the f32
-    bits read as integers, the epilogue's lo/hi combination, fold and reduction."""
+    bits read as integers, the epilogue's 64- and 32-bit arithmetic."""
     import struct
 
     S = [0] * 8
@@ -126,27 +149,30 @@ def _tc_convert(ys, Cs, t, sub):
             yj = (y >> (8 * j)) & 0xFF
             for c in range(7):
                 S[c] += yj * ((mj >> (8 * c)) & 0xFF)
-    bits = []
+    b = []
     for c in range(7):
         f = 2.0 ** 23 + S[c]
         assert f < 2.0 ** 24  # every partial sum is an exact f32 integer
-        b = struct.unpack("<I", struct.pack("<f", f))[0]
-        assert b == 0x4B000000 + S[c]
-        bits.append(b)
-    lo = bits[0] + (bits[1] << 8) + (bits[2] << 16) + (bits[3] << 24)
-    hi = bits[4] + (bits[5] << 8) + (bits[6] << 16)
-    assert lo < 1 << 56 and hi < 1 << 48
-    bias = 0x4B000000 * (1 + (1 << 8) + (1 << 16) + (1 << 24)) + ((0x4B000000 * (1 + (1 << 8) + (1 << 16))) << 32)
-    off = (t - (bias + sub) % t) % t
-    r32 = (1 << 32) % t
-    _, _, fold = shoup_approx(hi, r32, t)
-    v = lo + fold + off
-    assert v < 1 << 64
-    _, out = shoup_one(v, t)
-    return out
+        bits = struct.unpack("<I", struct.pack("<f", f))[0]
+        assert bits == 0x4B000000 + S[c]
+        b.append(bits)
+    lo_bias = 0x4B000000 * (1 + (1 << 8) + (1 << 16) + (1 << 24) + (1 << 32))
+    lo = b[0] + (b[1] << 8) + (b[2] << 16) + (b[3] << 24) + (b[4] << 32)
+    assert lo <= M64
+    lo -= lo_bias
+    hi = (b[5] + (b[6] << 8) - 0x4B000000 * 257) & M32
+    assert hi == S[5] + (S[6] << 8)
+    assert lo + (hi << 40) == sum(S[c] << (8 * c) for c in range(7))
+    v = lo + shoup_u32(hi, (1 << 40) % t, t) + (t - sub % t) % t
+    assert v <= M64
+    if lazy:
+        assert v < 8 * t  # the lazy forward NTT's input bound
+    else:
+        _, v = shoup_one(v, t)
+    return v
 
 
-@pytest.mark.parametrize("bits,nsrc", [(54, 9), (54, 16), (55, 16), (50, 4)])
+@pytest.mark.parametrize("bits,nsrc", [(54, 9), (54, 16), (55, 16), (50, 4), (50, 16)])
 def test_tc_conversion_arithmetic(bits, nsrc):
     rng = random.Random(bits * 100 + nsrc)
     for trial in range(60):
@@ -157,11 +183,20 @@ def test_tc_conversion_arithmetic(bits, nsrc):
             ys = [q - 1 for q in qs]
         else:
             ys = [rng.randrange(q) for q in qs]
+        if trial % 5 == 1:  # the smallest prime the lazy bound allows
+            t = (1 << (bits - 1)) + 1
         Cs = [rng.randrange(t) for _ in range(nsrc)]
         sub = rng.randrange(t)
-        out = _tc_convert(ys, Cs, t, sub)
-        assert out < 3 * t
+        lazy = _tc_lazy(nsrc, 1 << (bits - 1))
+        out = _tc_convert(ys, Cs, t, sub, lazy)
+        assert out < (8 if lazy else 3) * t
         assert out % t == (sum(y * C for y, C in zip(ys, Cs)) - sub) % t
+
+
+def test_tc_lazy_holds_at_the_key_switching_shapes():
+    # 54-bit primes with max(alpha, k + 1) = 9 sources: no final reduction
+    assert _tc_lazy(9, 1 << 53)
+    assert not _tc_lazy(16, 1 << 49)
 
 
 def test_tc_byte_sums_stay_below_two_to_23_at_sixteen_sources():
