@@ -28,9 +28,10 @@ namespace ckks {
 //  * forward (Cooley-Tukey): X' = X + T, Y' = X + 4p - T with T = W*Y in
 //    [0, 3p), no conditional subtraction: a value below M*p before a stage is
 //    below (M+4)*p after it.  Inputs may be lazy up to 8p (the basis
-//    conversions leave their outputs below 4p, the ModDown offset adds at
-//    most 4p more), so after all logN <= 17 stages every value is below
-//    (8 + 68)p < 2^64 and one reduction at the very end suffices;
+//    conversions leave their outputs below 4p on the integer units and
+//    below 8p on the tensor cores), so after all logN <= 17 stages every
+//    value is below (8 + 68)p < 2^64 and one reduction at the very end
+//    suffices (the ModDown/Rescale epilogue folds it into its product);
 //  * inverse (Gentleman-Sande): X' = (X + Y) mod' 4p, Y' = W*(X - Y + 4p),
 //    keeping every value in [0, 4p).
 // Otherwise (primes up to 2^60) Harvey's exact-quotient butterflies keep
@@ -178,11 +179,14 @@ ntt_pass_kernel(const __grid_constant__ MAP map, const PrimeInfo *__restrict__ p
             __syncthreads();
 #pragma unroll
             for (int k = 0; k < E; k++) x[k] = sm[sidx(g + (k << B))];
-            const u64 one_s = pinfo[prime].one_s;
+            // the ModDown/Rescale tail takes the lazy values (below 76p) as they are
+            if (!(EPI && SMALLP)) {
+                const u64 one_s = pinfo[prime].one_s;
 #pragma unroll
-            for (int k = 0; k < E; k++) {
-                u64 v = SMALLP ? shoup_one(x[k], one_s, np) : x[k];
-                x[k] = csub(csub(v, 2 * p), p);
+                for (int k = 0; k < E; k++) {
+                    u64 v = SMALLP ? shoup_one(x[k], one_s, np) : x[k];
+                    x[k] = csub(csub(v, 2 * p), p);
+                }
             }
             if (!EPI) {
 #pragma unroll
@@ -212,9 +216,19 @@ ntt_pass_kernel(const __grid_constant__ MAP map, const PrimeInfo *__restrict__ p
 #pragma unroll
                     for (int k = 0; k < GRP; k++) {
                         const uint32_t i = uint32_t(gidx(g + ((k0 + k) << B)));
-                        u64 r = shoup_mul(sub_mod(xv[k], x[k0 + k], p), c.x, c.y, p);
-                        r = add_mod(r, av[k], p);
-                        r = add_mod(r, ov[k], p);
+                        u64 r;
+                        if (SMALLP) {
+                            // x lazy below 76p (at most 17 stages from inputs below
+                            // 8p), xv < p: xv + 80p - x is below 81p < 2^64 and
+                            // congruent to xv - x; the product is in [0, 3p), the
+                            // two reduced addends bring it below 5p
+                            r = shoup_approx(xv[k] + 80 * p - x[k0 + k], c.x, c.y, np) + av[k] + ov[k];
+                            r = csub(csub(csub(r, 4 * p), 2 * p), p);
+                        } else {
+                            r = shoup_mul(sub_mod(xv[k], x[k0 + k], p), c.x, c.y, p);
+                            r = add_mod(r, av[k], p);
+                            r = add_mod(r, ov[k], p);
+                        }
                         op[i] = r;
                     }
                 }

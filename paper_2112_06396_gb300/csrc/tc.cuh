@@ -83,18 +83,18 @@ __device__ __forceinline__ bool mbar_test(uint64_t *mbar, uint32_t parity) {
         : "memory");
     return done != 0;
 }
-// Potentially blocking test: the thread is suspended until the phase
-// completes or a hardware time limit passes, without issuing instructions.
-__device__ __forceinline__ bool mbar_try(uint64_t *mbar, uint32_t parity) {
+// Potentially blocking test: the thread is suspended, without issuing
+// instructions, until the phase completes or about suspend_ns pass.
+__device__ __forceinline__ bool mbar_try(uint64_t *mbar, uint32_t parity, uint32_t suspend_ns = 1000000u) {
     uint32_t done;
     asm volatile(
         "{\n\t"
         ".reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t"
         "}"
         : "=r"(done)
-        : "r"(smem_addr(mbar)), "r"(parity)
+        : "r"(smem_addr(mbar)), "r"(parity), "r"(suspend_ns)
         : "memory");
     return done != 0;
 }
