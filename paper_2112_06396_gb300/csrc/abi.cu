@@ -522,8 +522,11 @@ struct LimbList {
         prime.push_back(uint16_t(p));
     }
 };
-static int run_ntt(ckks_ctx *ctx, const LimbList &ll, bool inverse, cudaStream_t st) {
+// lazy: forward transforms stored without their final reduction (EPI_LAZY).
+static int run_ntt(ckks_ctx *ctx, const LimbList &ll, bool inverse, cudaStream_t st, bool lazy = false) {
     const size_t n = ll.src.size();
+    Epi lz{};
+    lz.mode = EPI_LAZY;
     for (size_t b0 = 0; b0 < n; b0 += kMaxBatch) {
         NttBatch b;
         b.count = int(std::min(n - b0, size_t(kMaxBatch)));
@@ -532,7 +535,7 @@ static int run_ntt(ckks_ctx *ctx, const LimbList &ll, bool inverse, cudaStream_t
             b.dst[l] = ll.dst[b0 + l];
             b.prime[l] = ll.prime[b0 + l];
         }
-        CK(inverse ? launch_ntt_inv(ctx, b, st) : launch_ntt_fwd(ctx, b, nullptr, st));
+        CK(inverse ? launch_ntt_inv(ctx, b, st) : launch_ntt_fwd(ctx, b, lazy ? &lz : nullptr, st));
     }
     return CKKS_OK;
 }
@@ -544,6 +547,8 @@ static size_t words_moddown2(const ckks_ctx *c, int ell) { return size_t(2) * c-
 
 // ModUp of every digit of a (Algorithm 6 per digit): iNTT -> BConv -> NTT.
 // ext: [beta][ell+k][N] (digit limbs are not written); acoeff: [ell][N] scratch.
+// The new limbs are left lazy (below 2^64, see EPI_LAZY): every caller feeds
+// them only to inner products with exact 128-bit sums.
 static int modup_all(ckks_ctx *ctx, const u64 *a, int ell, u64 *ext, u64 *acoeff, cudaStream_t st) {
     const size_t N = ctx->N;
     const int k = ctx->k, beta = beta_of(ctx, ell), ext_n = ell + k;
@@ -575,7 +580,7 @@ static int modup_all(ckks_ctx *ctx, const u64 *a, int ell, u64 *ext, u64 *acoeff
             u64 *p = ext + (size_t(j) * ext_n + t) * N;
             fw.add(p, p, ext_prime(ctx, ell, t));
         }
-    return run_ntt(ctx, fw, false, st);
+    return run_ntt(ctx, fw, false, st, true);
 }
 
 // ModDown of npolys extended polynomials in[p] ([ell+k][N]) to out[p] ([ell][N]):

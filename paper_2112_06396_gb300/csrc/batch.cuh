@@ -26,6 +26,7 @@ struct LimbIO {
     const ulonglong2 *cmul;  // scale table (indexed by prime) of the epilogue
     uint32_t galois;
     int accumulate;
+    int lazy;  // store the forward transform without its final reduction (EPI_LAZY)
 };
 
 // Explicit limb list (single operations).
@@ -44,6 +45,7 @@ struct MapList {
         io.cmul = e.cmul;
         io.galois = 1;
         io.accumulate = 0;
+        io.lazy = e.mode == EPI_LAZY;
         if (e.mode == EPI_SCALE) {
             const int poly = l % e.npolys;
             const size_t base = size_t(l / e.npolys) * N;
@@ -161,6 +163,7 @@ struct MapBatch {
         io.cmul = cm;
         io.galois = 1;
         io.accumulate = 0;
+        io.lazy = phase == PH_NTT_UP;  // the ModUp digits go to the inner product only
         if (phase == PH_INTT_A) {
             io.src = ct.a + size_t(i) * N;
             io.dst = lo.acoeff + size_t(i) * N;

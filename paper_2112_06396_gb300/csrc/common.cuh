@@ -223,12 +223,15 @@ struct NttBatch {
 };
 
 // Epilogue of the last forward pass.  EPI_STORE writes the transform.
+// EPI_LAZY writes it without the final reduction (small primes: values below
+// 76p < 2^64), for consumers that only multiply-accumulate it exactly in 128
+// bits and reduce once (the inner products after ModUp).
 // EPI_SCALE treats batch limb l as limb (l / npolys) of polynomial (l % npolys)
 // (the polynomials' limbs of one prime are adjacent in the batch):
 //   out = (x - ntt) * c  [+ add[perm_g(n)]]  [+ out if accumulate]
 // with c = cmul[prime] (value, Shoup companion).  This is the last step of
 // ModDown (c = P^-1) and Rescale (c = q_{ell-1}^-1).
-enum { EPI_STORE = 0, EPI_SCALE = 1 };
+enum { EPI_STORE = 0, EPI_SCALE = 1, EPI_LAZY = 2 };
 struct Epi {
     int mode;
     int npolys;

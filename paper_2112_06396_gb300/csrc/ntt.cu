@@ -179,8 +179,9 @@ ntt_pass_kernel(const __grid_constant__ MAP map, const PrimeInfo *__restrict__ p
             __syncthreads();
 #pragma unroll
             for (int k = 0; k < E; k++) x[k] = sm[sidx(g + (k << B))];
-            // the ModDown/Rescale tail takes the lazy values (below 76p) as they are
-            if (!(EPI && SMALLP)) {
+            // the ModDown/Rescale tail, and a lazy store, take the lazy values
+            // (below 76p) as they are
+            if (!(SMALLP && (EPI || io.lazy))) {
                 const u64 one_s = pinfo[prime].one_s;
 #pragma unroll
                 for (int k = 0; k < E; k++) {
@@ -431,7 +432,7 @@ cudaError_t launch_ntt_fwd(const ckks_ctx *ctx, const NttBatch &b, const Epi *ep
     if (scale) m.e = *epi;
     else {
         m.e = Epi{};
-        m.e.mode = EPI_STORE;
+        m.e.mode = epi != nullptr && epi->mode == EPI_LAZY ? EPI_LAZY : EPI_STORE;
     }
     return run_fwd(m, b.count, scale, ctx, st);
 }
