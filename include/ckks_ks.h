@@ -415,6 +415,14 @@ int ckks_server_stats(const ckks_server *srv, ckks_server_stats_t *stats);
  * work are not valid. */
 int ckks_poll_status(ckks_ctx *ctx, ckks_stream_t stream, int *done);
 
+/* Self-test of that bounded wait (no counterpart in the paper): launches one
+ * CTA that waits on an mbarrier no thread arrives on.  The wait gives up after
+ * limit_us microseconds (1 .. 2000000, else CKKS_EINVAL) and records the
+ * timeout like the conversion does, so that the next ckks_poll_status on the
+ * stream, once it has finished, returns CKKS_ETIMEOUT.  Nothing else in the
+ * context is touched; later calls run normally. */
+int ckks_selftest_bounded_wait(ckks_ctx *ctx, uint32_t limit_us, ckks_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * Measurement hook (no counterpart in the paper).  While enabled, every
  * kernel the context launches is bracketed by a pair of CUDA events recorded

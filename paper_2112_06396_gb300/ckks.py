@@ -30,7 +30,11 @@ CKKS_OK, CKKS_EINVAL, CKKS_ENOMEM, CKKS_ECUDA, CKKS_EUNSUPPORTED, CKKS_ETIMEOUT 
 
 
 class CkksError(RuntimeError):
-    pass
+    """A status other than CKKS_OK; .code holds it."""
+
+    def __init__(self, msg, code=None):
+        super().__init__(msg)
+        self.code = code
 
 
 class _Params(ctypes.Structure):
@@ -104,6 +108,7 @@ _SIGS = {
     "ckks_autotune": (_i, [_vp, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_float)]),
     "ckks_tune_set": (_i, [_vp, ctypes.POINTER(_i)]),
     "ckks_bconv_select": (_i, [_vp, _i, ctypes.POINTER(_i)]),
+    "ckks_selftest_bounded_wait": (_i, [_vp, ctypes.c_uint32, _vp]),
     "ckks_server_add_key_seeded": (_i, [_vp, _i, _vp, ctypes.c_uint64, ctypes.POINTER(_i)]),
     "ckks_keygen_ksk_seeded": (_i, [_vp, _vp, _vp, ctypes.c_uint64, ctypes.c_uint32, _vp, _vp, _vp]),
     "ckks_ksk_expand": (_i, [_vp, _vp, ctypes.c_uint64, _vp, _vp]),
@@ -158,7 +163,7 @@ def _check(rc, ctx=None):
         msg = lib().ckks_strerror(rc).decode()
         if ctx is not None and rc == CKKS_ECUDA:
             msg += f" (cudaError {lib().ckks_last_cuda_error(ctx)})"
-        raise CkksError(msg)
+        raise CkksError(msg, rc)
 
 
 def _p(t):
@@ -277,6 +282,11 @@ class Context:
     def tune_set(self, choice):
         ch = (_i * 4)(*[int(x) for x in choice])
         _check(lib().ckks_tune_set(self._h, ch))
+
+    def selftest_bounded_wait(self, limit_us, stream=None):
+        """Launch the bounded-wait self-test (ckks_selftest_bounded_wait): a wait
+        on a barrier nothing arrives on, which gives up after limit_us."""
+        _check(lib().ckks_selftest_bounded_wait(self._h, int(limit_us), _stream(stream)), self._h)
 
     def bconv_tensor_cores(self, on=True):
         """Run the basis conversions on the tensor cores (on) or the integer

@@ -1545,6 +1545,12 @@ extern "C" int ckks_tune_set(ckks_ctx *ctx, const int *choice) {
     return CKKS_OK;
 }
 
+extern "C" int ckks_selftest_bounded_wait(ckks_ctx *ctx, uint32_t limit_us, ckks_stream_t stream) {
+    if (ctx == nullptr || limit_us == 0 || limit_us > 2000000u) return CKKS_EINVAL;
+    CK(launch_bounded_wait_selftest(ctx, uint64_t(limit_us) * 1000u, (cudaStream_t)stream));
+    return CKKS_OK;
+}
+
 extern "C" int ckks_bconv_select(ckks_ctx *ctx, int tensor_cores, int *available) {
     if (ctx == nullptr) return CKKS_EINVAL;
     if (available) *available = ctx->tc_kg != 0;

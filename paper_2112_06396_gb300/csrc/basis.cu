@@ -501,6 +501,21 @@ static cudaError_t launch_split(const ckks_ctx *ctx, const GMAP &gm, int ngroups
     return cudaGetLastError();
 }
 
+// Self-test of the bounded wait: one CTA waits on an mbarrier that expects an
+// arrival no thread makes; the wait gives up after limit_ns and the kernel
+// records the timeout in the status word exactly as bconv_tc_kernel does.
+__global__ void bounded_wait_selftest_kernel(uint64_t limit_ns, int *__restrict__ status) {
+    __shared__ uint64_t never;
+    if (threadIdx.x == 0) tc::mbar_init(&never, 1);
+    __syncthreads();
+    if (!tc::mbar_wait(&never, 0, limit_ns) && threadIdx.x == 0) atomicOr(status, 1);
+}
+
+cudaError_t launch_bounded_wait_selftest(const ckks_ctx *ctx, uint64_t limit_ns, cudaStream_t st) {
+    bounded_wait_selftest_kernel<<<1, 32, 0, st>>>(limit_ns, ctx->d_status);
+    return cudaGetLastError();
+}
+
 // The basis conversions of one batched phase: ModUp digits (GM_MODUP), the
 // ModDown of both polynomials (GM_MODDOWN) or the Rescale of both polynomials
 // of the Mult entries (GM_RESCALE).  Needs the split conversion.

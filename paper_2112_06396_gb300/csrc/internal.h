@@ -97,6 +97,7 @@ inline int ext_prime(const ckks_ctx *c, int ell, int pos) { return pos < ell ? p
 inline int beta_of(const ckks_ctx *c, int ell) { return (ell + c->alpha - 1) / c->alpha; }
 
 cudaError_t ntt_set_attributes(const ckks_ctx *ctx);
+cudaError_t launch_bounded_wait_selftest(const ckks_ctx *ctx, uint64_t limit_ns, cudaStream_t st);
 cudaError_t launch_ntt_fwd(const ckks_ctx *ctx, const NttBatch &b, const Epi *epi, cudaStream_t st);
 cudaError_t launch_ntt_inv(const ckks_ctx *ctx, const NttBatch &b, cudaStream_t st);
 cudaError_t launch_ntt_batch(const ckks_ctx *ctx, const KsBatchDesc &d, int phase, cudaStream_t st);

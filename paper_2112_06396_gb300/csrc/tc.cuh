@@ -111,11 +111,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, uint6
                                           const volatile int *abort = nullptr) {
     if (mbar_try(mbar, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
-    for (;;) {
+    // the iteration cap bounds the loop even if the timer did not advance
+    for (uint32_t i = 0; i < (1u << 26); ++i) {
         if (mbar_try(mbar, parity)) return true;
         if (abort != nullptr && *abort) return false;
         if (globaltimer_ns() - t0 > limit_ns) return false;
     }
+    return false;
 }
 
 // One arrival that also announces `bytes` of bulk copies to complete on the barrier.

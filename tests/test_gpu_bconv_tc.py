@@ -123,3 +123,38 @@ def test_headline_shape(cfgB):
     np.testing.assert_array_equal(tc[0], ra)
     np.testing.assert_array_equal(tc[1], rb)
     assert ctx.poll_status()
+
+
+@pytest.fixture(scope="module")
+def cfg1(oracle_lib):
+    return Setup(oracle_lib, 12, 6, 3, 2, 50)
+
+
+def test_bounded_wait_runs_out_and_is_reported(cfg1):
+    """The device-side wait of the tensor-core conversion is bounded: the
+    self-test waits on a barrier nothing arrives on, gives up after 20 ms and
+    records it; ckks_poll_status reports CKKS_ETIMEOUT once, and the context
+    keeps working (a KeySwitch afterwards still equals the oracle)."""
+    import time
+
+    ckks = _gpu()
+    S = cfg1
+    P, ctx = S.P, S.ctx
+    assert ctx.poll_status()
+    t0 = time.perf_counter()
+    ctx.selftest_bounded_wait(20000)
+    torch.cuda.synchronize()
+    waited = time.perf_counter() - t0
+    assert 0.015 < waited < 5.0
+    with pytest.raises(ckks.CkksError) as err:
+        ctx.poll_status()
+    assert err.value.code == ckks.CKKS_ETIMEOUT
+    assert ctx.poll_status()  # reported once, then cleared
+    with pytest.raises(ckks.CkksError):
+        ctx.selftest_bounded_wait(0)
+    key = S.key(0, "gpu/tc/after-timeout")[0]
+    a, _ = S.ct(P.L, "gpu/tc/after-timeout/ct")
+    u, v = ctx.keyswitch(dev(a), P.L, dev(key))
+    ru, rv = S.o.keyswitch(P, P.L, a, key)
+    np.testing.assert_array_equal(host(u), ru)
+    np.testing.assert_array_equal(host(v), rv)
