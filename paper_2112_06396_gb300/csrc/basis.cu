@@ -225,6 +225,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         u64 *out;
     };
     constexpr int kMmaWarp = kTcEpiWarps + kTcProdWarps, kLoadWarp = kMmaWarp + 1;
+    // f32 bits of 2^23 + S (the MMA's bias), and the bias of the low word lo
+    constexpr uint32_t kBias = 0x4B000000u;
+    constexpr u64 kLoBias = u64(kBias) * (1ull + (1ull << 8) + (1ull << 16) + (1ull << 24) + (1ull << 32));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const BConvGroup G = gm.get(blockIdx.y / chunks);
     const BConvPlan *__restrict__ plan = G.plan;
@@ -258,7 +261,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     for (int t = tid; t < nd; t += kTcThreads) {
         const int tt = t0 + t;
         const PrimeInfo &P = pinfo[plan->dst_prime[tt]];
-        sd[t] = Dst{plan->dst_r40[tt], plan->dst_r40_s[tt], plan->dst_off[tt], u64(0) - P.p, P.one_s,
+        sd[t] = Dst{plan->dst_r40[tt], plan->dst_r40_s[tt], plan->dst_off[tt] - kLoBias, u64(0) - P.p, P.one_s,
                     G.dst + size_t(plan->dst_pos[tt]) * N};
     }
     if (tid < n_src)
@@ -376,8 +379,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         constexpr int kParts = kTcEpiWarps / 4;
         const int quarter = warp & 3, part = warp >> 2;
         const int ngroups4 = ntp >> 2;
-        constexpr uint32_t kBias = 0x4B000000u;
-        constexpr u64 kLoBias = u64(kBias) * (1ull + (1ull << 8) + (1ull << 16) + (1ull << 24) + (1ull << 32));
         int it = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
             const int s = it & 1;
@@ -404,8 +405,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     mad_wide(lo, b[2], 1u << 16);
                     mad_wide(lo, b[3], 1u << 24);
                     lo += u64(b[4]) << 32;
-                    lo -= kLoBias;
                     const uint32_t hi = b[5] + (b[6] << 8) - kBias * 257u;  // exact: the true value is < 2^32
+                    // d.off = [-sub]_t - kLoBias (mod 2^64) removes the biases of lo
+                    // in the same add: the true sum is >= 0 and < 2^64
                     u64 v = lo + shoup_u32(hi, d.r40, d.r40_s, d.np) + d.off;
                     if (!lazy) v = shoup_one(v, d.one_s, d.np);
                     d.out[n] = v;

@@ -159,11 +159,14 @@ def _tc_convert(ys, Cs, t, sub, lazy):
     lo_bias = 0x4B000000 * (1 + (1 << 8) + (1 << 16) + (1 << 24) + (1 << 32))
     lo = b[0] + (b[1] << 8) + (b[2] << 16) + (b[3] << 24) + (b[4] << 32)
     assert lo <= M64
-    lo -= lo_bias
     hi = (b[5] + (b[6] << 8) - 0x4B000000 * 257) & M32
     assert hi == S[5] + (S[6] << 8)
-    assert lo + (hi << 40) == sum(S[c] << (8 * c) for c in range(7))
-    v = lo + shoup_u32(hi, (1 << 40) % t, t) + (t - sub % t) % t
+    assert lo - lo_bias + (hi << 40) == sum(S[c] << (8 * c) for c in range(7))
+    # the staged offset [-sub]_t - lo_bias, added modulo 2^64 as the kernel does
+    off = ((t - sub % t) % t - lo_bias) & M64
+    fold = shoup_u32(hi, (1 << 40) % t, t)
+    v = (lo + fold + off) & M64
+    assert v == lo - lo_bias + fold + (t - sub % t) % t  # no wrap in the true sum
     assert v <= M64
     if lazy:
         assert v < 8 * t  # the lazy forward NTT's input bound
