@@ -555,8 +555,8 @@ def job_throughput(world, per_rank_units_per_step, steps, ms):
 
 
 # ------------------------------------------------------------------ oracle (CPU) legs
-def oracle_keyswitch_seconds(reps=1):
-    """Time the oracle's HRotate (r=1) at the bench configuration, one thread."""
+def _oracle_inputs():
+    """The oracle's HRotate (r=1) inputs at the bench configuration."""
     import oracle
 
     N = 1 << LOGN
@@ -569,12 +569,72 @@ def oracle_keyswitch_seconds(reps=1):
     key = oracle.keygen(P, a_key, s, oracle.rot_secret(P, s, g), e_key)
     a = synth.uniform_residues(primes[:L], N, "bench/r0/ct0/a")
     b = synth.uniform_residues(primes[:L], N, "bench/r0/ct0/b")
-    times = []
-    for _ in range(reps):
+    return P, a, b, g, key
+
+
+def _oracle_worker(job):
+    """One process of the all-cores oracle timing: build the inputs, then for
+    every round wait for the other processes and run one HRotate; returns the
+    (start, end) of each round on the host's monotonic clock."""
+    import oracle
+
+    barrier, rounds = job
+    P, a, b, g, key = _oracle_inputs()
+    out = []
+    for _ in range(rounds):
+        barrier.wait()
         t0 = time.perf_counter()
         oracle.hrotate(P, L, a, b, [g], [key])
-        times.append(time.perf_counter() - t0)
-    return times
+        out.append((t0, time.perf_counter()))
+    return out
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+
+    return platform.machine()
+
+
+def oracle_rounds(procs, rounds):
+    """`rounds` rounds of `procs` concurrent oracle HRotates, one process per
+    host core (spawned: no process is forked from one that has initialised
+    CUDA).  Returns the span of each round (first start to last end) and every
+    process's own HRotate time."""
+    import multiprocessing as mp
+
+    mpc = mp.get_context("spawn")
+    with mpc.Manager() as man:
+        barrier = man.Barrier(procs)
+        with mpc.Pool(procs) as pool:
+            res = pool.map(_oracle_worker, [(barrier, rounds)] * procs)
+    spans = [max(r[k][1] for r in res) - min(r[k][0] for r in res) for k in range(rounds)]
+    singles = [r[k][1] - r[k][0] for r in res for k in range(rounds)]
+    return spans, singles
+
+
+def oracle_baseline(procs, rounds):
+    """The cpu_baseline object: the oracle as it stands on every host core."""
+    spans, singles = oracle_rounds(procs, rounds)
+    span = statistics.mean(spans)
+    return {"value": procs / span, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": (f"{procs} concurrent oracle HRotate(r=1) runs at N=2^16, ell=24, k=8, dnum=3, one process "
+                       f"per host core, {rounds} round(s)"),
+            "single_thread_s": statistics.median(singles), "single_thread_value": 1.0 / statistics.median(singles),
+            "nproc": host_cores(), "cpu_model": cpu_model()}
 
 
 def base_config(C):
@@ -588,16 +648,18 @@ def run_reference(args, rank, world):
         return 0
     W = min(args.warmup, 1)
     K = max(1, min(args.steps, 2))
-    _ = oracle_keyswitch_seconds(W) if W else None
-    times = oracle_keyswitch_seconds(K)
-    t = sum(times) / len(times)
-    value = 1.0 / t
-    sample = (f"oracle HRotate(r=1) of one ciphertext at N=2^16, ell=24, k=8, dnum=3 per step "
-              f"({K} timed steps, {W} warm-up, capped so the run ends in minutes)")
+    procs = args.oracle_procs or host_cores()
+    spans, singles = oracle_rounds(procs, W + K)
+    t = statistics.mean(spans[W:])
+    value = procs / t
+    sample = (f"per step {procs} concurrent oracle HRotate(r=1) runs (one process per host core) at N=2^16, "
+              f"ell=24, k=8, dnum=3 ({K} timed steps, {W} warm-up, capped so the run ends in minutes)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": W, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "u64", "data": "synthetic", "config": base_config(1),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "dtype": "u64", "data": "synthetic", "config": base_config(procs),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": sample,
+                             "single_thread_s": statistics.median(singles[W * procs:]), "nproc": host_cores(),
+                             "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -801,9 +863,7 @@ def run_gpu(args, rank, world, local_rank):
             line["other_rows"]["steps"] = measure_steps(ctx, ckks, torch)
             line["other_rows"]["serving"] = measure_serving(ctx, ckks, torch)
         if world == 1 and not args.no_cpu_baseline:
-            times = oracle_keyswitch_seconds(1)
-            line["cpu_baseline"] = {"value": 1.0 / times[0], "unit": UNIT, "cores": 1, "kind": "oracle",
-                                    "sample": "1 oracle HRotate(r=1) at N=2^16, ell=24, k=8, dnum=3, one thread"}
+            line["cpu_baseline"] = oracle_baseline(args.oracle_procs or host_cores(), 1)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
@@ -846,6 +906,8 @@ def main():
     ap.add_argument("--e2e-streams", type=int, default=4,
                     help="compute streams of the end-to-end measurement (host copies run on two more)")
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--oracle-procs", type=int, default=0,
+                    help="oracle processes for the CPU baseline and the reference arm (0: one per host core)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-rows", action="store_true", help="skip the Rescale / PtMatVecMult side measurements")
     ap.add_argument("--no-tune", action="store_true", help="keep the default NTT tile shapes (no autotuning)")
