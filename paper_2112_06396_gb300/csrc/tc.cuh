@@ -106,16 +106,23 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 // Waits for the phase of parity `parity` of the mbarrier to complete, at most
 // about `limit_ns` nanoseconds, giving up early once *abort (shared memory,
 // set by another role that gave up) is nonzero.  False if the phase did not
-// complete.
+// complete.  Between polls the warp sleeps (32 ns doubling to 128 ns), so a
+// waiting role takes few issue slots from the working ones; the abort flag and
+// the timer are read every 16th poll.
 __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, uint64_t limit_ns,
                                           const volatile int *abort = nullptr) {
     if (mbar_try(mbar, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
+    uint32_t nap = 32;
     // the iteration cap bounds the loop even if the timer did not advance
     for (uint32_t i = 0; i < (1u << 26); ++i) {
+        __nanosleep(nap);
+        if (nap < 128) nap <<= 1;
         if (mbar_try(mbar, parity)) return true;
-        if (abort != nullptr && *abort) return false;
-        if (globaltimer_ns() - t0 > limit_ns) return false;
+        if ((i & 15) == 15) {
+            if (abort != nullptr && *abort) return false;
+            if (globaltimer_ns() - t0 > limit_ns) return false;
+        }
     }
     return false;
 }
