@@ -626,6 +626,69 @@ def oracle_rounds(procs, rounds):
     return spans, singles
 
 
+ORACLE_TASKS = ["config1_keyswitch", "config3_keyswitch_l4", "config3_keyswitch_l14", "config3_keyswitch_l24",
+                "config4_ptmatvec_l24_8x1", "config5_hrotate_n15_l24", "config5_mult_n15_l24"]
+
+
+def _oracle_side_task(name):
+    """One single-thread oracle timing of a side configuration (spawned process).
+    Keys are uniform residues: the arithmetic, hence the time, does not depend
+    on them.  Returns (name, seconds, description)."""
+    import oracle
+
+    def setup(logN, ell_max, k, dnum, bits):
+        primes = oracle.gen_primes(bits, logN, ell_max + k)
+        return oracle.Params(logN, ell_max, k, dnum, primes=primes), primes
+
+    def ukey(P, primes, tag):
+        return np.stack([np.stack([synth.uniform_residues(primes, P.N, f"{tag}/{j}/{r}") for r in range(2)])
+                         for j in range(P.dnum)])
+
+    def timed(fn):
+        t0 = time.perf_counter()
+        fn()
+        return time.perf_counter() - t0
+
+    if name == "config1_keyswitch":
+        P, pr = setup(12, 6, 3, 2, 50)
+        key, a = ukey(P, pr, "ot/c1/k"), synth.uniform_residues(pr[:6], P.N, "ot/c1/a")
+        return name, timed(lambda: oracle.keyswitch(P, 6, a, key)), "KeySwitch N=2^12 ell=6 k=3 dnum=2"
+    if name.startswith("config3_keyswitch_l"):
+        ell = int(name.rsplit("_l", 1)[1])
+        P, pr = setup(LOGN, L, K_SP, DNUM, BITS)
+        key, a = ukey(P, pr, "ot/c3/k"), synth.uniform_residues(pr[:ell], P.N, f"ot/c3/a{ell}")
+        return name, timed(lambda: oracle.keyswitch(P, ell, a, key)), f"KeySwitch N=2^16 ell={ell} k=8 dnum=3"
+    if name == "config4_ptmatvec_l24_8x1":
+        P, pr = setup(LOGN, L, K_SP, DNUM, BITS)
+        nb, ng, twoN = 8, 1, 2 << LOGN
+        gb = [1] + [pow(5, i, twoN) for i in range(1, nb)]
+        kb = [None] + [ukey(P, pr, f"ot/c4/kb{i}") for i in range(1, nb)]
+        ext = [int(x) for x in pr[:L]] + [int(x) for x in pr[L:]]
+        diags = [synth.uniform_residues(ext, P.N, f"ot/c4/d{i}") for i in range(nb * ng)]
+        a, b = synth.uniform_residues(pr[:L], P.N, "ot/c4/a"), synth.uniform_residues(pr[:L], P.N, "ot/c4/b")
+        sec = timed(lambda: oracle.ptmatvec(P, L, a, b, nb, ng, gb, [1], kb, [None], diags, True))
+        return name, sec, "PtMatVecMult N=2^16 ell=24: 8 baby steps x 1 giant step (a quarter of one level), rescaled"
+    if name.startswith("config5_"):
+        P, pr = setup(15, L, K_SP, DNUM, BITS)
+        key = ukey(P, pr, "ot/c5/k")
+        a, b = synth.uniform_residues(pr[:L], P.N, "ot/c5/a"), synth.uniform_residues(pr[:L], P.N, "ot/c5/b")
+        if "hrotate" in name:
+            return name, timed(lambda: oracle.hrotate(P, L, a, b, [5], [key])), "HRotate(r=1) N=2^15 ell=24"
+        a2, b2 = synth.uniform_residues(pr[:L], P.N, "ot/c5/a2"), synth.uniform_residues(pr[:L], P.N, "ot/c5/b2")
+        return name, timed(lambda: oracle.mult(P, L, a, b, a2, b2, key)), "Mult+Relin+Rescale N=2^15 ell=24"
+    raise ValueError(name)
+
+
+def oracle_side_rows(procs):
+    """Single-thread oracle times of the side configurations, run side by side
+    on the host cores (spawned processes)."""
+    import multiprocessing as mp
+
+    with mp.get_context("spawn").Pool(min(procs, len(ORACLE_TASKS))) as pool:
+        res = pool.map(_oracle_side_task, ORACLE_TASKS)
+    return {n: {"seconds": sec, "ops_per_s": 1.0 / sec, "what": what} for n, sec, what in res}
+
+
 def oracle_baseline(procs, rounds):
     """The cpu_baseline object: the oracle as it stands on every host core."""
     spans, singles = oracle_rounds(procs, rounds)
@@ -864,6 +927,8 @@ def run_gpu(args, rank, world, local_rank):
             line["other_rows"]["serving"] = measure_serving(ctx, ckks, torch)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = oracle_baseline(args.oracle_procs or host_cores(), 1)
+            if not args.no_rows:
+                line["other_rows"]["oracle_single_thread"] = oracle_side_rows(args.oracle_procs or host_cores())
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
