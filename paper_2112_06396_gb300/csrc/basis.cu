@@ -167,10 +167,8 @@ __global__ void __launch_bounds__(128, 7) bconv_split_kernel(const __grid_consta
 // K) is the plan's precomputed image; the f32 sums land in tensor memory,
 // column 8t + c of the coefficient's lane.  A constant column (2048 in A, 4096
 // in B) adds 2^23 to every sum, so the bits of the f32 result read as the
-// integer 0x4B000000 + S_tc with no conversion; the epilogue combines the
-// seven columns of a target with wide multiply-adds into lo + hi * 2^32,
-// folds hi by [2^32]_t, adds the plan's dst_off (which removes the biases and
-// sub_t) and reduces once: the output is in [0, 3t) for the lazy forward NTT.
+// integer 0x4B000000 + S_tc with no conversion; the epilogue recombines the
+// seven columns of a target (the arithmetic is spelled out before the kernel).
 constexpr uint64_t kTcWaitNs = 1000000000ull;  // give up after a second (ns)
 
 __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {

@@ -70,19 +70,6 @@ __device__ __forceinline__ void mbar_init(uint64_t *mbar, uint32_t count) {
 __device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(mbar)) : "memory");
 }
-__device__ __forceinline__ bool mbar_test(uint64_t *mbar, uint32_t parity) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t"
-        ".reg .pred p;\n\t"
-        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t"
-        "}"
-        : "=r"(done)
-        : "r"(smem_addr(mbar)), "r"(parity)
-        : "memory");
-    return done != 0;
-}
 // Potentially blocking test: the thread is suspended, without issuing
 // instructions, until the phase completes or about suspend_ns pass.
 __device__ __forceinline__ bool mbar_try(uint64_t *mbar, uint32_t parity, uint32_t suspend_ns = 1000000u) {
@@ -141,22 +128,9 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
-// 16 consecutive 32-bit columns of this thread's tensor-memory lane (the warp
-// reads lanes 32*(warp % 4) .. +31), waited for inside the same block so the
-// values are complete when the statement ends.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15}, [%16];\n\t"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr)
-        : "memory");
-}
-
-// 32 consecutive 32-bit columns of this thread's lane, without waiting: the
-// registers are valid only after tmem_wait_ld() and tmem_hold() on them.
+// 32 consecutive 32-bit columns of this thread's tensor-memory lane (the warp
+// reads lanes 32*(warp % 4) .. +31), without waiting: the registers are valid
+// only after tmem_wait_ld() and tmem_hold() on them.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
