@@ -13,7 +13,7 @@
  * fusion: each function follows the paper's definition or algorithm in the
  * paper's order so it can be read against the paper.
  *
- * Conventions (readings of the paper recorded in the design doc):
+ * Conventions (readings of the paper where it is silent or ambiguous):
  *  - L and ell count limbs; alpha = ceil(L/dnum); beta = ceil(ell/alpha).
  *  - primes[0..L-1] are the chain q_0..q_{L-1}; primes[L..L+k-1] the special
  *    primes p_0..p_{k-1}.  At level ell the extended basis is ordered
