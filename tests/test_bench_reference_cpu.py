@@ -22,3 +22,13 @@ def test_reference_arm_json_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert d["config"]["workload"]
+
+
+def test_oracle_side_task_runs():
+    """The side-configuration oracle timing (one task, in this process)."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    name, sec, what = bench._oracle_side_task("config1_keyswitch")
+    assert name == "config1_keyswitch" and sec > 0 and "N=2^12" in what
+    assert set(bench.ORACLE_TASKS) >= {"config1_keyswitch", "config4_ptmatvec_l24_8x1"}
