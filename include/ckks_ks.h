@@ -36,7 +36,9 @@
  *    memory, 16-byte aligned, not shared with concurrently running calls.
  *  - Errors: CKKS_EINVAL for bad arguments (checked on the host before any
  *    launch), CKKS_ECUDA when a launch fails (ckks_last_cuda_error() gives the
- *    cudaError_t).  No call allocates device memory after ckks_ctx_create() except
+ *    cudaError_t), CKKS_EUNSUPPORTED for parameters a call cannot serve, and
+ *    CKKS_ETIMEOUT from ckks_poll_status when a bounded device-side wait gave up
+ *    (see there).  No call allocates device memory after ckks_ctx_create() except
  *    ckks_server_create().
  */
 #ifndef CKKS_KS_H
