@@ -17,9 +17,10 @@ pytestmark = pytest.mark.gpu
 # widest of the integer path too), 18 (alpha = 16 sources, the largest
 # supported), 16 with more than 32 targets (alpha = 14: ModUp converts to up to
 # 34 limbs and ModDown to 40, in two chunks of uneven size), and N = 2^10
-# (8 tiles of 128 coefficients, fewer than the CTAs a launch could use)
+# (8 tiles of 128 coefficients, fewer than the CTAs a launch could use), and the
+# longest chain (L = 64) with alpha = 16 sources: conversions to 56 and 64 limbs
 SHAPES = [(12, 6, 3, 2, 50), (11, 7, 3, 3, 50), (11, 10, 5, 2, 54), (11, 32, 8, 2, 50), (11, 40, 8, 3, 50),
-          (10, 5, 2, 2, 50)]
+          (10, 5, 2, 2, 50), (10, 64, 8, 4, 50)]
 
 
 @pytest.fixture(scope="module", params=SHAPES, ids=lambda s: "n%d_L%d_k%d_d%d_b%d" % s)
