@@ -430,6 +430,21 @@ def measure_steps(ctx, ckks, torch, reps=10):
     return rows
 
 
+def measure_rotation_sweep(ctx, items, lanes, torch, reps=10):
+    """The headline step with every ciphertext rotated by 5^r, r in {1, 2, 2^14}
+    (the Automorph gather pattern of the inner product depends on g).  The keys
+    of the headline are reused: the arithmetic, hence the time, does not depend
+    on them (these outputs are not checked; parity at each g is in the tests)."""
+    out = {}
+    twoN = 2 << LOGN
+    for r in (1, 2, 1 << 14):
+        g = pow(5, r, twoN)
+        its = [dict(it, g=g) for it in items]
+        ms = _timed(torch, lambda: step(ctx, its, lanes), reps)
+        out[f"r={r}"] = {"galois": g, "ms_per_step": ms, "keyswitch_per_s": len(items) / ms * 1e3}
+    return out
+
+
 def measure_other_rows(ctx, ckks, torch, reps=5):
     """Rescale (Alg. 1's ModDown_{B,1}) of one ciphertext, and a CoeffToSlot-shaped
     PtMatVecMult: fftIter = 3 levels at ell = 24, 23, 22 (Alg. 8 with 8 baby x 4
@@ -917,9 +932,11 @@ def run_gpu(args, rank, world, local_rank):
                     "d2h_bytes_per_step": bytes_io, "matches_device_result": ok},
         }
         if not args.no_rows:
+            sweep = measure_rotation_sweep(ctx, items, lanes, torch)
             del items, lanes, lane1, lanes_e, dev_in, dev_out
             torch.cuda.empty_cache()
             line["other_rows"] = measure_other_rows(ctx, ckks, torch)
+            line["other_rows"]["rotation_sweep"] = sweep
             line["other_rows"]["batched_keyswitch"] = measure_batched(ctx, ckks, torch)
             line["other_rows"]["small_keyswitch"] = measure_small_keyswitch(ckks, torch)
             line["other_rows"]["hoisted_rotations"] = measure_hoisted(ctx, ckks, torch)

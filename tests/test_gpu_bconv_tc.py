@@ -113,12 +113,14 @@ def cfgB(oracle_lib):
     return Setup(oracle_lib, 16, 24, 8, 3, 54)
 
 
-def test_headline_shape(cfgB):
-    """HRotate at N=2^16, ell=24, k=8, dnum=3: both paths equal and the oracle."""
+@pytest.mark.parametrize("r", [1, 2, 1 << 14])
+def test_headline_shape(cfgB, r):
+    """HRotate by 5^r (r = 1, 2 and 2^14, the largest rotation of N/2 slots)
+    at N=2^16, ell=24, k=8, dnum=3: both conversion paths equal the oracle."""
     S = cfgB
     P, ctx = S.P, S.ctx
-    g = 5
-    key = S.key(g, "gpu/tc/B/key5")[0]
+    g = pow(5, r, 2 << 16)
+    key = S.key(g, "gpu/tc/B/key%d" % r)[0]
     a, b = S.ct(P.L, "gpu/tc/B/ct")
     da, db, dk = dev(a), dev(b), dev(key)
     tc, sp = _both(ctx, lambda: _h(ctx.hrotate(da, db, P.L, [g], [dk])[0]))
