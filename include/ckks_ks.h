@@ -414,7 +414,11 @@ int ckks_server_stats(const ckks_server *srv, ckks_server_stats_t *stats);
  * of polls (about a second), skips its outputs and records the fact in the
  * context: once the stream's work has finished, ckks_poll_status returns
  * CKKS_ETIMEOUT for it (once; the record is cleared) and the outputs of that
- * work are not valid. */
+ * work are not valid.  The record is one word per context, shared by its
+ * streams: a timeout in work on another stream is reported by whichever poll
+ * reads it first, and one raised between this call's read and its clear is
+ * lost, so poll once more after synchronising every stream that uses the
+ * context when a complete account is needed. */
 int ckks_poll_status(ckks_ctx *ctx, ckks_stream_t stream, int *done);
 
 /* Self-test of that bounded wait (no counterpart in the paper): launches one
