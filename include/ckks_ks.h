@@ -34,6 +34,12 @@
  *    Outputs must not alias inputs unless a call says so.
  *  - Workspace: calls taking `ws` need ckks_workspace_bytes() bytes of device
  *    memory, 16-byte aligned, not shared with concurrently running calls.
+ *  - Host threads: compute calls only read the context (apart from recording
+ *    the last CUDA error), so several host threads may issue them at once on
+ *    different streams with separate workspaces while the measurement hook is
+ *    off.  The calls that change the context (ckks_key_register_seed,
+ *    ckks_key_unregister, ckks_bconv_select, ckks_tune_set, ckks_autotune,
+ *    ckks_profile_*, ckks_ctx_destroy) must not overlap any other call on it.
  *  - Errors: CKKS_EINVAL for bad arguments (checked on the host before any
  *    launch), CKKS_ECUDA when a launch fails (ckks_last_cuda_error() gives the
  *    cudaError_t), CKKS_EUNSUPPORTED for parameters a call cannot serve, and
