@@ -189,6 +189,8 @@ class Context:
     def __init__(self, logN, q, p, dnum, device=0):
         self.logN, self.L, self.k, self.dnum = int(logN), len(q), len(p), int(dnum)
         self.N = 1 << self.logN
+        self._compressed = set()  # data pointers registered as compressed keys
+        self._ws_bytes = {}  # (op, level, r) -> ckks_workspace_bytes
         self.q, self.p = [int(x) for x in q], [int(x) for x in p]
         self.device = torch.device("cuda", device)
         qa = (ctypes.c_uint64 * self.L)(*self.q)
@@ -224,6 +226,57 @@ class Context:
 
     def ext_primes(self, ell):
         return self.q[:ell] + self.p
+
+    # ------------------------------------------------------------ argument checks
+    # The library receives bare device pointers and cannot see how large a
+    # buffer is, so every tensor is checked here before its pointer is passed
+    # on: it must be on this context's device, of the expected dtype,
+    # contiguous, and hold at least the words the call reads or writes.  A
+    # failed check raises CkksError (CKKS_EINVAL) and nothing is launched.
+    def _arg(self, t, what, words, dtype=torch.uint64):
+        if not isinstance(t, torch.Tensor):
+            raise CkksError(f"{what}: expected a torch tensor, got {type(t).__name__}", CKKS_EINVAL)
+        if t.device != self.device:
+            raise CkksError(f"{what}: tensor on {t.device}, the context is on {self.device}", CKKS_EINVAL)
+        if t.dtype != dtype:
+            raise CkksError(f"{what}: dtype {t.dtype}, expected {dtype}", CKKS_EINVAL)
+        if not t.is_contiguous():
+            raise CkksError(f"{what}: the tensor is not contiguous", CKKS_EINVAL)
+        if t.numel() < words:
+            raise CkksError(f"{what}: {t.numel()} elements, the call needs {words}", CKKS_EINVAL)
+        return t
+
+    def _poly(self, t, what, nlimbs):
+        """A polynomial of at least nlimbs limbs of N words."""
+        return self._arg(t, what, max(int(nlimbs), 0) * self.N)
+
+    def _key_words(self, rows):
+        return rows * self.dnum * (self.L + self.k) * self.N
+
+    def _key(self, key, what="key"):
+        """A key-switching key [dnum][2][L+k][N], or its rows b_j [dnum][L+k][N]
+        when it is registered as a compressed key."""
+        compressed = isinstance(key, torch.Tensor) and key.data_ptr() in self._compressed
+        return self._arg(key, what, self._key_words(1 if compressed else 2))
+
+    def _ws(self, ws, nbytes, what="ws"):
+        return self._arg(ws, what, (int(nbytes) + 7) // 8)
+
+    def _ws_op(self, ws, op, level, r=1):
+        """The caller's workspace for `op` at `level` (checked), or a new one."""
+        if ws is None:
+            return self.workspace(op, level, r)
+        k = (int(op), int(level), int(r))
+        nbytes = self._ws_bytes.get(k)
+        if nbytes is None:
+            nbytes = self._ws_bytes[k] = self.workspace_bytes(op, level, r)
+        return self._ws(ws, nbytes)
+
+    @staticmethod
+    def _same_len(n, **lists):
+        for name, xs in lists.items():
+            if xs is not None and len(xs) != n:
+                raise CkksError(f"{name}: {len(xs)} entries, expected {n}", CKKS_EINVAL)
 
     def table_bytes(self):
         return int(lib().ckks_ctx_table_bytes(self._h))
@@ -311,43 +364,55 @@ class Context:
 
     # ------------------------------------------------------------ operations
     def ntt(self, x, level, first=0, count=None, stream=None):
-        count = x.shape[0] - first if count is None else count
+        self._arg(x, "x", 0)
+        count = (x.shape[0] if x.dim() else 0) - first if count is None else count
+        self._poly(x, "x", first + count)
         _check(lib().ckks_ntt(self._h, _p(x), level, first, count, _stream(stream)), self._h)
         return x
 
     def intt(self, x, level, first=0, count=None, stream=None):
-        count = x.shape[0] - first if count is None else count
+        self._arg(x, "x", 0)
+        count = (x.shape[0] if x.dim() else 0) - first if count is None else count
+        self._poly(x, "x", first + count)
         _check(lib().ckks_intt(self._h, _p(x), level, first, count, _stream(stream)), self._h)
         return x
 
     def automorph(self, x, galois, out=None, stream=None):
-        out = torch.empty_like(x) if out is None else out
-        _check(lib().ckks_automorph(self._h, _p(x), _p(out), x.shape[0], galois, _stream(stream)), self._h)
+        self._arg(x, "x", 0)
+        nlimbs = x.shape[0] if x.dim() else 0
+        self._poly(x, "x", nlimbs)
+        out = torch.empty_like(x) if out is None else self._poly(out, "out", nlimbs)
+        _check(lib().ckks_automorph(self._h, _p(x), _p(out), nlimbs, galois, _stream(stream)), self._h)
         return out
 
     def modup(self, a, level, digit, out=None, ws=None, stream=None):
-        out = self.empty(level + self.k) if out is None else out
-        ws = self.workspace(OP_MODUP, level) if ws is None else ws
+        self._poly(a, "a", level)
+        out = self.empty(level + self.k) if out is None else self._poly(out, "out", level + self.k)
+        ws = self._ws_op(ws, OP_MODUP, level)
         _check(lib().ckks_modup(self._h, _p(a), level, digit, _p(out), _p(ws), _stream(stream)), self._h)
         return out
 
     def ksk_inner_prod(self, digits, level, key, u=None, v=None, stream=None):
-        u = self.empty(level + self.k) if u is None else u
-        v = self.empty(level + self.k) if v is None else v
+        self._poly(digits, "digits", self.beta(level) * (level + self.k))
+        self._key(key)
+        u = self.empty(level + self.k) if u is None else self._poly(u, "u", level + self.k)
+        v = self.empty(level + self.k) if v is None else self._poly(v, "v", level + self.k)
         _check(lib().ckks_ksk_inner_prod(self._h, _p(digits), level, _p(key), _p(u), _p(v), _stream(stream)),
                self._h)
         return u, v
 
     def moddown(self, x, level, out=None, ws=None, stream=None):
-        out = self.empty(level) if out is None else out
-        ws = self.workspace(OP_MODDOWN, level) if ws is None else ws
+        self._poly(x, "x", level + self.k)
+        out = self.empty(level) if out is None else self._poly(out, "out", level)
+        ws = self._ws_op(ws, OP_MODDOWN, level)
         _check(lib().ckks_moddown(self._h, _p(x), level, _p(out), _p(ws), _stream(stream)), self._h)
         return out
 
     def moddown_noalloc(self, x, level, out=None, stream=None):
         """ModDown with its scratch in the library's fixed 16 MiB device array
         (no workspace; (k + level) * N must not exceed 2^21 words)."""
-        out = self.empty(level) if out is None else out
+        self._poly(x, "x", level + self.k)
+        out = self.empty(level) if out is None else self._poly(out, "out", level)
         rc = lib().ckks_moddown_noalloc(self._h, _p(x), level, _p(out), _stream(stream))
         if rc == CKKS_EUNSUPPORTED:
             raise CkksError(f"ckks_moddown_noalloc: (k + level) * N = {(self.k + level) * self.N} words exceeds "
@@ -356,36 +421,52 @@ class Context:
         return out
 
     def pmodup(self, x, level, out=None, stream=None):
-        out = self.empty(level + self.k) if out is None else out
+        self._poly(x, "x", level)
+        out = self.empty(level + self.k) if out is None else self._poly(out, "out", level + self.k)
         _check(lib().ckks_pmodup(self._h, _p(x), level, _p(out), _stream(stream)), self._h)
         return out
 
     def rescale(self, x, level, out=None, ws=None, stream=None):
-        out = self.empty(level - 1) if out is None else out
-        ws = self.workspace(OP_RESCALE, level) if ws is None else ws
+        self._poly(x, "x", level)
+        out = self.empty(level - 1) if out is None else self._poly(out, "out", level - 1)
+        ws = self._ws_op(ws, OP_RESCALE, level)
         _check(lib().ckks_rescale(self._h, _p(x), level, _p(out), _p(ws), _stream(stream)), self._h)
         return out
 
     def keyswitch(self, a, level, key, u=None, v=None, ws=None, stream=None):
-        u = self.empty(level) if u is None else u
-        v = self.empty(level) if v is None else v
-        ws = self.workspace(OP_KEYSWITCH, level) if ws is None else ws
+        self._poly(a, "a", level)
+        self._key(key)
+        u = self.empty(level) if u is None else self._poly(u, "u", level)
+        v = self.empty(level) if v is None else self._poly(v, "v", level)
+        ws = self._ws_op(ws, OP_KEYSWITCH, level)
         _check(lib().ckks_keyswitch(self._h, _p(a), level, _p(key), _p(u), _p(v), _p(ws), _stream(stream)), self._h)
         return u, v
 
     def rotate(self, a, b, level, galois, key, oa=None, ob=None, ws=None, stream=None):
-        oa = self.empty(level) if oa is None else oa
-        ob = self.empty(level) if ob is None else ob
-        ws = self.workspace(OP_ROTATE, level) if ws is None else ws
+        self._poly(a, "a", level)
+        self._poly(b, "b", level)
+        self._key(key)
+        oa = self.empty(level) if oa is None else self._poly(oa, "oa", level)
+        ob = self.empty(level) if ob is None else self._poly(ob, "ob", level)
+        ws = self._ws_op(ws, OP_ROTATE, level)
         _check(lib().ckks_rotate(self._h, _p(a), _p(b), level, galois, _p(key), _p(oa), _p(ob), _p(ws),
                                  _stream(stream)), self._h)
         return oa, ob
 
     def hrotate(self, a, b, level, galois, keys, outs=None, ws=None, stream=None):
         r = len(galois)
+        self._same_len(r, keys=keys, outs=outs)
+        self._poly(a, "a", level)
+        self._poly(b, "b", level)
+        for i, k in enumerate(keys):
+            self._key(k, f"keys[{i}]")
         if outs is None:
             outs = [(self.empty(level), self.empty(level)) for _ in range(r)]
-        ws = self.workspace(OP_HROTATE, level, r) if ws is None else ws
+        else:
+            for i, (oa, ob) in enumerate(outs):
+                self._poly(oa, f"outs[{i}][0]", level)
+                self._poly(ob, f"outs[{i}][1]", level)
+        ws = self._ws_op(ws, OP_HROTATE, level, r)
         g = (ctypes.c_uint32 * r)(*galois)
         kp = (_vp * r)(*[k.data_ptr() for k in keys])
         oa = (_vp * r)(*[o[0].data_ptr() for o in outs])
@@ -393,12 +474,16 @@ class Context:
         _check(lib().ckks_hrotate(self._h, _p(a), _p(b), level, r, g, kp, oa, ob, _p(ws), _stream(stream)), self._h)
         return outs
 
-    def batch_workspace(self, levels):
+    def batch_workspace_bytes(self, levels):
         n = len(levels)
         lv = (_i * max(n, 1))(*[int(x) for x in levels])
         nbytes = ctypes.c_size_t()
         _check(lib().ckks_batch_workspace_bytes(self._h, n, lv, ctypes.byref(nbytes)))
-        return torch.empty(max(nbytes.value // 8, 2), dtype=torch.uint64, device=self.device)
+        return int(nbytes.value)
+
+    def batch_workspace(self, levels):
+        nbytes = self.batch_workspace_bytes(levels)
+        return torch.empty(max(nbytes // 8, 2), dtype=torch.uint64, device=self.device)
 
     def keyswitch_batch(self, a, b, levels, galois, keys, outs=None, ws=None, stream=None, seeds=None):
         """Batched key switching.  a, keys: lists of tensors; b: None or a list
@@ -407,9 +492,22 @@ class Context:
         or one seed per entry (keys are then compressed, b rows only).
         Returns [(oa, ob)]."""
         n = len(a)
+        self._same_len(n, levels=levels, keys=keys, b=b, galois=galois, outs=outs, seeds=seeds)
+        for i in range(n):
+            self._poly(a[i], f"a[{i}]", levels[i])
+            if b is not None and b[i] is not None:
+                self._poly(b[i], f"b[{i}]", levels[i])
+            if seeds is None:
+                self._key(keys[i], f"keys[{i}]")
+            else:
+                self._arg(keys[i], f"keys[{i}]", self._key_words(1))
         if outs is None:
             outs = [(self.empty(levels[i]), self.empty(levels[i])) for i in range(n)]
-        ws = self.batch_workspace(levels) if ws is None else ws
+        else:
+            for i, (oa, ob) in enumerate(outs):
+                self._poly(oa, f"outs[{i}][0]", levels[i])
+                self._poly(ob, f"outs[{i}][1]", levels[i])
+        ws = self.batch_workspace(levels) if ws is None else self._ws(ws, self.batch_workspace_bytes(levels))
         m = max(n, 1)
         ap = (_vp * m)(*[x.data_ptr() for x in a])
         bp = None if b is None else (_vp * m)(*[None if x is None else x.data_ptr() for x in b])
@@ -431,18 +529,32 @@ class Context:
         """cts: list of (a, b); rotations: per ciphertext a list of (galois, key).
         Returns per ciphertext a list of (oa, ob), one per rotation."""
         n = len(cts)
+        self._same_len(n, levels=levels, rotations=rotations, outs=outs)
         nrot = [len(r) for r in rotations]
         flat = [gk for r in rotations for gk in r]
+        for c in range(n):
+            self._poly(cts[c][0], f"cts[{c}][0]", levels[c])
+            self._poly(cts[c][1], f"cts[{c}][1]", levels[c])
+            for i, (_, k) in enumerate(rotations[c]):
+                self._key(k, f"rotations[{c}][{i}] key")
         if outs is None:
             outs = [[(self.empty(levels[c]), self.empty(levels[c])) for _ in rotations[c]] for c in range(n)]
+        else:
+            for c in range(n):
+                self._same_len(nrot[c], **{f"outs[{c}]": outs[c]})
+                for i, (oa, ob) in enumerate(outs[c]):
+                    self._poly(oa, f"outs[{c}][{i}][0]", levels[c])
+                    self._poly(ob, f"outs[{c}][{i}][1]", levels[c])
         flat_out = [o for oc in outs for o in oc]
         m = max(len(flat), 1)
         lv = (_i * max(n, 1))(*[int(x) for x in levels])
         nr = (_i * max(n, 1))(*nrot)
+        nbytes = ctypes.c_size_t()
+        _check(lib().ckks_hrotate_batch_workspace_bytes(self._h, n, lv, nr, ctypes.byref(nbytes)))
         if ws is None:
-            nbytes = ctypes.c_size_t()
-            _check(lib().ckks_hrotate_batch_workspace_bytes(self._h, n, lv, nr, ctypes.byref(nbytes)))
             ws = torch.empty(max(nbytes.value // 8, 2), dtype=torch.uint64, device=self.device)
+        else:
+            self._ws(ws, nbytes.value)
         arr = lambda xs, k: (_vp * k)(*[x.data_ptr() for x in xs])
         _check(lib().ckks_hrotate_batch(self._h, n, arr([c[0] for c in cts], max(n, 1)),
                                         arr([c[1] for c in cts], max(n, 1)), lv, nr,
@@ -453,23 +565,30 @@ class Context:
 
     def keygen_ksk_seeded(self, s, e, seed, galois, key_b=None, ws=None, stream=None):
         """Compressed key (rows b_j only, [dnum][L+k][N]); a_j comes from seed."""
+        self._arg(s, "s", self.N, torch.int64)
+        self._arg(e, "e", self.dnum * self.N, torch.int64)
         key_b = torch.empty((self.dnum, self.L + self.k, self.N), dtype=torch.uint64,
-                            device=self.device) if key_b is None else key_b
-        ws = self.workspace(OP_KEYGEN_SEEDED, 1) if ws is None else ws
+                            device=self.device) if key_b is None else self._arg(key_b, "key_b", self._key_words(1))
+        ws = self._ws_op(ws, OP_KEYGEN_SEEDED, 1)
         _check(lib().ckks_keygen_ksk_seeded(self._h, _p(s), _p(e), int(seed) & 0xFFFFFFFFFFFFFFFF, int(galois),
                                             _p(key_b), _p(ws), _stream(stream)), self._h)
         return key_b
 
     def register_compressed_key(self, key_b, seed):
         """Every call of this context that receives key_b treats it as a compressed key."""
+        self._arg(key_b, "key_b", self._key_words(1))
         _check(lib().ckks_key_register_seed(self._h, _p(key_b), int(seed) & 0xFFFFFFFFFFFFFFFF))
+        self._compressed.add(key_b.data_ptr())
 
     def unregister_compressed_key(self, key_b):
+        self._arg(key_b, "key_b", 0)
         _check(lib().ckks_key_unregister(self._h, _p(key_b)))
+        self._compressed.discard(key_b.data_ptr())
 
     def ksk_expand(self, key_b, seed, key=None, stream=None):
+        self._arg(key_b, "key_b", self._key_words(1))
         key = torch.empty((self.dnum, 2, self.L + self.k, self.N), dtype=torch.uint64,
-                          device=self.device) if key is None else key
+                          device=self.device) if key is None else self._arg(key, "key", self._key_words(2))
         _check(lib().ckks_ksk_expand(self._h, _p(key_b), int(seed) & 0xFFFFFFFFFFFFFFFF, _p(key), _stream(stream)),
                self._h)
         return key
@@ -477,9 +596,12 @@ class Context:
     def mult(self, a1, b1, a2, b2, level, key, oa=None, ob=None, ws=None, stream=None, new=False):
         """Algorithm 2 (Mult + relinearisation + Rescale), or Algorithm 7 (NewMult)
         with new=True; outputs at level-1."""
-        oa = self.empty(level - 1) if oa is None else oa
-        ob = self.empty(level - 1) if ob is None else ob
-        ws = self.workspace(OP_NEWMULT if new else OP_MULT, level) if ws is None else ws
+        for name, t in (("a1", a1), ("b1", b1), ("a2", a2), ("b2", b2)):
+            self._poly(t, name, level)
+        self._key(key)
+        oa = self.empty(level - 1) if oa is None else self._poly(oa, "oa", level - 1)
+        ob = self.empty(level - 1) if ob is None else self._poly(ob, "ob", level - 1)
+        ws = self._ws_op(ws, OP_NEWMULT if new else OP_MULT, level)
         fn = lib().ckks_newmult if new else lib().ckks_mult
         _check(fn(self._h, _p(a1), _p(b1), _p(a2), _p(b2), level, _p(key), _p(oa), _p(ob), _p(ws), _stream(stream)),
                self._h)
@@ -488,20 +610,35 @@ class Context:
     def newmult(self, a1, b1, a2, b2, level, key, oa=None, ob=None, ws=None, stream=None):
         return self.mult(a1, b1, a2, b2, level, key, oa, ob, ws, stream, new=True)
 
-    def mult_batch_workspace(self, levels, new=False):
+    def mult_batch_workspace_bytes(self, levels, new=False):
         n = len(levels)
         lv = (_i * max(n, 1))(*[int(x) for x in levels])
         nbytes = ctypes.c_size_t()
         fn = lib().ckks_newmult_batch_workspace_bytes if new else lib().ckks_mult_batch_workspace_bytes
         _check(fn(self._h, n, lv, ctypes.byref(nbytes)))
-        return torch.empty(max(nbytes.value // 8, 2), dtype=torch.uint64, device=self.device)
+        return int(nbytes.value)
+
+    def mult_batch_workspace(self, levels, new=False):
+        nbytes = self.mult_batch_workspace_bytes(levels, new)
+        return torch.empty(max(nbytes // 8, 2), dtype=torch.uint64, device=self.device)
 
     def mult_batch(self, cts1, cts2, levels, keys, outs=None, ws=None, stream=None, new=False):
         """cts1, cts2: lists of (a, b); returns [(oa, ob)] at level-1 each."""
         n = len(cts1)
+        self._same_len(n, cts2=cts2, levels=levels, keys=keys, outs=outs)
+        for i in range(n):
+            for name, t in ((f"cts1[{i}][0]", cts1[i][0]), (f"cts1[{i}][1]", cts1[i][1]),
+                            (f"cts2[{i}][0]", cts2[i][0]), (f"cts2[{i}][1]", cts2[i][1])):
+                self._poly(t, name, levels[i])
+            self._key(keys[i], f"keys[{i}]")
         if outs is None:
             outs = [(self.empty(levels[i] - 1), self.empty(levels[i] - 1)) for i in range(n)]
-        ws = self.mult_batch_workspace(levels, new) if ws is None else ws
+        else:
+            for i, (oa, ob) in enumerate(outs):
+                self._poly(oa, f"outs[{i}][0]", levels[i] - 1)
+                self._poly(ob, f"outs[{i}][1]", levels[i] - 1)
+        ws = (self.mult_batch_workspace(levels, new) if ws is None
+              else self._ws(ws, self.mult_batch_workspace_bytes(levels, new)))
         m = max(n, 1)
         arr = lambda xs: (_vp * m)(*[x.data_ptr() for x in xs])
         lv = (_i * m)(*[int(x) for x in levels])
@@ -514,9 +651,16 @@ class Context:
     def newmult_sum(self, cts1, cts2, level, key, oa=None, ob=None, ws=None, stream=None):
         """Sum of NewMult products with one merged ModDown; cts: lists of (a, b) at one level."""
         n = len(cts1)
-        oa = self.empty(level - 1) if oa is None else oa
-        ob = self.empty(level - 1) if ob is None else ob
-        ws = self.mult_batch_workspace([level] * n, new=True) if ws is None else ws
+        self._same_len(n, cts2=cts2)
+        for i in range(n):
+            for name, t in ((f"cts1[{i}][0]", cts1[i][0]), (f"cts1[{i}][1]", cts1[i][1]),
+                            (f"cts2[{i}][0]", cts2[i][0]), (f"cts2[{i}][1]", cts2[i][1])):
+                self._poly(t, name, level)
+        self._key(key)
+        oa = self.empty(level - 1) if oa is None else self._poly(oa, "oa", level - 1)
+        ob = self.empty(level - 1) if ob is None else self._poly(ob, "ob", level - 1)
+        ws = (self.mult_batch_workspace([level] * n, new=True) if ws is None
+              else self._ws(ws, self.mult_batch_workspace_bytes([level] * n, new=True)))
         arr = lambda xs: (_vp * n)(*[x.data_ptr() for x in xs])
         _check(lib().ckks_newmult_sum(self._h, n, arr([c[0] for c in cts1]), arr([c[1] for c in cts1]),
                                       arr([c[0] for c in cts2]), arr([c[1] for c in cts2]), level, _p(key), _p(oa),
@@ -526,9 +670,21 @@ class Context:
     def ptmatvecmult(self, a, b, level, nb, ng, g_baby, g_giant, key_baby, key_giant, diags, rescale=True,
                      oa=None, ob=None, ws=None, stream=None):
         out_l = level - 1 if rescale else level
-        oa = self.empty(out_l) if oa is None else oa
-        ob = self.empty(out_l) if ob is None else ob
-        ws = self.workspace(OP_PTMATVEC, level, ng) if ws is None else ws
+        self._same_len(nb, g_baby=g_baby, key_baby=key_baby)
+        self._same_len(ng, g_giant=g_giant, key_giant=key_giant)
+        self._same_len(nb * ng, diags=diags)
+        self._poly(a, "a", level)
+        self._poly(b, "b", level)
+        # baby step 0 and giant step 0 are the identity: their keys are not read
+        for i in range(1, nb):
+            self._key(key_baby[i], f"key_baby[{i}]")
+        for t in range(1, ng):
+            self._key(key_giant[t], f"key_giant[{t}]")
+        for d, x in enumerate(diags):
+            self._poly(x, f"diags[{d}]", level + self.k)
+        oa = self.empty(out_l) if oa is None else self._poly(oa, "oa", out_l)
+        ob = self.empty(out_l) if ob is None else self._poly(ob, "ob", out_l)
+        ws = self._ws_op(ws, OP_PTMATVEC, level, ng)
         gb = (ctypes.c_uint32 * nb)(*[int(x) for x in g_baby])
         gg = (ctypes.c_uint32 * ng)(*[int(x) for x in g_giant])
         kb = (_vp * nb)(*[None if k is None else k.data_ptr() for k in key_baby])
@@ -540,9 +696,12 @@ class Context:
 
     def keygen_ksk(self, s, e, a, galois, key=None, ws=None, stream=None):
         """s: int64 [N]; e: int64 [dnum][N]; a: uint64 [dnum][L+k][N]; galois 0 = relinearisation."""
+        self._arg(s, "s", self.N, torch.int64)
+        self._arg(e, "e", self.dnum * self.N, torch.int64)
+        self._arg(a, "a", self._key_words(1))
         key = torch.empty((self.dnum, 2, self.L + self.k, self.N), dtype=torch.uint64,
-                          device=self.device) if key is None else key
-        ws = self.workspace(OP_KEYGEN, 1) if ws is None else ws
+                          device=self.device) if key is None else self._arg(key, "key", self._key_words(2))
+        ws = self._ws_op(ws, OP_KEYGEN, 1)
         _check(lib().ckks_keygen_ksk(self._h, _p(s), _p(e), _p(a), galois, _p(key), _p(ws), _stream(stream)),
                self._h)
         return key
@@ -578,6 +737,12 @@ class Server:
 
     def add_key(self, ctx, key, seed=None):
         """Register a resident key; with seed, key is a compressed key (rows b_j only)."""
+        c = self._ctx(ctx)
+        if c is not None:
+            if seed is None:
+                c._key(key)
+            else:
+                c._arg(key, "key", c._key_words(1))
         hd = _i()
         if seed is None:
             _check(lib().ckks_server_add_key(self._h, int(ctx), _p(key), ctypes.byref(hd)))
@@ -590,7 +755,23 @@ class Server:
     def now_ms(self):
         return float(lib().ckks_server_now_ms(self._h))
 
+    def _ctx(self, ctx):
+        """The context of index ctx (None when out of range: the library rejects it)."""
+        try:
+            i = int(ctx)
+        except (TypeError, ValueError):
+            return None
+        return self.contexts[i] if 0 <= i < len(self.contexts) else None
+
     def _submit(self, op, ctx, level, a, b, a2, b2, galois, key, oa, ob, arrival_ms):
+        c = self._ctx(ctx)
+        if c is not None:
+            for name, t in (("a", a), ("b", b), ("a2", a2), ("b2", b2)):
+                if t is not None:
+                    c._poly(t, name, level)
+            out_l = level - 1 if op in (REQ_MULT, REQ_NEWMULT) else level
+            c._poly(oa, "oa", out_l)
+            c._poly(ob, "ob", out_l)
         r = _Request(op, int(ctx), int(level), _p(a), _p(b), _p(a2), _p(b2), int(galois), int(key), _p(oa), _p(ob),
                      float(arrival_ms))
         rid = ctypes.c_uint64()
