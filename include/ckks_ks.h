@@ -316,7 +316,10 @@ int ckks_ksk_expand(ckks_ctx *ctx, const uint64_t *d_key_b, uint64_t seed, uint6
  * ckks_newmult_sum, ckks_server_add_key) treats that pointer as a compressed key
  * and regenerates its rows a_j on chip.  ckks_key_unregister forgets it.
  * Host-side only (no device work); not thread-safe against concurrent calls on
- * the same context. */
+ * the same context.  The registry is keyed by address: memory freed while
+ * registered and reused for another key would make that key read as
+ * compressed, so unregister before freeing (the Python binding keeps a
+ * registered tensor referenced until it is unregistered). */
 int ckks_key_register_seed(ckks_ctx *ctx, const uint64_t *d_key_b, uint64_t seed);
 int ckks_key_unregister(ckks_ctx *ctx, const uint64_t *d_key_b);
 int ckks_keyswitch_batch_seeded(ckks_ctx *ctx, int n, const uint64_t *const *d_a, const uint64_t *const *d_b,

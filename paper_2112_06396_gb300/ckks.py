@@ -189,7 +189,10 @@ class Context:
     def __init__(self, logN, q, p, dnum, device=0):
         self.logN, self.L, self.k, self.dnum = int(logN), len(q), len(p), int(dnum)
         self.N = 1 << self.logN
-        self._compressed = set()  # data pointers registered as compressed keys
+        # registered compressed keys by data pointer; holding the tensor keeps its
+        # memory from being reused by another key while the library treats that
+        # address as compressed
+        self._compressed = {}
         self._ws_bytes = {}  # (op, level, r) -> ckks_workspace_bytes
         self.q, self.p = [int(x) for x in q], [int(x) for x in p]
         self.device = torch.device("cuda", device)
@@ -575,15 +578,16 @@ class Context:
         return key_b
 
     def register_compressed_key(self, key_b, seed):
-        """Every call of this context that receives key_b treats it as a compressed key."""
+        """Every call of this context that receives key_b treats it as a compressed key.
+        The context keeps key_b referenced until unregister_compressed_key."""
         self._arg(key_b, "key_b", self._key_words(1))
         _check(lib().ckks_key_register_seed(self._h, _p(key_b), int(seed) & 0xFFFFFFFFFFFFFFFF))
-        self._compressed.add(key_b.data_ptr())
+        self._compressed[key_b.data_ptr()] = key_b
 
     def unregister_compressed_key(self, key_b):
         self._arg(key_b, "key_b", 0)
         _check(lib().ckks_key_unregister(self._h, _p(key_b)))
-        self._compressed.discard(key_b.data_ptr())
+        self._compressed.pop(key_b.data_ptr(), None)
 
     def ksk_expand(self, key_b, seed, key=None, stream=None):
         self._arg(key_b, "key_b", self._key_words(1))

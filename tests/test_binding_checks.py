@@ -48,7 +48,7 @@ class HostContext(ckks.Context):
         self.q, self.p = list(range(L)), list(range(L, L + K))
         self.device = torch.device("cpu")
         self._h = ctypes.c_void_p(1)
-        self._compressed = set()
+        self._compressed = {}
         self._ws_bytes = {}
 
     def close(self):
@@ -118,8 +118,10 @@ def test_well_formed_arguments_reach_the_library(env):
     kb = ctx.keygen_ksk_seeded(s, e, 3, 5, stream=S)
     ctx.ksk_expand(kb, 3, stream=S)
     ctx.register_compressed_key(kb, 3)
+    assert ctx._compressed[kb.data_ptr()] is kb  # held while registered
     ctx.keyswitch(poly(L), L, kb, stream=S)  # a registered compressed key: rows b_j only
     ctx.unregister_compressed_key(kb)
+    assert kb.data_ptr() not in ctx._compressed
     for name in ("ckks_ntt", "ckks_intt", "ckks_automorph", "ckks_modup", "ckks_ksk_inner_prod", "ckks_moddown",
                  "ckks_moddown_noalloc", "ckks_pmodup", "ckks_rescale", "ckks_keyswitch", "ckks_rotate",
                  "ckks_hrotate", "ckks_keyswitch_batch", "ckks_keyswitch_batch_seeded", "ckks_hrotate_batch",
