@@ -374,8 +374,9 @@ int ckks_bconv_select(ckks_ctx *ctx, int tensor_cores, int *available);
  * arrival time on the server's clock, ckks_server_now_ms; a negative
  * arrival_ms means "at submission").  Nothing blocks; the caller calls step
  * and poll in a loop.  Single-threaded: one thread at a time per server.
- * ckks_server_create allocates the arena (mem_budget bytes) and is the only
- * call of this library besides ckks_ctx_create that allocates device memory.
+ * ckks_server_create allocates the arena (mem_budget bytes), one status word
+ * per stream and its pinned host copy; it is the only call of this library
+ * besides ckks_ctx_create that allocates device memory.
  * Errors: CKKS_EINVAL for bad arguments, CKKS_ENOMEM when a key or a request
  * can never fit the budget; after CKKS_ECUDA the server must be destroyed.
  * ------------------------------------------------------------------------ */
@@ -407,9 +408,21 @@ int ckks_server_add_key_seeded(ckks_server *srv, int ctx, const uint64_t *d_key_
 double ckks_server_now_ms(const ckks_server *srv);
 int ckks_server_submit(ckks_server *srv, const ckks_request *req, uint64_t *id);
 int ckks_server_step(ckks_server *srv, int *n_launched);
-/* Up to max finished requests: ids[i], latency_ms[i] and done_ms[i] (device
- * completion time on the server's clock; either array may be NULL); *n = count. */
-int ckks_server_poll(ckks_server *srv, int max, uint64_t *ids, double *latency_ms, double *done_ms, int *n);
+/* Up to max finished requests: ids[i], latency_ms[i], done_ms[i] (device
+ * completion time on the server's clock) and status[i]; any of the last three
+ * arrays may be NULL; *n = count.  status[i] is CKKS_OK, or CKKS_ETIMEOUT when
+ * a bounded device-side wait (see ckks_poll_status) ran out in the batch that
+ * carried the request: its outputs are then not valid and it should be
+ * resubmitted.  Each stream of the server has its own status word, so such a
+ * failure is charged only to the requests of the batch that had it. */
+int ckks_server_poll(ckks_server *srv, int max, uint64_t *ids, double *latency_ms, double *done_ms, int *status,
+                     int *n);
+/* Test hook (no counterpart in the paper): the next batch the server launches
+ * first runs the bounded-wait self-test (ckks_selftest_bounded_wait, limit_us
+ * 1 .. 2000000, else CKKS_EINVAL) on its stream, recording into that stream's
+ * status word, so that every request of that batch is reported with
+ * CKKS_ETIMEOUT.  Nothing faults; later batches run normally. */
+int ckks_server_selftest_timeout(ckks_server *srv, uint32_t limit_us);
 int ckks_server_stats(const ckks_server *srv, ckks_server_stats_t *stats);
 
 /* Asynchronous errors: every call returns after enqueueing its kernels, so a

@@ -122,7 +122,8 @@ _SIGS = {
     "ckks_server_submit": (_i, [_vp, ctypes.POINTER(_Request), ctypes.POINTER(ctypes.c_uint64)]),
     "ckks_server_step": (_i, [_vp, ctypes.POINTER(_i)]),
     "ckks_server_poll": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double),
-                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i)]),
+                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "ckks_server_selftest_timeout": (_i, [_vp, ctypes.c_uint32]),
     "ckks_server_stats": (_i, [_vp, ctypes.POINTER(_Stats)]),
     "ckks_profile_enable": (_i, [_vp, _i]),
     "ckks_profile_reset": (_i, [_vp]),
@@ -798,17 +799,35 @@ class Server:
         _check(lib().ckks_server_step(self._h, ctypes.byref(n)))
         return n.value
 
-    def poll(self, max_n=4096):
+    def poll(self, max_n=4096, with_status=False):
+        """Finished requests as (id, latency_ms, done_ms), or (id, latency_ms,
+        done_ms, status) with with_status; status is CKKS_OK, or CKKS_ETIMEOUT
+        when the request's outputs are not valid.  Without with_status a failed
+        request raises CkksError."""
         ids = (ctypes.c_uint64 * max_n)()
         lat = (ctypes.c_double * max_n)()
         done = (ctypes.c_double * max_n)()
+        sts = (ctypes.c_int * max_n)()
         n = _i()
-        _check(lib().ckks_server_poll(self._h, max_n, ids, lat, done, ctypes.byref(n)))
+        _check(lib().ckks_server_poll(self._h, max_n, ids, lat, done, sts, ctypes.byref(n)))
         out = []
+        failed = []
         for i in range(n.value):
             self._live.pop(ids[i], None)
-            out.append((int(ids[i]), float(lat[i]), float(done[i])))
+            if with_status:
+                out.append((int(ids[i]), float(lat[i]), float(done[i]), int(sts[i])))
+            else:
+                out.append((int(ids[i]), float(lat[i]), float(done[i])))
+                if sts[i] != CKKS_OK:
+                    failed.append(int(ids[i]))
+        if failed:
+            raise CkksError(f"served requests {failed} failed: a bounded device wait ran out", CKKS_ETIMEOUT)
         return out
+
+    def selftest_timeout(self, limit_us=20000):
+        """Arm the test hook: the next batch runs the bounded-wait self-test first,
+        so its requests come back with CKKS_ETIMEOUT."""
+        _check(lib().ckks_server_selftest_timeout(self._h, int(limit_us)))
 
     def stats(self):
         st = _Stats()

@@ -402,8 +402,9 @@ extern "C" int ckks_ctx_create(const ckks_params *prm, int device, ckks_ctx **ou
     if (err == cudaSuccess) err = cudaMalloc(&c->d_block, off);
     if (err != cudaSuccess) {
         cudaGetLastError();  // not sticky: leave no error behind for the caller
-        cudaSetDevice(prev);
+        const cudaError_t back = cudaSetDevice(prev);
         delete c;
+        if (back != cudaSuccess) return CKKS_ECUDA;  // the caller's device could not be restored
         return err == cudaErrorMemoryAllocation ? CKKS_ENOMEM : CKKS_ECUDA;
     }
     char *base = static_cast<char *>(c->d_block);
@@ -446,7 +447,9 @@ extern "C" int ckks_ctx_create(const ckks_params *prm, int device, ckks_ctx **ou
         if (err == cudaSuccess && u.n) err = cudaMemcpy(u.dst, u.src, u.n, cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemset(c->d_status, 0, sizeof(int));
     if (err == cudaSuccess) err = ntt_set_attributes(c);
-    cudaSetDevice(prev);
+    // the caller's current device is restored; a failure to do so fails the call
+    const cudaError_t back = cudaSetDevice(prev);
+    if (err == cudaSuccess) err = back;
     if (err != cudaSuccess) {
         cudaFree(c->d_block);
         delete c;
@@ -459,18 +462,19 @@ extern "C" int ckks_ctx_create(const ckks_params *prm, int device, ckks_ctx **ou
 extern "C" int ckks_ctx_destroy(ckks_ctx *c) {
     if (c == nullptr) return CKKS_EINVAL;
     int prev = 0;
-    cudaGetDevice(&prev);
-    cudaSetDevice(c->device);
+    cudaError_t err = cudaGetDevice(&prev);
+    if (err == cudaSuccess) err = cudaSetDevice(c->device);
     for (auto &r : c->prof_pending) {
         cudaEventSynchronize(r.b);
         c->prof_pool.push_back(r.a);
         c->prof_pool.push_back(r.b);
     }
     for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
-    cudaFree(c->d_block);
-    cudaSetDevice(prev);
+    cudaFree(c->d_block);  // a device pointer is freed whichever device is current
+    const cudaError_t back = cudaSetDevice(prev);
+    if (err == cudaSuccess) err = back;
     delete c;
-    return CKKS_OK;
+    return err == cudaSuccess ? CKKS_OK : CKKS_ECUDA;
 }
 
 extern "C" int ckks_last_cuda_error(const ckks_ctx *c) { return c ? c->last_cuda_error : 0; }
@@ -1077,23 +1081,24 @@ static int entry_one(ckks_ctx *ctx, const CtDesc &c, const TensorEntry *te, cuda
 
 // The steps of a batch up to the inner product: tensor step of the Mult
 // entries, iNTT of the inputs, ModUp conversion, NTT of the new limbs, KSKInnerProd.
-static int batch_front(ckks_ctx *ctx, const KsBatchDesc &d, const TensorBatch &T, cudaStream_t st) {
+static int batch_front(ckks_ctx *ctx, const KsBatchDesc &d, const TensorBatch &T, cudaStream_t st,
+                       int *status = nullptr) {
     CK(launch_tensor(ctx, T, st));
     CK(launch_ntt_batch(ctx, d, PH_INTT_A, st));
-    CK(launch_bconv_batch(ctx, d, GM_MODUP, st));
+    CK(launch_bconv_batch(ctx, d, GM_MODUP, st, status));
     CK(launch_ntt_batch(ctx, d, PH_NTT_UP, st));
     CK(launch_inner_prod_batch(ctx, d, st));
     return CKKS_OK;
 }
 
 // The ModDown steps (and the Rescale of Mult entries).
-static int batch_back(ckks_ctx *ctx, const KsBatchDesc &d, bool rescale, cudaStream_t st) {
+static int batch_back(ckks_ctx *ctx, const KsBatchDesc &d, bool rescale, cudaStream_t st, int *status = nullptr) {
     CK(launch_ntt_batch(ctx, d, PH_INTT_P, st));
-    CK(launch_bconv_batch(ctx, d, GM_MODDOWN, st));
+    CK(launch_bconv_batch(ctx, d, GM_MODDOWN, st, status));
     CK(launch_ntt_batch(ctx, d, PH_NTT_DOWN, st));
     if (rescale) {
         CK(launch_ntt_batch(ctx, d, PH_RS_INTT, st));
-        CK(launch_bconv_batch(ctx, d, GM_RESCALE, st));
+        CK(launch_bconv_batch(ctx, d, GM_RESCALE, st, status));
         CK(launch_ntt_batch(ctx, d, PH_RS_NTT, st));
     }
     return CKKS_OK;
@@ -1101,7 +1106,7 @@ static int batch_back(ckks_ctx *ctx, const KsBatchDesc &d, bool rescale, cudaStr
 
 // Runs a batch in groups of kMaxCts entries.  An entry's workspace is its ws
 // when set, else the next entry_ws_words region of w (batch order).
-int ckks::run_batch(ckks_ctx *ctx, int n, const BatchEntry *e, u64 *w, cudaStream_t st) {
+int ckks::run_batch(ckks_ctx *ctx, int n, const BatchEntry *e, u64 *w, cudaStream_t st, int *status) {
     for (int c0 = 0; c0 < n; c0 += kMaxCts) {
         KsBatchDesc d{};
         d.n = std::min(n - c0, kMaxCts);
@@ -1130,8 +1135,8 @@ int ckks::run_batch(ckks_ctx *ctx, int n, const BatchEntry *e, u64 *w, cudaStrea
             continue;
         }
         // one launch per step over the whole batch
-        RC(batch_front(ctx, d, T, st));
-        RC(batch_back(ctx, d, T.n > 0, st));
+        RC(batch_front(ctx, d, T, st, status));
+        RC(batch_back(ctx, d, T.n > 0, st, status));
     }
     return CKKS_OK;
 }
@@ -1622,7 +1627,10 @@ static cudaError_t noalloc_scratch(int device, uint64_t **out) {
         if (prev != device && (err = cudaSetDevice(device)) != cudaSuccess) return err;
         void *p = nullptr;
         err = cudaGetSymbolAddress(&p, g_moddown_scratch);
-        if (prev != device) cudaSetDevice(prev);
+        if (prev != device) {
+            const cudaError_t back = cudaSetDevice(prev);
+            if (err == cudaSuccess) err = back;
+        }
         if (err != cudaSuccess) return err;
         g_noalloc_ptr[device] = static_cast<uint64_t *>(p);
     }

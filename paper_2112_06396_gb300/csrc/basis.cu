@@ -425,7 +425,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 }
 
 template <int KG, class GMAP>
-static void launch_tc_kg(const ckks_ctx *ctx, const GMAP &gm, int ngroups, int chunks, int chunk, cudaStream_t st) {
+static void launch_tc_kg(const ckks_ctx *ctx, const GMAP &gm, int ngroups, int chunks, int chunk, cudaStream_t st,
+                         int *status) {
     // 512 tensor-memory columns: one CTA of this kernel per SM (the shared
     // memory is sized so that a second cannot be placed beside it and wait in
     // tcgen05.alloc; CTAs of other kernels still fit); as many CTAs per
@@ -440,27 +441,27 @@ static void launch_tc_kg(const ckks_ctx *ctx, const GMAP &gm, int ngroups, int c
     const int rows = ngroups * chunks;
     const int per = std::max(1, std::min(tiles, ctx->sms / rows));
     const dim3 grid(static_cast<unsigned>(per), static_cast<unsigned>(rows));
-    kern<<<grid, kTcThreads, smem, st>>>(gm, chunks, chunk, ctx->d_pinfo, ctx->logN, ctx->tc_lazy ? 1 : 0,
-                                         ctx->d_status);
+    kern<<<grid, kTcThreads, smem, st>>>(gm, chunks, chunk, ctx->d_pinfo, ctx->logN, ctx->tc_lazy ? 1 : 0, status);
 }
 
 // Tensor-core conversion over `ngroups` groups of up to n_all targets each,
 // in chunks of at most 32 targets (256 tensor-memory columns), each a
-// multiple of four targets.
+// multiple of four targets.  A wait that runs out is recorded in *status.
 template <class GMAP>
-static cudaError_t launch_tc(const ckks_ctx *ctx, const GMAP &gm, int ngroups, int n_all, cudaStream_t st) {
+static cudaError_t launch_tc(const ckks_ctx *ctx, const GMAP &gm, int ngroups, int n_all, cudaStream_t st,
+                             int *status) {
     const int chunks = (n_all + 31) / 32;
     const int chunk = ((n_all + chunks - 1) / chunks + 3) & ~3;
     ProfScope ps(ctx, K_BCONV, double(ngroups) * n_all, st);
     switch (ctx->tc_kg) {
-    case 4: launch_tc_kg<4>(ctx, gm, ngroups, chunks, chunk, st); break;
-    case 6: launch_tc_kg<6>(ctx, gm, ngroups, chunks, chunk, st); break;
-    case 8: launch_tc_kg<8>(ctx, gm, ngroups, chunks, chunk, st); break;
-    case 10: launch_tc_kg<10>(ctx, gm, ngroups, chunks, chunk, st); break;
-    case 12: launch_tc_kg<12>(ctx, gm, ngroups, chunks, chunk, st); break;
-    case 14: launch_tc_kg<14>(ctx, gm, ngroups, chunks, chunk, st); break;
-    case 16: launch_tc_kg<16>(ctx, gm, ngroups, chunks, chunk, st); break;
-    case 18: launch_tc_kg<18>(ctx, gm, ngroups, chunks, chunk, st); break;
+    case 4: launch_tc_kg<4>(ctx, gm, ngroups, chunks, chunk, st, status); break;
+    case 6: launch_tc_kg<6>(ctx, gm, ngroups, chunks, chunk, st, status); break;
+    case 8: launch_tc_kg<8>(ctx, gm, ngroups, chunks, chunk, st, status); break;
+    case 10: launch_tc_kg<10>(ctx, gm, ngroups, chunks, chunk, st, status); break;
+    case 12: launch_tc_kg<12>(ctx, gm, ngroups, chunks, chunk, st, status); break;
+    case 14: launch_tc_kg<14>(ctx, gm, ngroups, chunks, chunk, st, status); break;
+    case 16: launch_tc_kg<16>(ctx, gm, ngroups, chunks, chunk, st, status); break;
+    case 18: launch_tc_kg<18>(ctx, gm, ngroups, chunks, chunk, st, status); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -471,8 +472,8 @@ static cudaError_t launch_tc(const ckks_ctx *ctx, const GMAP &gm, int ngroups, i
 // source word is still scaled once per 12 targets).
 template <class GMAP>
 static cudaError_t launch_split(const ckks_ctx *ctx, const GMAP &gm, int ngroups, int n_all, int max_src,
-                                cudaStream_t st) {
-    if (ctx->tc_kg && ctx->tc_on) return launch_tc(ctx, gm, ngroups, n_all, st);
+                                cudaStream_t st, int *status) {
+    if (ctx->tc_kg && ctx->tc_on) return launch_tc(ctx, gm, ngroups, n_all, st, status);
     const int chunks = (n_all + 11) / 12;
     const int chunk = (n_all + chunks - 1) / chunks;
     const int tpb = 128;
@@ -511,15 +512,16 @@ __global__ void bounded_wait_selftest_kernel(uint64_t limit_ns, int *__restrict_
     if (!tc::mbar_wait(&never, 0, limit_ns) && threadIdx.x == 0) atomicOr(status, 1);
 }
 
-cudaError_t launch_bounded_wait_selftest(const ckks_ctx *ctx, uint64_t limit_ns, cudaStream_t st) {
-    bounded_wait_selftest_kernel<<<1, 32, 0, st>>>(limit_ns, ctx->d_status);
+cudaError_t launch_bounded_wait_selftest(const ckks_ctx *ctx, uint64_t limit_ns, cudaStream_t st, int *status) {
+    bounded_wait_selftest_kernel<<<1, 32, 0, st>>>(limit_ns, status != nullptr ? status : ctx->d_status);
     return cudaGetLastError();
 }
 
 // The basis conversions of one batched phase: ModUp digits (GM_MODUP), the
 // ModDown of both polynomials (GM_MODDOWN) or the Rescale of both polynomials
-// of the Mult entries (GM_RESCALE).  Needs the split conversion.
-cudaError_t launch_bconv_batch(const ckks_ctx *ctx, const KsBatchDesc &d, int down, cudaStream_t st) {
+// of the Mult entries (GM_RESCALE).  Needs the split conversion.  A bounded
+// wait that runs out is recorded in *status (the context's word when null).
+cudaError_t launch_bconv_batch(const ckks_ctx *ctx, const KsBatchDesc &d, int down, cudaStream_t st, int *status) {
     GroupMapBatch gm;
     gm.d = d;
     gm.down = down;
@@ -547,7 +549,7 @@ cudaError_t launch_bconv_batch(const ckks_ctx *ctx, const KsBatchDesc &d, int do
     }
     gm.d.pre[d.n] = groups;
     if (groups == 0 || n_all == 0) return cudaSuccess;
-    return launch_split(ctx, gm, groups, n_all, max_src, st);
+    return launch_split(ctx, gm, groups, n_all, max_src, st, status != nullptr ? status : ctx->d_status);
 }
 
 cudaError_t launch_bconv(const ckks_ctx *ctx, const BConvLaunch &l, int max_src, cudaStream_t st) {
@@ -556,7 +558,7 @@ cudaError_t launch_bconv(const ckks_ctx *ctx, const BConvLaunch &l, int max_src,
     if (ctx->split_bits && max_src <= kMaxSrc) {
         GroupMapList gm;
         gm.l = l;
-        return launch_split(ctx, gm, l.ngroups, l.chunk * l.chunks, max_src, st);
+        return launch_split(ctx, gm, l.ngroups, l.chunk * l.chunks, max_src, st, ctx->d_status);
     }
     dim3 grid(unsigned((ctx->N / 2 + threads - 1) / threads), unsigned(l.ngroups * l.chunks));
     ProfScope ps(ctx, K_BCONV, double(l.ngroups) * l.chunk, st);

@@ -97,14 +97,16 @@ inline int ext_prime(const ckks_ctx *c, int ell, int pos) { return pos < ell ? p
 inline int beta_of(const ckks_ctx *c, int ell) { return (ell + c->alpha - 1) / c->alpha; }
 
 cudaError_t ntt_set_attributes(const ckks_ctx *ctx);
-cudaError_t launch_bounded_wait_selftest(const ckks_ctx *ctx, uint64_t limit_ns, cudaStream_t st);
+cudaError_t launch_bounded_wait_selftest(const ckks_ctx *ctx, uint64_t limit_ns, cudaStream_t st,
+                                         int *status = nullptr);
 cudaError_t launch_ntt_fwd(const ckks_ctx *ctx, const NttBatch &b, const Epi *epi, cudaStream_t st);
 cudaError_t launch_ntt_inv(const ckks_ctx *ctx, const NttBatch &b, cudaStream_t st);
 cudaError_t launch_ntt_batch(const ckks_ctx *ctx, const KsBatchDesc &d, int phase, cudaStream_t st);
 constexpr int kTuneSmallBatch = 48;
 cudaError_t ntt_autotune(ckks_ctx *ctx, u64 *scratch, int small, int large, cudaStream_t st, float *times_out);
 cudaError_t launch_bconv(const ckks_ctx *ctx, const BConvLaunch &l, int max_src, cudaStream_t st);
-cudaError_t launch_bconv_batch(const ckks_ctx *ctx, const KsBatchDesc &d, int down, cudaStream_t st);
+cudaError_t launch_bconv_batch(const ckks_ctx *ctx, const KsBatchDesc &d, int down, cudaStream_t st,
+                               int *status = nullptr);
 
 // keyswitch.cu
 struct InnerArgs {
@@ -140,7 +142,8 @@ struct BatchEntry {
     u64 seed;
 };
 size_t entry_ws_words(const ckks_ctx *c, int kind, int ell);
-int run_batch(ckks_ctx *ctx, int n, const BatchEntry *e, u64 *w, cudaStream_t st);
+// status: the word a bounded device wait that runs out sets (the context's when null)
+int run_batch(ckks_ctx *ctx, int n, const BatchEntry *e, u64 *w, cudaStream_t st, int *status = nullptr);
 
 struct PmvArgs {
     const u64 *ext;      // hoisted ModUp outputs [beta][ell+k][N]

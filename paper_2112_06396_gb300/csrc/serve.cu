@@ -11,6 +11,15 @@
 // one clock: at creation the server synchronises the device, records an origin
 // event and reads the host clock, so event times and host times share t = 0.
 // The admission and batching policy lives in serve_policy.h.
+//
+// Device-side failures of a batch: each lane (stream) has its own status word,
+// cleared before the lane's batch and handed to every kernel of the batch that
+// has a bounded wait (the tensor-core basis conversion); after the batch its
+// value is copied to pinned host memory on the lane, before the lane's
+// completion event.  When the event has completed the host reads the copy, and
+// a set word marks every request of that batch as failed (CKKS_ETIMEOUT): its
+// outputs are not valid.  Lanes never share a word, so a timeout is charged to
+// the batch that had it.
 #include "../../include/ckks_ks.h"
 #include "internal.h"
 #include "serve_policy.h"
@@ -26,6 +35,7 @@ namespace {
 struct Done {
     uint64_t id;
     double arrival_ms, done_ms;
+    int status;  // CKKS_OK, or CKKS_ETIMEOUT when a bounded wait of its batch ran out
 };
 }  // namespace
 
@@ -47,6 +57,9 @@ struct ckks_server {
     std::unordered_map<uint64_t, ckks_request> reqs;
     std::deque<Done> finished;
     cudaEvent_t origin = nullptr;
+    int *d_status = nullptr;  // [nstreams] device status words, one per lane
+    int *h_status = nullptr;  // [nstreams] pinned host copies, valid once the lane's event completed
+    uint32_t inject_wait_us = 0;  // test hook: the next batch also runs the bounded-wait self-test
     std::chrono::steady_clock::time_point t0;
     uint64_t next_id = 1;
     int last_cuda_error = 0;
@@ -75,6 +88,8 @@ static void destroy(ckks_server *s) {
         if (ev) cudaEventDestroy(ev);
     if (s->origin) cudaEventDestroy(s->origin);
     if (s->arena) cudaFree(s->arena);
+    if (s->d_status) cudaFree(s->d_status);
+    if (s->h_status) cudaFreeHost(s->h_status);
     delete s->sched;
     delete s;
 }
@@ -102,6 +117,12 @@ extern "C" int ckks_server_create(ckks_ctx *const *ctxs, int nctx, size_t mem_bu
     // the workspace arena: one allocation, made here and nowhere else
     const size_t arena = mem_budget / Arena::kAlign * Arena::kAlign;
     if ((e = cudaMalloc(&s->arena, arena)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&s->d_status, size_t(nstreams) * sizeof(int))) != cudaSuccess) return fail(e);
+    if ((e = cudaMemset(s->d_status, 0, size_t(nstreams) * sizeof(int))) != cudaSuccess) return fail(e);
+    if ((e = cudaHostAlloc(reinterpret_cast<void **>(&s->h_status), size_t(nstreams) * sizeof(int),
+                           cudaHostAllocDefault)) != cudaSuccess)
+        return fail(e);
+    for (int i = 0; i < nstreams; ++i) s->h_status[i] = 0;
     s->sched = new Scheduler(mem_budget, arena, max_batch, nstreams);
     s->streams.assign(size_t(nstreams), nullptr);
     s->done.assign(size_t(nstreams), nullptr);
@@ -115,7 +136,7 @@ extern "C" int ckks_server_create(ckks_ctx *const *ctxs, int nctx, size_t mem_bu
     if ((e = cudaEventRecord(s->origin, s->streams[0])) != cudaSuccess) return fail(e);
     if ((e = cudaEventSynchronize(s->origin)) != cudaSuccess) return fail(e);
     s->t0 = std::chrono::steady_clock::now();
-    cudaSetDevice(prev);
+    if ((e = cudaSetDevice(prev)) != cudaSuccess) return fail(e);
     *out = s;
     return CKKS_OK;
 }
@@ -220,9 +241,11 @@ extern "C" int ckks_server_step(ckks_server *s, int *n_launched) {
         }
         float ms = 0.f;
         cudaEventElapsedTime(&ms, s->origin, s->done[lane]);
+        const int status = s->h_status[lane] != 0 ? CKKS_ETIMEOUT : CKKS_OK;
+        s->h_status[lane] = 0;
         for (const auto &a : batch) {
             auto it = s->reqs.find(a.r.id);
-            s->finished.push_back({a.r.id, it->second.arrival_ms, double(ms)});
+            s->finished.push_back({a.r.id, it->second.arrival_ms, double(ms), status});
             s->reqs.erase(it);
         }
         s->sched->complete(int(lane), batch);
@@ -255,11 +278,22 @@ extern "C" int ckks_server_step(ckks_server *s, int *n_launched) {
             ent.push_back(be);
         }
         cudaStream_t st = s->streams[size_t(lane)];
-        rc = run_batch(c, int(ent.size()), ent.data(), nullptr, st);
-        if (rc != CKKS_OK) {
-            s->last_cuda_error = c->last_cuda_error;
+        int *lane_status = s->d_status + lane;
+        cudaError_t e = cudaMemsetAsync(lane_status, 0, sizeof(int), st);
+        if (e == cudaSuccess && s->inject_wait_us != 0) {
+            e = launch_bounded_wait_selftest(c, uint64_t(s->inject_wait_us) * 1000u, st, lane_status);
+            s->inject_wait_us = 0;
+        }
+        if (e != cudaSuccess) {
+            s->last_cuda_error = int(e);
+            rc = CKKS_ECUDA;
         } else {
-            const cudaError_t e = cudaEventRecord(s->done[size_t(lane)], st);
+            rc = run_batch(c, int(ent.size()), ent.data(), nullptr, st, lane_status);
+            if (rc != CKKS_OK) s->last_cuda_error = c->last_cuda_error;
+        }
+        if (rc == CKKS_OK) {
+            e = cudaMemcpyAsync(s->h_status + lane, lane_status, sizeof(int), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaEventRecord(s->done[size_t(lane)], st);
             if (e != cudaSuccess) {
                 s->last_cuda_error = int(e);
                 rc = CKKS_ECUDA;
@@ -270,12 +304,19 @@ extern "C" int ckks_server_step(ckks_server *s, int *n_launched) {
         launched += int(adm.size());
     }
     s->launched += launched;
-    if (prev != s->device) cudaSetDevice(prev);
+    if (prev != s->device) {
+        const cudaError_t e = cudaSetDevice(prev);
+        if (e != cudaSuccess && rc == CKKS_OK) {
+            s->last_cuda_error = int(e);
+            rc = CKKS_ECUDA;
+        }
+    }
     if (n_launched) *n_launched = launched;
     return rc;
 }
 
-extern "C" int ckks_server_poll(ckks_server *s, int max, uint64_t *ids, double *latency_ms, double *done_ms, int *n) {
+extern "C" int ckks_server_poll(ckks_server *s, int max, uint64_t *ids, double *latency_ms, double *done_ms,
+                                int *status, int *n) {
     if (s == nullptr || n == nullptr || max < 0 || (max > 0 && ids == nullptr)) return CKKS_EINVAL;
     int k = 0;
     while (k < max && !s->finished.empty()) {
@@ -284,9 +325,16 @@ extern "C" int ckks_server_poll(ckks_server *s, int max, uint64_t *ids, double *
         ids[k] = d.id;
         if (latency_ms) latency_ms[k] = d.done_ms - d.arrival_ms;
         if (done_ms) done_ms[k] = d.done_ms;
+        if (status) status[k] = d.status;
         ++k;
     }
     *n = k;
+    return CKKS_OK;
+}
+
+extern "C" int ckks_server_selftest_timeout(ckks_server *s, uint32_t limit_us) {
+    if (s == nullptr || limit_us == 0 || limit_us > 2000000u) return CKKS_EINVAL;
+    s->inject_wait_us = limit_us;
     return CKKS_OK;
 }
 

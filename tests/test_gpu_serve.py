@@ -1,8 +1,10 @@
 """The serving loop through the C ABI: requests of two ring degrees, mixed
 operations (HRotate, KeySwitch, Mult + relinearisation + Rescale, NewMult) and mixed
-levels arrive while others run; every result must carry the bits of the same
-request run alone (tolerance 0, exact modular arithmetic), whatever batch it
-landed in and whatever ran beside it."""
+levels arrive while others run; every result must carry the bits of the oracle's
+result for that request (HRotate = Algorithm 4, Mult = Algorithm 2, NewMult =
+Algorithm 7, KeySwitch = Algorithms 2-4's key switch) and of the same request run
+alone through the single-ciphertext calls (tolerance 0, exact modular arithmetic),
+whatever batch it landed in and whatever ran beside it."""
 import numpy as np
 import pytest
 
@@ -14,20 +16,24 @@ pytestmark = pytest.mark.gpu
 
 
 class Pool:
-    """Two contexts (N = 2^11 and 2^12, L = 6, k = 2, dnum = 3), a relinearisation
-    key and two rotation keys each."""
+    """Contexts (by default N = 2^11 and 2^12, L = 6, k = 2, dnum = 3), a
+    relinearisation key and two rotation keys each, generated by the oracle."""
 
-    def __init__(self, oracle_lib):
-        self.S = [Setup(oracle_lib, 11, 6, 2, 3, 50), Setup(oracle_lib, 12, 6, 2, 3, 50)]
+    def __init__(self, oracle_lib, shapes=((11, 6, 2, 3, 50), (12, 6, 2, 3, 50)), tag="gpu/serve"):
+        self.S = [Setup(oracle_lib, *sh) for sh in shapes]
+        self.o = oracle_lib
         self.gs = [5, 25]
         self.keys = []
+        self.okeys = []
         for c, S in enumerate(self.S):
-            self.keys.append({g: dev(S.key(g, f"gpu/serve/{c}/key{g}")[0]) for g in [0] + self.gs})
+            ok = {g: S.key(g, f"{tag}/{c}/key{g}")[0] for g in [0] + self.gs}
+            self.okeys.append(ok)
+            self.keys.append({g: dev(k) for g, k in ok.items()})
 
-    def requests(self, n, tag, gap_ms=0.02):
+    def requests(self, n, tag, gap_ms=0.02, min_level=2):
         ops = synth.uniform_ints(n, 0, 3, f"{tag}/op")
-        ctxs = synth.uniform_ints(n, 0, 1, f"{tag}/ctx")
-        lv = synth.uniform_ints(n, 2, 6, f"{tag}/level")
+        ctxs = synth.uniform_ints(n, 0, len(self.S) - 1, f"{tag}/ctx")
+        lv = synth.uniform_ints(n, min_level, min(S.P.L for S in self.S), f"{tag}/level")
         gaps = synth.exponential_gaps(n, gap_ms, f"{tag}/gaps")
         t = np.cumsum(gaps)
         reqs = []
@@ -45,8 +51,25 @@ class Pool:
                          oa=S.ctx.empty(ell - 1), ob=S.ctx.empty(ell - 1))
             else:
                 r.update(op="keyswitch", galois=1, kkey=0, oa=S.ctx.empty(ell), ob=S.ctx.empty(ell))
+            r["host"] = (a, b) if ops[i] in (0, 2) else (a, b, a2, b2)
             reqs.append(r)
         return reqs
+
+    def oracle(self, r):
+        """The oracle's result for request r (host arrays)."""
+        S, o = self.S[r["ctx"]], self.o
+        key = self.okeys[r["ctx"]][r["kkey"]]
+        ell = r["level"]
+        if r["op"] == "hrotate":
+            a, b = r["host"]
+            ((oa, ob),) = o.hrotate(S.P, ell, a, b, [r["galois"]], [key])
+        elif r["op"] == "mult":
+            oa, ob = o.mult(S.P, ell, *r["host"], key)
+        elif r["op"] == "newmult":
+            oa, ob = o.newmult(S.P, ell, *r["host"], key)
+        else:
+            oa, ob = o.keyswitch(S.P, ell, r["host"][0], key)
+        return oa, ob
 
     def alone(self, r):
         ctx = self.S[r["ctx"]].ctx
@@ -90,9 +113,14 @@ def test_results_same_alone_and_in_the_mix(pool, max_batch, streams):
         assert st["batches"] < len(reqs)  # requests really were batched
     for i, r in enumerate(reqs):
         ga, gb = host(r["oa"]), host(r["ob"])
+        what = f"request {i} ({r['op']}, ctx {r['ctx']}, ell {r['level']})"
+        oa, ob = pool.oracle(r)
+        np.testing.assert_array_equal(ga, oa, err_msg=f"{what} vs oracle")
+        np.testing.assert_array_equal(gb, ob, err_msg=f"{what} vs oracle")
         ra, rb = pool.alone(r)
-        np.testing.assert_array_equal(ga, ra, err_msg=f"request {i} ({r['op']}, ctx {r['ctx']}, ell {r['level']})")
-        np.testing.assert_array_equal(gb, rb, err_msg=f"request {i}")
+        np.testing.assert_array_equal(ga, ra, err_msg=f"{what} vs alone")
+        np.testing.assert_array_equal(gb, rb, err_msg=f"{what} vs alone")
+    assert {r["op"] for r in reqs} == {"hrotate", "mult", "newmult", "keyswitch"}
     assert stats["p99_ms"] >= stats["p50_ms"] > 0
     srv.close()
 
@@ -131,9 +159,96 @@ def test_memory_admission_limits_what_runs(pool):
     assert sorted(d[0] for d in done) == sorted(ids)
     assert seen_max > key_bytes
     for r in reqs:
+        oa, ob = pool.oracle(r)
+        np.testing.assert_array_equal(host(r["oa"]), oa)
+        np.testing.assert_array_equal(host(r["ob"]), ob)
         ra, rb = pool.alone(r)
         np.testing.assert_array_equal(host(r["oa"]), ra)
         np.testing.assert_array_equal(host(r["ob"]), rb)
+    srv.close()
+
+
+def test_serving_mix_ring_degree_n15_against_the_oracle(oracle_lib):
+    """A served mix at N = 2^15 with 54-bit primes and levels up to 12 (L = 12,
+    k = 4, dnum = 3) beside N = 2^12 requests: every request equals its single
+    call, and a sample of each operation (the largest level first) equals the
+    oracle."""
+    from paper_2112_06396_gb300 import serving
+
+    big = Pool(oracle_lib, shapes=((15, 12, 4, 3, 54), (12, 12, 4, 3, 54)), tag="gpu/serve15")
+    srv, handles = _server(big, 1 << 32, 16, 3)
+    reqs = big.requests(24, "gpu/serve15/mix", min_level=3)
+    for r in reqs:
+        r["key"] = handles[r["ctx"]][r["kkey"]]
+    results, stats = serving.replay(srv, reqs)
+    assert len(results) == len(reqs)
+    assert srv.stats()["batches"] < len(reqs)
+    checked = {}
+    for i in sorted(range(len(reqs)), key=lambda i: (reqs[i]["ctx"], -reqs[i]["level"])):
+        r = reqs[i]
+        ga, gb = host(r["oa"]), host(r["ob"])
+        ra, rb = big.alone(r)
+        np.testing.assert_array_equal(ga, ra, err_msg=f"request {i} vs alone")
+        np.testing.assert_array_equal(gb, rb, err_msg=f"request {i} vs alone")
+        if r["ctx"] == 0 and checked.get(r["op"], 0) < 1:
+            oa, ob = big.oracle(r)
+            np.testing.assert_array_equal(ga, oa, err_msg=f"request {i} ({r['op']}, ell {r['level']}) vs oracle")
+            np.testing.assert_array_equal(gb, ob, err_msg=f"request {i} vs oracle")
+            checked[r["op"]] = checked.get(r["op"], 0) + 1
+    assert len(checked) >= 3, checked
+    srv.close()
+
+
+def test_timeout_in_a_served_batch_fails_only_that_batch(pool):
+    """The serving loop reads its lane's status word when a batch completes: the
+    test hook runs the bounded-wait self-test (an mbarrier nothing arrives on,
+    20 ms) in front of the next batch, and every request of that batch must come
+    back with CKKS_ETIMEOUT; the requests of the next batch must come back valid
+    and equal to the oracle.  Nothing faults."""
+    ckks = _gpu()
+    srv, handles = _server(pool, 1 << 30, 16, 2)
+    reqs = pool.requests(8, "gpu/serve/timeout", gap_ms=0.0)
+    for r in reqs:
+        r["key"] = handles[r["ctx"]][r["kkey"]]
+
+    def submit(rs):
+        ids = {}
+        for r in rs:
+            if r["op"] in ("mult", "newmult"):
+                rid = srv.submit_mult(r["ctx"], (r["a"], r["b"]), (r["a2"], r["b2"]), r["level"], r["key"], r["oa"],
+                                      r["ob"], new=r["op"] == "newmult")
+            elif r["op"] == "hrotate":
+                rid = srv.submit_hrotate(r["ctx"], r["a"], r["b"], r["level"], r["galois"], r["key"], r["oa"],
+                                         r["ob"])
+            else:
+                rid = srv.submit_keyswitch(r["ctx"], r["a"], r["level"], r["key"], r["oa"], r["ob"])
+            ids[rid] = r
+        return ids
+
+    def drain(n):
+        out = []
+        while len(out) < n:
+            srv.step()
+            out += srv.poll(with_status=True)
+        return out
+
+    first = reqs[0]
+    srv.selftest_timeout(20000)
+    ids = submit([first])
+    got = drain(1)
+    assert [(g[0], g[3]) for g in got] == [(next(iter(ids)), ckks.CKKS_ETIMEOUT)]
+    ids = submit(reqs)
+    got = drain(len(reqs))
+    assert sorted(g[0] for g in got) == sorted(ids)
+    assert all(g[3] == ckks.CKKS_OK for g in got)
+    for r in reqs:
+        oa, ob = pool.oracle(r)
+        np.testing.assert_array_equal(host(r["oa"]), oa)
+        np.testing.assert_array_equal(host(r["ob"]), ob)
+    # the contexts' own status words were not touched by the served timeout
+    torch.cuda.synchronize()
+    for S in pool.S:
+        assert S.ctx.poll_status() is True  # raises CkksError on CKKS_ETIMEOUT
     srv.close()
 
 

@@ -4,7 +4,8 @@ Some callers have no way to hand the library a workspace (they run inside a
 framework that owns all device memory, or must not allocate after start-up);
 this entry point keeps its scratch in a fixed array inside the library.  The
 test calls it through the C ABI twice in a row, with different inputs, and
-checks each result against the existing ckks_moddown entry point, bit for bit
+checks each result against the existing ckks_moddown entry point and against
+the oracle's ModDown (the division by P with rounding of Sec. 2.4), bit for bit
 (the tolerance of every parity test here is 0: the arithmetic is exact).
 It also checks that a request larger than the fixed array is refused.
 
@@ -38,17 +39,21 @@ def _noalloc(ckks, ctx, x, level, out):
 
 
 @pytest.mark.parametrize("logN,L,k,dnum,bits,level", [(16, 24, 8, 3, 54, 24), (12, 6, 3, 2, 50, 5)])
-def test_moddown_noalloc_matches_moddown_twice(logN, L, k, dnum, bits, level):
+def test_moddown_noalloc_matches_moddown_twice(oracle_lib, logN, L, k, dnum, bits, level):
     ckks = _ckks()
     ctx = ckks.Context.from_bits(logN, L, k, dnum, bits)
+    P = oracle_lib.Params(logN, L, k, dnum, primes=list(ctx.q) + list(ctx.p))
     ext = ctx.ext_primes(level)
     for call in range(2):
-        x = torch.from_numpy(synth.uniform_residues(ext, ctx.N, f"noalloc/{logN}/{call}")).cuda()
+        xh = synth.uniform_residues(ext, ctx.N, f"noalloc/{logN}/{call}")
+        x = torch.from_numpy(xh).cuda()
         want = ctx.moddown(x, level)
         got = torch.full((level, ctx.N), 7, dtype=torch.uint64, device="cuda")
         assert _noalloc(ckks, ctx, x, level, got) == ckks.CKKS_OK
         torch.cuda.synchronize()
-        assert np.array_equal(got.cpu().numpy(), want.cpu().numpy()), f"call {call}"
+        g = got.cpu().numpy()
+        assert np.array_equal(g, want.cpu().numpy()), f"call {call} vs ckks_moddown"
+        assert np.array_equal(g, oracle_lib.moddown(P, level, xh)), f"call {call} vs the oracle"
 
 
 def test_moddown_noalloc_rejects_oversize():
