@@ -445,6 +445,40 @@ def measure_rotation_sweep(ctx, items, lanes, torch, reps=10):
     return out
 
 
+def measure_fused(ctx, ckks, items, lanes, torch, reps=10):
+    """The fused key-switching dataflow (ckks_fuse_select: ModUp's last forward
+    pass, KSKInnerProd and ModDown's first inverse pass in one kernel) against
+    the default kernels: the headline step on the same streams, one HRotate
+    alone, and the single KeySwitch at N=2^12."""
+    one = Lanes(ctx, 1, torch, ckks)
+    it0 = items[0]
+    # on the current stream, the one _timed's events are recorded on
+    alone = lambda: ctx.hrotate(it0["a"], it0["b"], L, [it0["g"]], [it0["key"]], outs=[(it0["oa"], it0["ob"])],
+                                ws=one.ws[0])
+    out = {}
+    for on in (False, True):
+        ctx.fuse_modup(on)
+        ms_step = _timed(torch, lambda: step(ctx, items, lanes), reps)
+        ms_one = _timed(torch, alone, 20)
+        out["fused" if on else "default"] = {"ms_per_step": ms_step, "keyswitch_per_s": len(items) / ms_step * 1e3,
+                                              "hrotate_alone_us": ms_one * 1e3,
+                                              "launches_per_hrotate": 9 if on else 11}
+    ctx.fuse_modup(False)
+    small = ckks.Context.from_bits(12, 6, 3, 2, 50)
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(small.device)
+    s = dev(synth.ternary(small.N, "bench/small/s"))
+    key = _keygen(small, torch, s, 0, "bench/small/key")
+    a = dev(synth.uniform_residues(small.q, small.N, "bench/small/a"))
+    u, v = small.empty(6), small.empty(6)
+    ws = small.workspace(ckks.OP_KEYSWITCH, 6)
+    for on in (False, True):
+        small.fuse_modup(on)
+        ms = _timed(torch, lambda: small.keyswitch(a, 6, key, u, v, ws), 50)
+        out["fused" if on else "default"]["small_keyswitch_us"] = ms * 1e3
+    small.close()
+    return out
+
+
 def measure_other_rows(ctx, ckks, torch, reps=5):
     """Rescale (Alg. 1's ModDown_{B,1}) of one ciphertext, and a CoeffToSlot-shaped
     PtMatVecMult: fftIter = 3 levels at ell = 24, 23, 22 (Alg. 8 with 8 baby x 4
@@ -808,6 +842,15 @@ def run_gpu(args, rank, world, local_rank):
     launches_per_step = sum(v[1] for v in prof.values()) / prof_steps
     by_class = {k: {"ms_per_step": v[0] / prof_steps, "launches_per_step": v[1] / prof_steps} for k, v in prof.items()}
 
+    # ---- measured ceiling of the butterfly (register-only, every SM)
+    ctx.butterfly_peak(rounds=2000)  # warm-up
+    bps, bms, nbf = ctx.butterfly_peak(rounds=40000)
+    bfly_peak = {"gbfly_s": bps / 1e9, "ms": bms, "butterflies": nbf,
+                 "per_sm_per_clock_at_max": bps / (torch.cuda.get_device_properties(local_rank).multi_processor_count
+                                                   * load_peaks()["sm_max_mhz"] * 1e6),
+                 "kernel": "ckks_butterfly_peak: 16 words/thread in registers, 4 lazy CT stages per round, "
+                           "32 warps/SM"}
+
     # ---- end to end through the public API with host buffers
     pin_in = [(torch.empty((L, N), dtype=torch.uint64).pin_memory(), torch.empty((L, N), dtype=torch.uint64).pin_memory())
               for _ in range(C)]
@@ -906,6 +949,13 @@ def run_gpu(args, rank, world, local_rank):
         peak_gbfly = 152 * 64 * peaks["sm_max_mhz"] * 1e6 / 10 / 1e9
         tr = ncu_traffic_per_limb()
         hbm_achieved = bytes_per_launch / (avg_launch_ms * 1e-3) / 1e9
+        # The same kernel class in the timed (multi-stream) regime: its share of
+        # the kernel time times the measured step time, against the butterflies
+        # of one step.  This time per step is never above ms_per_step.
+        share = ntt_ms / sum(v[0] for v in prof.values())
+        ntt_ms_in_step = share * ms_per_step
+        bfly_per_step = limb_transforms / prof_steps * traffic.ntt_butterflies_per_limb(N)
+        achieved_in_step = bfly_per_step / (ntt_ms_in_step * 1e-3) / 1e9
         ks_bytes = traffic.compulsory_hrotate_bytes(N, L, K_SP, L, DNUM, 1)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -923,11 +973,21 @@ def run_gpu(args, rank, world, local_rank):
                     "frac_of_measured": ks_bytes * value / world / 1e9 / peaks["hbm_gbs"]},
             "roofline": {"kernel": "ntt (forward+inverse passes)", "bound": "alu", "achieved": achieved_gbfly,
                          "peak": peak_gbfly, "unit": "Gbutterfly/s", "frac": achieved_gbfly / peak_gbfly,
+                         "peak_how": "152 SMs x 64 IMAD/clk x sm_max_mhz / 10 IMAD per butterfly",
+                         "measured_peak": bfly_peak["gbfly_s"],
+                         "frac_of_measured_peak": achieved_gbfly / bfly_peak["gbfly_s"],
+                         "measured_peak_how": bfly_peak,
+                         "in_step": {"ntt_ms_per_step": ntt_ms_in_step, "ms_per_step": ms_per_step,
+                                     "butterflies_per_step": bfly_per_step, "achieved": achieved_in_step,
+                                     "frac": achieved_in_step / peak_gbfly,
+                                     "frac_of_measured_peak": achieved_in_step / bfly_peak["gbfly_s"],
+                                     "how": "share of kernel time (one-stream hook) x ms_per_step of the timed "
+                                            "multi-stream region"},
                          "traffic": None if tr is None else tr * limb_transforms / ntt_launch,
                          "algorithmic_bytes_per_launch": bytes_per_launch, "hbm_gbs_achieved": hbm_achieved,
                          "hbm_frac_of_measured": hbm_achieved / peaks["hbm_gbs"], "peak_src": peaks["src"],
                          "avg_launch_us": avg_launch_ms * 1e3,
-                         "share_of_kernel_time": ntt_ms / sum(v[0] for v in prof.values())},
+                         "share_of_kernel_time": share},
             "kernels": by_class,
             "e2e": {"value": job_throughput(world, C, e2e_steps, e2e_ms), "unit": UNIT, "compute_streams": args.e2e_streams,
                     "steps": e2e_steps, "h2d_bytes_per_step": bytes_io,
@@ -935,10 +995,12 @@ def run_gpu(args, rank, world, local_rank):
         }
         if not args.no_rows:
             sweep = measure_rotation_sweep(ctx, items, lanes, torch)
+            fused = measure_fused(ctx, ckks, items, lanes, torch)
             del items, lanes, lane1, lanes_e, dev_in, dev_out
             torch.cuda.empty_cache()
             line["other_rows"] = measure_other_rows(ctx, ckks, torch)
             line["other_rows"]["rotation_sweep"] = sweep
+            line["other_rows"]["fused_dataflow"] = fused
             line["other_rows"]["batched_keyswitch"] = measure_batched(ctx, ckks, torch)
             line["other_rows"]["small_keyswitch"] = measure_small_keyswitch(ckks, torch)
             line["other_rows"]["hoisted_rotations"] = measure_hoisted(ctx, ckks, torch)

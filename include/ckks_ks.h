@@ -353,6 +353,21 @@ int ckks_tune_set(ckks_ctx *ctx, const int *choice);
  * for this context.  Takes effect for later calls. */
 int ckks_bconv_select(ckks_ctx *ctx, int tensor_cores, int *available);
 
+/* The fused key-switching dataflow (Sec. 4.2 beta-limb caching with the
+ * Sec. 4.4 re-ordering of ModDown): with on = 1, ckks_keyswitch, ckks_rotate
+ * and a one-rotation ckks_hrotate run the last forward NTT pass of ModUp, the
+ * KSKInnerProd (digits read through Automorph, keys streamed once per digit)
+ * and the first inverse NTT pass of ModDown's special limbs in one kernel, so
+ * the new ModUp limbs and the special limbs of (u, v) never reach HBM in
+ * evaluation form (9 launches per HRotate instead of 11).  Same residues bit
+ * for bit.  Off by default: on one GB300 the unfused kernels give more
+ * throughput when many calls overlap on several streams, the fused one lower
+ * latency for a call alone.  *available (optional) = 1 when the context's
+ * primes and digit count allow it (every prime < 2^57, at most 4 digits at the
+ * full level, N from 2^10 to 2^17); elsewhere the calls stay unfused.  Takes
+ * effect for later calls. */
+int ckks_fuse_select(ckks_ctx *ctx, int on, int *available);
+
 /* ------------------------------------------------------------------------
  * Serving loop (no counterpart in the paper; it serves the paper's operations).
  * A server owns one device arena for request workspace and nstreams CUDA
@@ -467,11 +482,26 @@ enum {
     CKKS_K_INNER = 3,     /* KSKInnerProd (with Automorph of the digits) */
     CKKS_K_PMV = 4,       /* PtMatVecMult inner loop */
     CKKS_K_ELEMWISE = 5,  /* Automorph, PModUp, key-generation element-wise kernels */
-    CKKS_K_COUNT = 6
+    CKKS_K_FUSED = 6,     /* fused ModUp tail: last forward NTT pass + KSKInnerProd (+ ModDown's first
+                             inverse pass on the special positions) */
+    CKKS_K_COUNT = 7
 };
 int ckks_profile_enable(ckks_ctx *ctx, int on);
 int ckks_profile_reset(ckks_ctx *ctx);
 int ckks_profile_read(ckks_ctx *ctx, int kclass, double *total_ms, long long *launches, double *units);
+
+/* Measured ceiling of the transforms' butterfly rate (no counterpart in the
+ * paper; the measurement behind the NTT's ALU roofline, Sec. 2.3's butterfly
+ * with the Shoup product of Sec. 2.2).  Runs the forward lazy butterfly of
+ * the transforms from registers only (16 words per thread, 4 stages per round,
+ * no memory access in the loop) over every SM at the transforms' occupancy
+ * (32 warps per SM) for `rounds` rounds (1 .. 2^24), timed with CUDA events on
+ * `stream`; blocks until done.  *ms = the kernel's time, *butterflies = the
+ * butterflies it ran.  sink: a device buffer of at least
+ * ckks_butterfly_peak_sink_bytes bytes (16-byte aligned) that receives
+ * meaningless words.  CKKS_EINVAL on bad arguments, CKKS_ECUDA on a CUDA error. */
+int ckks_butterfly_peak_sink_bytes(const ckks_ctx *ctx, size_t *bytes);
+int ckks_butterfly_peak(ckks_ctx *ctx, int rounds, void *sink, ckks_stream_t stream, float *ms, double *butterflies);
 
 /* ------------------------------------------------------------------------
  * ModDown without a caller-supplied workspace (the paper has no counterpart;

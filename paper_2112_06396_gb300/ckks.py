@@ -124,6 +124,10 @@ _SIGS = {
     "ckks_server_poll": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double),
                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "ckks_server_selftest_timeout": (_i, [_vp, ctypes.c_uint32]),
+    "ckks_fuse_select": (_i, [_vp, _i, ctypes.POINTER(_i)]),
+    "ckks_butterfly_peak_sink_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "ckks_butterfly_peak": (_i, [_vp, _i, _vp, _vp, ctypes.POINTER(ctypes.c_float),
+                                 ctypes.POINTER(ctypes.c_double)]),
     "ckks_server_stats": (_i, [_vp, ctypes.POINTER(_Stats)]),
     "ckks_profile_enable": (_i, [_vp, _i]),
     "ckks_profile_reset": (_i, [_vp]),
@@ -132,7 +136,7 @@ _SIGS = {
 }
 
 K_NTT_FWD, K_NTT_INV, K_BCONV, K_INNER, K_PMV, K_ELEMWISE = range(6)
-K_NAMES = ["ntt_fwd", "ntt_inv", "bconv", "inner_prod", "pmv_accum", "elementwise"]
+K_NAMES = ["ntt_fwd", "ntt_inv", "bconv", "inner_prod", "pmv_accum", "elementwise", "fused_modup_ip"]
 
 
 def library_path() -> str:
@@ -301,6 +305,17 @@ class Context:
             out[name] = (ms.value, int(n.value), u.value)
         return out
 
+    def butterfly_peak(self, rounds=20000, stream=None):
+        """(butterflies per second, ms, butterflies) of the register-only butterfly
+        ceiling (ckks_butterfly_peak); blocks until the measurement is done."""
+        nb = ctypes.c_size_t()
+        _check(lib().ckks_butterfly_peak_sink_bytes(self._h, ctypes.byref(nb)))
+        sink = torch.empty(nb.value // 8, dtype=torch.uint64, device=self.device)
+        ms, bf = ctypes.c_float(), ctypes.c_double()
+        _check(lib().ckks_butterfly_peak(self._h, int(rounds), _p(sink), _stream(stream), ctypes.byref(ms),
+                                         ctypes.byref(bf)), self._h)
+        return bf.value / (ms.value * 1e-3), ms.value, bf.value
+
     def poll_status(self, stream=None):
         """True once the stream's work has finished; raises on an asynchronous CUDA error."""
         done = _i()
@@ -344,6 +359,14 @@ class Context:
         """Launch the bounded-wait self-test (ckks_selftest_bounded_wait): a wait
         on a barrier nothing arrives on, which gives up after limit_us."""
         _check(lib().ckks_selftest_bounded_wait(self._h, int(limit_us), _stream(stream)), self._h)
+
+    def fuse_modup(self, on=True):
+        """Run single KeySwitches and one-rotation HRotates through the fused
+        ModUp tail + KSKInnerProd kernel (ckks_fuse_select); returns whether the
+        context supports it."""
+        avail = _i()
+        _check(lib().ckks_fuse_select(self._h, 1 if on else 0, ctypes.byref(avail)))
+        return bool(avail.value)
 
     def bconv_tensor_cores(self, on=True):
         """Run the basis conversions on the tensor cores (on) or the integer

@@ -591,21 +591,42 @@ static int modup_all(ckks_ctx *ctx, const u64 *a, int ell, u64 *ext, u64 *acoeff
 // iNTT of the k P-limbs -> BConv P -> q with rounding -> NTT with the
 // (x - w) * P^-1 epilogue; add[p] (read through Automorph_g) and accumulation
 // are folded into the epilogue.  Scratch: pcoeff [npolys*k][N], w [npolys*ell][N].
+// p_half: the P-limbs of in[p] already went through the first pass of the
+// inverse NTT (the fused ModUp tail wrote them so): the second pass runs in
+// place on them, they are the conversion's sources, and pcoeff is not used.
 static int moddown_polys(ckks_ctx *ctx, int ell, int npolys, const u64 *const in[2], u64 *const out[2],
-                         const u64 *const add[2], uint32_t g, int accumulate, u64 *pcoeff, u64 *w, cudaStream_t st) {
+                         const u64 *const add[2], uint32_t g, int accumulate, u64 *pcoeff, u64 *w, cudaStream_t st,
+                         bool p_half = false) {
     const size_t N = ctx->N;
     const int k = ctx->k;
-    LimbList inv;  // prime-major: both polynomials' limbs of one prime are adjacent
-    for (int m = 0; m < k; ++m)
-        for (int p = 0; p < npolys; ++p) inv.add(in[p] + size_t(ell + m) * N, pcoeff + size_t(p * k + m) * N, ctx->L + m);
-    RC(run_ntt(ctx, inv, true, st));
+    const u64 *csrc[2] = {nullptr, nullptr};
+    if (p_half) {
+        NttBatch b;
+        b.count = 0;
+        for (int m = 0; m < k; ++m)
+            for (int p = 0; p < npolys; ++p) {
+                u64 *limb = const_cast<u64 *>(in[p]) + size_t(ell + m) * N;
+                b.src[b.count] = limb;
+                b.dst[b.count] = limb;
+                b.prime[b.count++] = uint16_t(ctx->L + m);
+            }
+        CK(launch_ntt_inv_colpass(ctx, b, st));
+        for (int p = 0; p < npolys; ++p) csrc[p] = in[p] + size_t(ell) * N;
+    } else {
+        LimbList inv;  // prime-major: both polynomials' limbs of one prime are adjacent
+        for (int m = 0; m < k; ++m)
+            for (int p = 0; p < npolys; ++p)
+                inv.add(in[p] + size_t(ell + m) * N, pcoeff + size_t(p * k + m) * N, ctx->L + m);
+        RC(run_ntt(ctx, inv, true, st));
+        for (int p = 0; p < npolys; ++p) csrc[p] = pcoeff + size_t(p) * k * N;
+    }
     BConvLaunch l{};
     l.ngroups = npolys;
     l.chunk = ell;
     l.chunks = 1;
     for (int p = 0; p < npolys; ++p) {
         l.g[p].plan = ctx->d_moddown + ell;
-        l.g[p].src = pcoeff + size_t(p) * k * N;
+        l.g[p].src = csrc[p];
         l.g[p].dst = w + size_t(p) * ell * N;
     }
     CK(launch_bconv(ctx, l, k, st));
@@ -743,12 +764,67 @@ static KsLayout ks_layout(const ckks_ctx *c, int ell) {
     return o;
 }
 
+// ModUp of every digit with the fused tail: iNTT -> conversion -> pass S of the
+// new limbs' forward NTT -> modup_ip_kernel (pass C, KSKInnerProd with the
+// digits read through Automorph_g, and the first inverse pass of ModDown on the
+// special positions of u and v).  ext: [beta][ell+k][N] and acoeff: [ell][N]
+// scratch; u, v: [ell+k][N] (special positions half inverse-transformed, for
+// moddown_polys with p_half).
+static int modup_ip_fused(ckks_ctx *ctx, const u64 *a, int ell, const u64 *key, uint32_t g, u64 *ext, u64 *acoeff,
+                          u64 *u, u64 *v, cudaStream_t st) {
+    const size_t N = ctx->N;
+    const int k = ctx->k, beta = beta_of(ctx, ell), ext_n = ell + k;
+    LimbList inv;
+    for (int i = 0; i < ell; ++i) inv.add(a + i * N, acoeff + i * N, i);
+    RC(run_ntt(ctx, inv, true, st));
+    for (int j0 = 0; j0 < beta; j0 += kMaxGroups) {
+        BConvLaunch l{};
+        l.ngroups = std::min(beta - j0, kMaxGroups);
+        l.chunk = ext_n - std::min(ctx->alpha, ell - (beta - 1) * ctx->alpha);
+        l.chunks = 1;
+        for (int gi = 0; gi < l.ngroups; ++gi) {
+            const int j = j0 + gi;
+            l.g[gi].plan = ctx->d_modup + size_t(ell) * ctx->dnum + j;
+            l.g[gi].src = acoeff + size_t(j) * ctx->alpha * N;
+            l.g[gi].dst = ext + size_t(j) * ext_n * N;
+        }
+        CK(launch_bconv(ctx, l, std::min(ctx->alpha, ell), st));
+    }
+    NttBatch b;
+    b.count = 0;
+    for (int t = 0; t < ext_n; ++t)
+        for (int j = 0; j < beta; ++j) {
+            const int lo = j * ctx->alpha, hi = std::min(lo + ctx->alpha, ell);
+            if (t >= lo && t < hi) continue;
+            if (b.count == kMaxBatch) {
+                CK(launch_ntt_fwd_colpass(ctx, b, st));
+                b.count = 0;
+            }
+            u64 *p = ext + (size_t(j) * ext_n + t) * N;
+            b.src[b.count] = p;
+            b.dst[b.count] = p;
+            b.prime[b.count++] = uint16_t(ext_prime(ctx, ell, t));
+        }
+    CK(launch_ntt_fwd_colpass(ctx, b, st));
+    FusedIpArgs f{ext, a, key, u, v, ell, g, 0, 0};
+    f.compressed = key_seed(ctx, key, &f.seed);
+    CK(launch_modup_ip(ctx, f, st));
+    return CKKS_OK;
+}
+
 // KeySwitch core: ModUp(a), inner product (digits through Automorph_gin), ModDown.
 static int keyswitch_core(ckks_ctx *ctx, const u64 *a, int ell, const u64 *key, uint32_t gin, u64 *out0, u64 *out1,
                           const u64 *add1, uint32_t gadd, int accumulate, u64 *ws, cudaStream_t st) {
     const size_t N = ctx->N;
     const KsLayout lo = ks_layout(ctx, ell);
     u64 *u = ws + lo.uv, *v = u + size_t(ell + ctx->k) * N;
+    if (ctx->fuse_on && modup_ip_supported(ctx, ell)) {
+        RC(modup_ip_fused(ctx, a, ell, key, gin, ws + lo.ext, ws + lo.acoeff, u, v, st));
+        const u64 *in[2] = {u, v};
+        u64 *out[2] = {out0, out1};
+        const u64 *add[2] = {nullptr, add1};
+        return moddown_polys(ctx, ell, 2, in, out, add, gadd, accumulate, ws + lo.pcoeff, ws + lo.w, st, true);
+    }
     RC(modup_all(ctx, a, ell, ws + lo.ext, ws + lo.acoeff, st));
     InnerArgs ia{ws + lo.ext, a, key, u, v, ell, gin};
     ia.compressed = key_seed(ctx, key, &ia.seed);
@@ -787,12 +863,15 @@ static HrLayout hr_layout(const ckks_ctx *c, int ell) {
 struct PmvLayout {
     size_t ext, acc, tmp, ct, res, rot, total;
 };
+// acc holds one (a, b) accumulator pair per giant step when every giant step
+// runs in one launch (pmv_all_kernel), else one pair reused per giant step.
 static PmvLayout pmv_layout(const ckks_ctx *c, int ell, int ng) {
     const size_t N = c->N;
     PmvLayout o;
     o.ext = 0;
     o.acc = size_t(beta_of(c, ell)) * (ell + c->k) * N;
-    o.tmp = o.acc + size_t(2) * (ell + c->k) * N;
+    const int nacc = ng >= 1 && ng <= kMaxGiant && beta_of(c, ell) <= 4 ? ng : 1;
+    o.tmp = o.acc + size_t(2) * nacc * (ell + c->k) * N;
     o.ct = o.tmp + std::max(size_t(ell), words_moddown2(c, ell)) * N;
     o.res = o.ct + size_t(2) * ell * N;
     o.rot = o.res + size_t(2) * ell * N;
@@ -955,8 +1034,19 @@ extern "C" int ckks_hrotate(ckks_ctx *ctx, const uint64_t *a, const uint64_t *b,
     const size_t N = ctx->N;
     u64 *w = static_cast<u64 *>(ws);
     const HrLayout lo = hr_layout(ctx, ell);
-    RC(modup_all(ctx, a, ell, w + lo.ext, w + lo.tmp, st));
     u64 *u = w + lo.uv, *v = u + size_t(ell + ctx->k) * N;
+    if (r == 1 && ctx->fuse_on && modup_ip_supported(ctx, ell)) {
+        // one rotation: the ModUp tail, the inner product and ModDown's first
+        // inverse pass in one kernel (several rotations share the transformed
+        // digits instead)
+        RC(modup_ip_fused(ctx, a, ell, keys[0], galois[0], w + lo.ext, w + lo.tmp, u, v, st));
+        const u64 *in[2] = {u, v};
+        u64 *out[2] = {oa[0], ob[0]};
+        const u64 *add[2] = {nullptr, b};
+        return moddown_polys(ctx, ell, 2, in, out, add, galois[0], 0, w + lo.tmp, w + lo.tmp + size_t(2) * ctx->k * N,
+                             st, true);
+    }
+    RC(modup_all(ctx, a, ell, w + lo.ext, w + lo.tmp, st));
     for (int i = 0; i < r; ++i) {
         InnerArgs ia{w + lo.ext, a, keys[i], u, v, ell, galois[i]};
         ia.compressed = key_seed(ctx, keys[i], &ia.seed);
@@ -1388,7 +1478,40 @@ extern "C" int ckks_ptmatvecmult(ckks_ctx *ctx, const uint64_t *a, const uint64_
     u64 *acc_a = w + lo.acc, *acc_b = acc_a + size_t(ell + k) * N;
     u64 *res_a = rescale ? w + lo.res : oa, *res_b = rescale ? w + lo.res + size_t(ell) * N : ob;
     u64 *ct_a = w + lo.ct, *ct_b = ct_a + size_t(ell) * N;
-    for (int t = 0; t < ng; ++t) {
+    if (pmv_all_supported(ctx, ell, nb, ng)) {
+        // every giant step's accumulator in one pass over the baby-step keys
+        PmvAllArgs pa{};
+        pa.ext = w + lo.ext;
+        pa.a = a;
+        pa.b = b;
+        pa.ell = ell;
+        pa.nb = nb;
+        pa.ng = ng;
+        for (int t = 0; t < ng; ++t) {
+            pa.acc_a[t] = acc_a + size_t(2) * t * (ell + k) * N;
+            pa.acc_b[t] = pa.acc_a[t] + size_t(ell + k) * N;
+        }
+        for (int i = 0; i < nb; ++i) {
+            pa.galois[i] = i == 0 ? 1u : g_baby[i];
+            pa.key[i] = i == 0 ? nullptr : key_baby[i];
+            pa.compressed[i] = i == 0 ? 0 : uint8_t(key_seed(ctx, key_baby[i], &pa.seed[i]));
+        }
+        for (int d = 0; d < nb * ng; ++d) pa.diag[d] = diag[d];
+        CK(launch_pmv_all(ctx, pa, st));
+        const u64 *noadd[2] = {nullptr, nullptr};
+        for (int t = 0; t < ng; ++t) {
+            const u64 *in[2] = {pa.acc_a[t], pa.acc_b[t]};
+            if (t == 0) {
+                u64 *out[2] = {res_a, res_b};
+                RC(moddown_polys(ctx, ell, 2, in, out, noadd, 1, 0, w + lo.tmp, w + lo.tmp + size_t(2) * k * N, st));
+            } else {
+                u64 *out[2] = {ct_a, ct_b};
+                RC(moddown_polys(ctx, ell, 2, in, out, noadd, 1, 0, w + lo.tmp, w + lo.tmp + size_t(2) * k * N, st));
+                RC(rotate_core(ctx, ct_a, ct_b, ell, g_giant[t], key_giant[t], res_a, res_b, 1, w + lo.rot, st));
+            }
+        }
+    }
+    for (int t = 0; t < ng && !pmv_all_supported(ctx, ell, nb, ng); ++t) {
         PmvArgs pa{};
         pa.ext = w + lo.ext;
         pa.a = a;
@@ -1553,6 +1676,40 @@ extern "C" int ckks_tune_set(ckks_ctx *ctx, const int *choice) {
 extern "C" int ckks_selftest_bounded_wait(ckks_ctx *ctx, uint32_t limit_us, ckks_stream_t stream) {
     if (ctx == nullptr || limit_us == 0 || limit_us > 2000000u) return CKKS_EINVAL;
     CK(launch_bounded_wait_selftest(ctx, uint64_t(limit_us) * 1000u, (cudaStream_t)stream));
+    return CKKS_OK;
+}
+
+extern "C" int ckks_butterfly_peak_sink_bytes(const ckks_ctx *ctx, size_t *bytes) {
+    if (ctx == nullptr || bytes == nullptr) return CKKS_EINVAL;
+    *bytes = bfly_peak_sink_words(ctx) * sizeof(u64);
+    return CKKS_OK;
+}
+
+extern "C" int ckks_butterfly_peak(ckks_ctx *ctx, int rounds, void *sink, ckks_stream_t stream, float *ms,
+                                   double *butterflies) {
+    OpRange r_("ckks_butterfly_peak");
+    if (ctx == nullptr || rounds < 1 || rounds > (1 << 24) || !al16(sink) || ms == nullptr || butterflies == nullptr)
+        return CKKS_EINVAL;
+    const cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    cudaError_t err = cudaEventCreate(&e1);
+    if (err == cudaSuccess) err = cudaEventRecord(e0, st);
+    if (err == cudaSuccess) err = launch_bfly_peak(ctx, rounds, static_cast<u64 *>(sink), st, butterflies);
+    if (err == cudaSuccess) err = cudaEventRecord(e1, st);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    if (err == cudaSuccess) err = cudaEventElapsedTime(ms, e0, e1);
+    cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    CK(err);
+    return CKKS_OK;
+}
+
+extern "C" int ckks_fuse_select(ckks_ctx *ctx, int on, int *available) {
+    if (ctx == nullptr) return CKKS_EINVAL;
+    if (available) *available = ctx->small_primes && ctx->logN >= 10 && ctx->logN <= 17 && ctx->alpha > 0 &&
+                                beta_of(ctx, ctx->L) <= 4;
+    ctx->fuse_on = on != 0;
     return CKKS_OK;
 }
 

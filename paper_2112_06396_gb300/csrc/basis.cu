@@ -288,6 +288,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     give_up();
                     break;
                 }
+                // order the producers' reads of the stage (generic proxy), seen
+                // through x_empty, before the bulk copies that overwrite it
+                tc::fence_async_smem();
                 tc::mbar_arrive_expect_tx(&x_full[xs], uint32_t(n_src) * 1024u);
                 for (int g = 0; g < n_src; ++g)
                     tc::bulk_g2s(Xs + (size_t(xs) * (KG - 1) + g) * 128, G.src + size_t(g) * N + size_t(tile) * 128,
@@ -322,7 +325,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const int g = 2 * i + par;
                 x[i] = g < n_src ? xrow[g * 128] : 0;
             }
-            tc::mbar_arrive(&x_empty[xs]);
             uint4 *row = As + s * (128 * KG) + (m >> 3) * (KG * 8) + (m & 7);
 #pragma unroll
             for (int i = 0; i < KG / 2; ++i) {
@@ -340,6 +342,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 row[g * 8] = v;
             }
             tc::fence_async_smem();
+            // the source stage is handed back only now, after every value read
+            // from it has been used: releasing it right after the loads let the
+            // next bulk copy into the stage land before some of them completed
+            // when the SM was shared with other kernels (wrong sums, no error)
+            tc::mbar_arrive(&x_empty[xs]);
             tc::mbar_arrive(&a_full[s]);
         }
     } else if (warp == kMmaWarp) {

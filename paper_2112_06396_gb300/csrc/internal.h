@@ -18,6 +18,8 @@ struct ckks_ctx {
     int tc_kg;                        // K groups of the tensor-core basis conversion, 0 if not available
     bool tc_on = true;                // use it when available (ckks_bconv_select can switch it off)
     bool tc_lazy;                     // its outputs stay below 8t without a final reduction
+    bool fuse_on = false;             // single KeySwitch / one-rotation HRotate through modup_ip_kernel
+                                      // (ckks_fuse_select)
     std::vector<u64> primes;          // L + k: q_0..q_{L-1}, p_0..p_{k-1}
     // device tables (one allocation)
     void *d_block;
@@ -53,12 +55,12 @@ struct ckks_ctx {
     mutable std::vector<cudaEvent_t> prof_pool;
     mutable double prof_ms[8] = {};
     mutable long long prof_n[8] = {};
-    mutable double prof_units[8] = {};
+    mutable double prof_units[8] = {};  // indexed by kernel class (K_*, at most 8)
 };
 
 namespace ckks {
 
-enum { K_NTT_FWD = 0, K_NTT_INV = 1, K_BCONV = 2, K_INNER = 3, K_PMV = 4, K_ELEMWISE = 5 };
+enum { K_NTT_FWD = 0, K_NTT_INV = 1, K_BCONV = 2, K_INNER = 3, K_PMV = 4, K_ELEMWISE = 5, K_FUSED = 6 };
 
 // Brackets one launch with CUDA events when the context's measurement hook is on.
 class ProfScope {
@@ -103,6 +105,25 @@ cudaError_t launch_ntt_fwd(const ckks_ctx *ctx, const NttBatch &b, const Epi *ep
 cudaError_t launch_ntt_inv(const ckks_ctx *ctx, const NttBatch &b, cudaStream_t st);
 cudaError_t launch_ntt_batch(const ckks_ctx *ctx, const KsBatchDesc &d, int phase, cudaStream_t st);
 constexpr int kTuneSmallBatch = 48;
+// Fused ModUp tail + KSKInnerProd (+ ModDown's first inverse pass on the
+// special positions), modup_ip_kernel.
+struct FusedIpArgs {
+    const u64 *ext;   // [beta][ell+k][N]: the new ModUp limbs after pass S of the forward NTT
+    const u64 *own;   // [ell][N] evaluation-form input: the digits' own limbs
+    const u64 *key;   // [dnum][2][L+k][N], or the rows b_j only [dnum][L+k][N] when compressed
+    u64 *u, *v;       // [ell+k][N]: chain positions in evaluation form; special positions after
+                      // the first pass of the inverse NTT
+    int ell;
+    uint32_t galois;  // digits read through Automorph_galois (1: none)
+    int compressed;
+    u64 seed;
+};
+bool modup_ip_supported(const ckks_ctx *ctx, int ell);
+cudaError_t launch_modup_ip(const ckks_ctx *ctx, const FusedIpArgs &f, cudaStream_t st);
+cudaError_t launch_ntt_fwd_colpass(const ckks_ctx *ctx, const NttBatch &b, cudaStream_t st);
+cudaError_t launch_ntt_inv_colpass(const ckks_ctx *ctx, const NttBatch &b, cudaStream_t st);
+cudaError_t launch_bfly_peak(const ckks_ctx *ctx, int rounds, u64 *sink, cudaStream_t st, double *butterflies);
+size_t bfly_peak_sink_words(const ckks_ctx *ctx);
 cudaError_t ntt_autotune(ckks_ctx *ctx, u64 *scratch, int small, int large, cudaStream_t st, float *times_out);
 cudaError_t launch_bconv(const ckks_ctx *ctx, const BConvLaunch &l, int max_src, cudaStream_t st);
 cudaError_t launch_bconv_batch(const ckks_ctx *ctx, const KsBatchDesc &d, int down, cudaStream_t st,
@@ -157,6 +178,23 @@ struct PmvArgs {
     uint8_t compressed[kMaxRot];  // key[i] holds the rows b_j only
 };
 cudaError_t launch_pmv_accum(const ckks_ctx *ctx, const PmvArgs &a, cudaStream_t st);
+
+// Every giant step of Algorithm 8 in one launch (pmv_all_kernel): ng <= 8
+// giant steps, nb * ng <= kMaxRot diagonals, beta <= 4.
+constexpr int kMaxGiant = 8;
+struct PmvAllArgs {
+    const u64 *ext;               // hoisted ModUp outputs [beta][ell+k][N]
+    const u64 *a, *b;             // input ciphertext [ell][N]
+    u64 *acc_a[kMaxGiant], *acc_b[kMaxGiant];  // per giant step [ell+k][N]
+    int ell, nb, ng;
+    uint32_t galois[kMaxRot];
+    const u64 *key[kMaxRot];
+    const u64 *diag[kMaxRot];     // diagonal (t, i) at t*nb + i
+    u64 seed[kMaxRot];
+    uint8_t compressed[kMaxRot];
+};
+bool pmv_all_supported(const ckks_ctx *ctx, int ell, int nb, int ng);
+cudaError_t launch_pmv_all(const ckks_ctx *ctx, const PmvAllArgs &a, cudaStream_t st);
 
 cudaError_t launch_automorph(const ckks_ctx *ctx, const u64 *in, u64 *out, int nlimbs, uint32_t g, cudaStream_t st);
 cudaError_t launch_pmodup(const ckks_ctx *ctx, const u64 *in, u64 *out, int ell, cudaStream_t st);

@@ -470,6 +470,134 @@ cudaError_t launch_pmv_accum(const ckks_ctx *ctx, const PmvArgs &a, cudaStream_t
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ PtMatVecMult, every giant step at once
+// The same sums as pmv_accum_kernel, for all giant steps t < NG in one pass:
+// baby step i's (u_i, v_i + [P*b_rot,i]) is formed once per slot and added,
+// times M_{t,i}, into every giant step's accumulator.  Each baby-step key is
+// therefore read once per call instead of once per giant step (the key stream
+// dominates the bytes of Algorithm 8 with BSGS, Sec. 5.2), and every diagonal
+// once.  One slot per thread (8-byte loads, coalesced by the warp; the
+// Automorph gather stays inside aligned 32-slot blocks): the NG x 2 128-bit
+// accumulators live in registers.  Grid (slot tile, extended position).
+template <int BETA, int NG, bool COMP>
+__global__ void __launch_bounds__(256) pmv_all_kernel(const __grid_constant__ PmvAllArgs A,
+                                                      const PrimeInfo *__restrict__ pinfo,
+                                                      const ulonglong2 *__restrict__ Pmod, int logN, int L, int k,
+                                                      int alpha) {
+    const size_t N = size_t(1) << logN;
+    const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int t = blockIdx.y;
+    const int ell = A.ell, ext = ell + k, LK = L + k;
+    const int prime = t < ell ? t : L + (t - ell);
+    const PrimeInfo P = pinfo[prime];
+    const ulonglong2 pm = Pmod[prime];
+    const size_t to = size_t(t) * N;
+    u64 al[NG], ah[NG], bl[NG], bh[NG];
+#pragma unroll
+    for (int g = 0; g < NG; g++) al[g] = ah[g] = bl[g] = bh[g] = 0;
+#pragma unroll 1
+    for (int i = 0; i < A.nb; i++) {
+        u64 M[NG];
+#pragma unroll
+        for (int g = 0; g < NG; g++) M[g] = g < A.ng ? __ldcs(A.diag[g * A.nb + i] + to + n) : 0;
+        u64 u, w;
+        if (A.key[i] == nullptr) {
+            // baby step 0 (no rotation): (P*a, P*b) on the chain, 0 on the special primes
+            u = w = 0;
+            if (t < ell) {
+                u = shoup_mul(A.a[to + n], pm.x, pm.y, P.p);
+                w = shoup_mul(A.b[to + n], pm.x, pm.y, P.p);
+            }
+        } else {
+            const uint32_t g = A.galois[i];
+            const uint32_t src = g == 1 ? n : automorph_src(n, g, logN);
+            const u64 *key = A.key[i];
+            u64 dv[BETA], ka[BETA], kb[BETA];
+#pragma unroll
+            for (int j = 0; j < BETA; j++) {
+                const bool own = t < ell && (t / alpha) == j;
+                const u64 *d = own ? A.a + to : A.ext + (size_t(j) * ext + t) * N;
+                dv[j] = d[src];
+                if (COMP && A.compressed[i]) {
+                    kb[j] = __ldcs(key + (size_t(j) * LK + prime) * N + n);
+                } else {
+                    ka[j] = __ldcs(key + ((size_t(j) * 2 + 0) * LK + prime) * N + n);
+                    kb[j] = __ldcs(key + ((size_t(j) * 2 + 1) * LK + prime) * N + n);
+                }
+            }
+            const u64 bsrc = t < ell ? A.b[to + src] : 0;
+            if (COMP && A.compressed[i]) {
+                const int shift = __clzll(P.p);
+#pragma unroll
+                for (int j = 0; j < BETA; j++)
+                    ka[j] = key_a_element(A.seed[i], (u64(j) * LK + prime) * N + n, P.p, shift);
+            }
+            u64 ul = 0, uh = 0, vl = 0, vh = 0;
+#pragma unroll
+            for (int j = 0; j < BETA; j++) {
+                mac128(ul, uh, dv[j], ka[j]);
+                mac128(vl, vh, dv[j], kb[j]);
+            }
+            u = reduce128(ul, uh, P);
+            w = reduce128(vl, vh, P);
+            if (t < ell) w = add_mod(w, shoup_mul(bsrc, pm.x, pm.y, P.p), P.p);
+        }
+#pragma unroll
+        for (int g = 0; g < NG; g++) {
+            mac128(al[g], ah[g], M[g], u);
+            mac128(bl[g], bh[g], M[g], w);
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < NG; g++) {
+        if (g < A.ng) {
+            A.acc_a[g][to + n] = reduce128(al[g], ah[g], P);
+            A.acc_b[g][to + n] = reduce128(bl[g], bh[g], P);
+        }
+    }
+}
+
+bool pmv_all_supported(const ckks_ctx *ctx, int ell, int nb, int ng) {
+    return beta_of(ctx, ell) <= 4 && ng >= 1 && ng <= kMaxGiant && nb * ng <= kMaxRot;
+}
+
+cudaError_t launch_pmv_all(const ckks_ctx *ctx, const PmvAllArgs &a, cudaStream_t st) {
+    const int threads = 256;
+    dim3 grid(unsigned((ctx->N + threads - 1) / threads), unsigned(a.ell + ctx->k));
+    ProfScope ps(ctx, K_PMV, double(a.ell + ctx->k) * a.nb * a.ng, st);
+    bool comp = false;
+    for (int i = 0; i < a.nb; ++i) comp = comp || a.compressed[i];
+    const int beta = beta_of(ctx, a.ell);
+#define CKKS_PMV(B, G, C)                                                                                          \
+    pmv_all_kernel<B, G, C><<<grid, threads, 0, st>>>(a, ctx->d_pinfo, ctx->d_Pmod, ctx->logN, ctx->L, ctx->k,    \
+                                                      ctx->alpha)
+#define CKKS_PMV_G(B, C)                                                                                           \
+    switch (a.ng) {                                                                                                \
+    case 1: CKKS_PMV(B, 1, C); break;                                                                              \
+    case 2: CKKS_PMV(B, 2, C); break;                                                                              \
+    case 3: CKKS_PMV(B, 3, C); break;                                                                              \
+    case 4: CKKS_PMV(B, 4, C); break;                                                                              \
+    default: CKKS_PMV(B, 8, C);                                                                                    \
+    }
+#define CKKS_PMV_B(C)                                                                                              \
+    switch (beta) {                                                                                                \
+    case 1: CKKS_PMV_G(1, C) break;                                                                                \
+    case 2: CKKS_PMV_G(2, C) break;                                                                                \
+    case 3: CKKS_PMV_G(3, C) break;                                                                                \
+    default: CKKS_PMV_G(4, C) break;                                                                               \
+    }
+    if (comp) {
+        CKKS_PMV_B(true)
+    } else {
+        CKKS_PMV_B(false)
+    }
+#undef CKKS_PMV_B
+#undef CKKS_PMV_G
+#undef CKKS_PMV
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ Automorph
 __global__ void __launch_bounds__(256) automorph_kernel(const u64 *__restrict__ in, u64 *__restrict__ out, uint32_t g,
                                                         int logN) {

@@ -20,6 +20,8 @@
 #include "batch.cuh"
 #include "common.cuh"
 #include "internal.h"
+#include "prng.cuh"
+#include "tc.cuh"
 
 namespace ckks {
 
@@ -303,6 +305,220 @@ ntt_pass_kernel(const __grid_constant__ MAP map, const PrimeInfo *__restrict__ p
     }
 }
 
+// ------------------------------------------------------------------ fused ModUp tail + KSKInnerProd
+// The last forward pass of ModUp's NTT (pass C) fused with KSKInnerProd and,
+// on the special positions, with the first pass of ModDown's inverse NTT (the
+// beta-limb caching of Sec. 4.2 and the re-ordering of Sec. 4.4).  A CTA owns
+// one extended position t and C consecutive output blocks of 2^L2 slots, with
+// one group of 64 threads per digit (four groups; a group whose digit does not
+// exist or holds t, on a chain position, has no pass to run):
+//  0. One thread asks the TMA unit to pull the CTA's key rows (2 beta tiles of
+//     C * 2^L2 contiguous words, or beta with a compressed key) and, on a
+//     chain position, the C source blocks of the digit's own limb into L2:
+//     the key stream overlaps step 1 and step 2 reads it from L2.
+//  1. Each group runs pass C of its digit's limb at t, written by pass S of
+//     ModUp's NTT, on the C source blocks that the output blocks read through
+//     Automorph_g (an aligned block of slots maps onto one aligned block, a
+//     slot pair onto an aligned pair), leaving the lazy values in shared
+//     memory; the groups share the prime's twiddles through L1.
+//  2. The threads form u = sum_j d_j a_j and v = sum_j d_j b_j slot pair by
+//     slot pair: digits from shared memory through the permutation, exact
+//     128-bit sums (digits below 76p), one reduction.
+//  3. Chain positions store u and v.  Special positions, which ModDown only
+//     reads in coefficient form, run pass C of the inverse NTT on u and v and
+//     store the result in place of u and v, where ModDown's inverse pass S
+//     continues.
+// The new ModUp limbs never reach HBM in evaluation form, nor the special
+// limbs of u and v in evaluation form.
+template <int LOGN, bool COMP>
+__global__ void __launch_bounds__(256, 4)
+modup_ip_kernel(const __grid_constant__ FusedIpArgs F, const PrimeInfo *__restrict__ pinfo,
+                const ulonglong2 *__restrict__ twf_all, const ulonglong2 *__restrict__ twi_all, int L, int k,
+                int alpha, int t_base) {
+    constexpr int L2 = LOGN >> 1, L1 = LOGN - L2, LOGR = L2;
+    constexpr int A = (LOGR + 1) / 2, B = LOGR - A, TPC = 1 << B, E = 1 << A, R = 1 << LOGR, RS = R + TPC;
+    constexpr int C = 64 / TPC;                   // blocks per CTA: 64 threads of E words cover them
+    constexpr int CR = C * R;                     // slots of the CTA
+    constexpr uint32_t N = 1u << LOGN;
+    constexpr int logN = LOGN;
+    extern __shared__ __align__(16) u64 sm[];
+    constexpr int PAIRS = CR / 2 / 256;           // slot pairs per thread in step 2
+    u64 *const dig = sm;                          // [4][C * RS]: transformed digits (padded rows)
+    u64 *const uvs = sm + 4 * C * RS;             // [2][C * RS]: u, v of a special position
+    const int tid = threadIdx.x, grp = tid >> 6, lt = tid & 63;
+    const int g = lt % TPC, cl = lt / TPC;
+    const int t = t_base + int(blockIdx.y);
+    const int ell = F.ell, ext = ell + k, LK = L + k;
+    const int prime = t < ell ? t : L + (t - ell);
+    const int beta = (ell + alpha - 1) / alpha;
+    const int own_j = t < ell ? t / alpha : -1;
+    const uint32_t c0 = blockIdx.x * C;
+    const uint32_t gal = F.galois;
+    const u64 p = pinfo[prime].p, np = u64(0) - p;
+    auto sidx = [&](int b, int r) -> int { return b * RS + r + (r >> A); };
+    auto group_sync = [&]() { asm volatile("bar.sync %0, 64;" ::"r"(1 + grp) : "memory"); };
+    auto src_block = [&](uint32_t oblk) -> uint32_t {
+        return gal == 1 ? oblk : (automorph_src(oblk << L2, gal, logN) >> L2);
+    };
+    // shared-memory buffer of digit j (the digits with a pass, in order)
+    auto buf = [&](int j) -> int { return (own_j >= 0 && j > own_j) ? j - 1 : j; };
+
+    // ---- 0. the key rows and the own limb's blocks into L2
+    if (tid == 0) {
+        const uint32_t rowb = uint32_t(CR) * sizeof(u64);
+        for (int j = 0; j < beta; j++) {
+            for (int ab = COMP ? 1 : 0; ab < 2; ab++) {
+                const u64 *src = COMP ? F.key + (size_t(j) * LK + prime) * N
+                                      : F.key + ((size_t(j) * 2 + ab) * LK + prime) * N;
+                l2_prefetch(src + (size_t(c0) << L2), rowb);
+            }
+        }
+        if (own_j >= 0)
+            for (int b = 0; b < C; b++)
+                l2_prefetch(F.own + size_t(t) * N + (size_t(src_block(c0 + b)) << L2), uint32_t(R) * sizeof(u64));
+    }
+
+    // ---- 1. pass C of the digits' new limbs (group grp: the grp-th digit with a pass)
+    const int jd = (own_j >= 0 && grp >= own_j) ? grp + 1 : grp;
+    if (jd < beta) {
+        u64 *gs = dig + grp * (C * RS);
+        const uint32_t sblk = src_block(c0 + cl);
+        const u64 *__restrict__ src = F.ext + (size_t(jd) * ext + t) * N + (size_t(sblk) << L2);
+        const ulonglong2 *__restrict__ tw = twf_all + size_t(prime) * N;
+        auto TW = [&](int sigma, int r) -> ulonglong2 {
+            return ld_keep(&tw[(1u << (L1 + sigma)) + (sblk << sigma) + (uint32_t(r) >> (LOGR - sigma))]);
+        };
+        u64 x[E];
+#pragma unroll
+        for (int q = 0; q < E; q++) x[q] = src[g + (q << B)];
+#pragma unroll
+        for (int sg = 0; sg < A; sg++) {
+            const int half = 1 << (A - 1 - sg);
+#pragma unroll
+            for (int q = 0; q < E; q++) {
+                if (q & half) continue;
+                ct_bfly<true>(x[q], x[q + half], TW(sg, g + (q << B)), p, np);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < E; q++) gs[sidx(cl, g + (q << B))] = x[q];
+        group_sync();
+#pragma unroll
+        for (int e = 0; e < E; e++) x[e] = gs[sidx(cl, (g << A) + e)];
+#pragma unroll
+        for (int sg = A; sg < LOGR; sg++) {
+            const int half = 1 << (LOGR - 1 - sg);
+#pragma unroll
+            for (int e = 0; e < E; e++) {
+                if (e & half) continue;
+                ct_bfly<true>(x[e], x[e + half], TW(sg, (g << A) + e), p, np);
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < E; e++) gs[sidx(cl, (g << A) + e)] = x[e];  // the slots this thread read
+    }
+    __syncthreads();
+
+    // ---- 2. the inner product, PAIRS slot pairs per thread
+    const PrimeInfo P = pinfo[prime];
+    const int shift = __clzll(p);
+#pragma unroll
+    for (int q = 0; q < PAIRS; q++) {
+        const int pi = tid + q * 256;
+        const int b = pi / (R / 2), r = (pi % (R / 2)) * 2;
+        const uint32_t n0 = ((c0 + uint32_t(b)) << L2) + uint32_t(r);
+        const uint32_t s = gal == 1 ? n0 : automorph_src(n0, gal, logN);
+        const int rs = int(s & uint32_t(R - 1)) & ~1;
+        const bool swap = s & 1u;
+        u64 ul0 = 0, uh0 = 0, ul1 = 0, uh1 = 0, vl0 = 0, vh0 = 0, vl1 = 0, vh1 = 0;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            if (j < beta) {
+                ulonglong2 dv;
+                if (j == own_j) {
+                    const u64 *o = F.own + size_t(t) * N + (size_t(s >> L2) << L2);
+                    dv = *reinterpret_cast<const ulonglong2 *>(o + rs);
+                } else {
+                    const u64 *gs = dig + buf(j) * (C * RS);
+                    dv = make_ulonglong2(gs[sidx(b, rs)], gs[sidx(b, rs + 1)]);
+                }
+                if (swap) {
+                    const u64 tmp = dv.x;
+                    dv.x = dv.y;
+                    dv.y = tmp;
+                }
+                ulonglong2 ka, kb;
+                if (COMP) {
+                    kb = __ldcs(reinterpret_cast<const ulonglong2 *>(F.key + (size_t(j) * LK + prime) * N + n0));
+                    const u64 e0 = (u64(j) * LK + prime) * N + n0;
+                    ka = make_ulonglong2(key_a_element(F.seed, e0, p, shift), key_a_element(F.seed, e0 + 1, p, shift));
+                } else {
+                    ka = __ldcs(reinterpret_cast<const ulonglong2 *>(F.key + ((size_t(j) * 2 + 0) * LK + prime) * N + n0));
+                    kb = __ldcs(reinterpret_cast<const ulonglong2 *>(F.key + ((size_t(j) * 2 + 1) * LK + prime) * N + n0));
+                }
+                mac128(ul0, uh0, dv.x, ka.x);
+                mac128(ul1, uh1, dv.y, ka.y);
+                mac128(vl0, vh0, dv.x, kb.x);
+                mac128(vl1, vh1, dv.y, kb.y);
+            }
+        }
+        const ulonglong2 uo = make_ulonglong2(reduce128(ul0, uh0, P), reduce128(ul1, uh1, P));
+        const ulonglong2 vo = make_ulonglong2(reduce128(vl0, vh0, P), reduce128(vl1, vh1, P));
+        if (t < ell) {
+            const size_t o = size_t(t) * N + n0;
+            *reinterpret_cast<ulonglong2 *>(F.u + o) = uo;
+            *reinterpret_cast<ulonglong2 *>(F.v + o) = vo;
+        } else {
+            uvs[sidx(b, r)] = uo.x;
+            uvs[sidx(b, r + 1)] = uo.y;
+            uvs[C * RS + sidx(b, r)] = vo.x;
+            uvs[C * RS + sidx(b, r + 1)] = vo.y;
+        }
+    }
+    if (t < ell) return;  // uniform: t is the CTA's
+
+    // ---- 3. special positions: pass C of the inverse NTT on u (group 0) and v (group 1)
+    __syncthreads();
+    if (grp < 2) {
+        const int poly = grp;
+        u64 *gs = uvs + poly * (C * RS);
+        const uint32_t oblk = c0 + cl;
+        const ulonglong2 *__restrict__ tw = twi_all + size_t(prime) * N;
+        auto TW = [&](int sigma, int r) -> ulonglong2 {
+            return ld_keep(&tw[(1u << (L1 + sigma)) + (oblk << sigma) + (uint32_t(r) >> (LOGR - sigma))]);
+        };
+        u64 x[E];
+#pragma unroll
+        for (int e = 0; e < E; e++) x[e] = gs[sidx(cl, (g << A) + e)];
+#pragma unroll
+        for (int sg = LOGR - 1; sg >= A; sg--) {
+            const int half = 1 << (LOGR - 1 - sg);
+#pragma unroll
+            for (int e = 0; e < E; e++) {
+                if (e & half) continue;
+                gs_bfly<true>(x[e], x[e + half], TW(sg, (g << A) + e), p, np);
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < E; e++) gs[sidx(cl, (g << A) + e)] = x[e];
+        group_sync();
+#pragma unroll
+        for (int q = 0; q < E; q++) x[q] = gs[sidx(cl, g + (q << B))];
+#pragma unroll
+        for (int sg = A - 1; sg >= 0; sg--) {
+            const int half = 1 << (A - 1 - sg);
+#pragma unroll
+            for (int q = 0; q < E; q++) {
+                if (q & half) continue;
+                gs_bfly<true>(x[q], x[q + half], TW(sg, g + (q << B)), p, np);
+            }
+        }
+        u64 *dst = (poly == 0 ? F.u : F.v) + size_t(t) * N + (size_t(oblk) << L2);
+#pragma unroll
+        for (int q = 0; q < E; q++) dst[g + (q << B)] = x[q];
+    }
+}
+
 // ------------------------------------------------------------------ host side
 namespace {
 
@@ -416,10 +632,14 @@ cudaError_t run_inv(MAP m, int count, const ckks_ctx *ctx, cudaStream_t st) {
 
 }  // namespace
 
+static cudaError_t modup_ip_dispatch(const ckks_ctx *ctx, const FusedIpArgs &f, cudaStream_t st, bool set_attr);
+
 cudaError_t ntt_set_attributes(const ckks_ctx *ctx) {
     cudaError_t err = set_attributes_for<MapList>(ctx);
     if (err != cudaSuccess) return err;
-    return set_attributes_for<MapBatch>(ctx);
+    err = set_attributes_for<MapBatch>(ctx);
+    if (err != cudaSuccess || ctx->logN < 10 || ctx->logN > 17) return err;
+    return modup_ip_dispatch(ctx, FusedIpArgs{}, nullptr, true);
 }
 
 // Forward transform of a limb list (src -> dst, then in place); the optional
@@ -464,6 +684,143 @@ cudaError_t launch_ntt_batch(const ckks_ctx *ctx, const KsBatchDesc &d, int phas
     if (phase == PH_INTT_A || phase == PH_INTT_P || phase == PH_RS_INTT) return run_inv(m, count, ctx, st);
     return run_fwd(m, count, phase == PH_NTT_DOWN || phase == PH_RS_NTT, ctx, st);
 }
+
+// ------------------------------------------------------------------ fused ModUp tail launchers
+template <int LOGN>
+static size_t modup_ip_smem(int groups) {
+    constexpr int L2 = LOGN >> 1, A = (L2 + 1) / 2, B = L2 - A, TPC = 1 << B;
+    constexpr int C = 64 / TPC, RS = (1 << L2) + TPC;
+    return size_t(groups + 2) * C * RS * sizeof(u64);
+}
+
+// One launch over every extended position, 256 threads.  Two variants were
+// measured slower at N=2^16, ell=24, dnum=3: beta groups only (192 threads,
+// one launch) and separate launches for the chain positions (beta - 1 busy
+// groups) and the special positions (whose few CTAs then run as a tail).
+template <int LOGN>
+static cudaError_t launch_modup_ip_n(const ckks_ctx *ctx, const FusedIpArgs &f, cudaStream_t st, bool set_attr) {
+    constexpr int L2 = LOGN >> 1, L1 = LOGN - L2, A = (L2 + 1) / 2, B = L2 - A, TPC = 1 << B;
+    constexpr int C = 64 / TPC;
+    if (set_attr) {
+        const int smax = int(modup_ip_smem<LOGN>(4));
+        cudaError_t e = cudaFuncSetAttribute(modup_ip_kernel<LOGN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             smax);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(modup_ip_kernel<LOGN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+        return e;
+    }
+    const int beta = beta_of(ctx, f.ell);  // at most 4 (modup_ip_supported)
+    const struct {
+        int t0, count, groups;
+    } parts[1] = {{0, f.ell + ctx->k, 4}};
+    (void)beta;
+    for (const auto &pt : parts) {
+        const dim3 grid(unsigned((1 << L1) / C), unsigned(pt.count));
+        const size_t smem = modup_ip_smem<LOGN>(pt.groups);
+        if (f.compressed)
+            modup_ip_kernel<LOGN, true><<<grid, 64 * pt.groups, smem, st>>>(f, ctx->d_pinfo, ctx->d_tw_fwd, ctx->d_tw_inv,
+                                                                           ctx->L, ctx->k, ctx->alpha, pt.t0);
+        else
+            modup_ip_kernel<LOGN, false><<<grid, 64 * pt.groups, smem, st>>>(f, ctx->d_pinfo, ctx->d_tw_fwd,
+                                                                            ctx->d_tw_inv, ctx->L, ctx->k, ctx->alpha,
+                                                                            pt.t0);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+static cudaError_t modup_ip_dispatch(const ckks_ctx *ctx, const FusedIpArgs &f, cudaStream_t st, bool set_attr) {
+    switch (ctx->logN) {
+    case 10: return launch_modup_ip_n<10>(ctx, f, st, set_attr);
+    case 11: return launch_modup_ip_n<11>(ctx, f, st, set_attr);
+    case 12: return launch_modup_ip_n<12>(ctx, f, st, set_attr);
+    case 13: return launch_modup_ip_n<13>(ctx, f, st, set_attr);
+    case 14: return launch_modup_ip_n<14>(ctx, f, st, set_attr);
+    case 15: return launch_modup_ip_n<15>(ctx, f, st, set_attr);
+    case 16: return launch_modup_ip_n<16>(ctx, f, st, set_attr);
+    case 17: return launch_modup_ip_n<17>(ctx, f, st, set_attr);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+bool modup_ip_supported(const ckks_ctx *ctx, int ell) {
+    return ctx->small_primes && beta_of(ctx, ell) <= 4 && ctx->logN >= 10 && ctx->logN <= 17;
+}
+
+cudaError_t launch_modup_ip(const ckks_ctx *ctx, const FusedIpArgs &f, cudaStream_t st) {
+    ProfScope ps(ctx, K_FUSED, f.ell + ctx->k, st);
+    return modup_ip_dispatch(ctx, f, st, false);
+}
+
+// Pass S alone of the forward transform (src -> dst, lazy values): the fused
+// ModUp tail runs pass C.
+cudaError_t launch_ntt_fwd_colpass(const ckks_ctx *ctx, const NttBatch &b, cudaStream_t st) {
+    if (b.count == 0) return cudaSuccess;
+    MapList m;
+    m.b = b;
+    m.e = Epi{};
+    m.e.mode = EPI_STORE;
+    m.second = 0;
+    ProfScope ps(ctx, K_NTT_FWD, b.count, st);
+    return dispatch<false, false, false>(m, b.count, ctx, st, false);
+}
+
+// Pass S alone of the inverse transform, in place on dst (pass C ran in the
+// fused ModUp tail).
+cudaError_t launch_ntt_inv_colpass(const ckks_ctx *ctx, const NttBatch &b, cudaStream_t st) {
+    if (b.count == 0) return cudaSuccess;
+    MapList m;
+    m.b = b;
+    m.e = Epi{};
+    m.e.mode = EPI_STORE;
+    m.second = 1;
+    ProfScope ps(ctx, K_NTT_INV, b.count, st);
+    return dispatch<true, false, false>(m, b.count, ctx, st, false);
+}
+
+// ------------------------------------------------------------------ butterfly ceiling
+// Register-only throughput of the forward butterfly of the transforms (the
+// measured ceiling of their ALU roofline): every thread keeps 16 words in
+// registers and runs rounds of 4 lazy Cooley-Tukey stages (8 butterflies per
+// stage, one twiddle per stage held in registers), with no memory access
+// inside the loop.  The instruction stream is that of ct_bfly<true>; the values
+// wrap and mean nothing, so one word per thread is stored only to keep the
+// work.  Launched at the transforms' occupancy (32 warps per SM).
+__global__ void __launch_bounds__(256) bfly_peak_kernel(int rounds, const PrimeInfo *__restrict__ pinfo,
+                                                        const ulonglong2 *__restrict__ tw, u64 *__restrict__ sink) {
+    const u64 p = pinfo[0].p, np = u64(0) - p;
+    ulonglong2 w[4];
+#pragma unroll
+    for (int sg = 0; sg < 4; sg++) w[sg] = tw[1 + sg + (threadIdx.x & 7)];
+    u64 x[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) x[k] = (u64(blockIdx.x * blockDim.x + threadIdx.x) << 20) + u64(k) * 977u;
+    for (int r = 0; r < rounds; r++) {
+#pragma unroll
+        for (int sg = 0; sg < 4; sg++) {
+            const int half = 8 >> sg;
+#pragma unroll
+            for (int k = 0; k < 16; k++) {
+                if (k & half) continue;
+                ct_bfly<true>(x[k], x[k + half], w[sg], p, np);
+            }
+        }
+    }
+    u64 acc = 0;
+#pragma unroll
+    for (int k = 0; k < 16; k++) acc ^= x[k];
+    sink[size_t(blockIdx.x) * blockDim.x + threadIdx.x] = acc;
+}
+
+cudaError_t launch_bfly_peak(const ckks_ctx *ctx, int rounds, u64 *sink, cudaStream_t st, double *butterflies) {
+    const int threads = 256, blocks = ctx->sms * 4;  // 32 warps per SM
+    bfly_peak_kernel<<<blocks, threads, 0, st>>>(rounds, ctx->d_pinfo, ctx->d_tw_fwd, sink);
+    *butterflies = double(blocks) * threads * rounds * 32.0;
+    return cudaGetLastError();
+}
+
+size_t bfly_peak_sink_words(const ckks_ctx *ctx) { return size_t(ctx->sms) * 4 * 256; }
 
 // ------------------------------------------------------------------ autotuner
 // Times every CTA width of the column pass (S) and the block pass (C), forward

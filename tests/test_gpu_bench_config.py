@@ -61,3 +61,41 @@ def test_bench_step_matches_oracle(oracle_lib):
         (ra, rb), = o.hrotate(P, L, a, b, [g], [key])
         np.testing.assert_array_equal(first[c][0], ra)
         np.testing.assert_array_equal(first[c][1], rb)
+
+
+@pytest.mark.parametrize("choice", [[0, 0, 0, 0], [1, 1, 1, 1], [2, 2, 1, 0]])
+def test_concurrent_streams_equal_one_at_a_time(choice):
+    """Sixteen HRotates on 8 streams, repeated, against the same HRotates run
+    one at a time, for several NTT tile shapes.  The tensor-core conversion
+    keeps a ring of source stages per CTA; with other kernels sharing the SMs
+    (the small tile shapes put the most CTAs beside it) a stage handed back too
+    early was overwritten before it was fully read.  Every output of every step
+    must carry the one-at-a-time bits (tolerance 0)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import bench
+    from paper_2112_06396_gb300 import ckks
+
+    L = bench.L
+    primes = ckks.ckks_gen_primes(bench.BITS, bench.LOGN, L + bench.K_SP)
+    ctx = ckks.Context(bench.LOGN, primes[:L], primes[L:], bench.DNUM)
+    ctx.tune_set(choice)
+    items = bench.make_workload(ctx, 16, 0, torch)
+    one = bench.Lanes(ctx, 1, torch, ckks)
+    ref = []
+    for it in items:
+        ctx.hrotate(it["a"], it["b"], L, [it["g"]], [it["key"]], outs=[(it["oa"], it["ob"])], ws=one.ws[0])
+        torch.cuda.synchronize()
+        ref.append((it["oa"].clone(), it["ob"].clone()))
+    lanes = bench.Lanes(ctx, bench.STREAMS, torch, ckks)
+    bad = []
+    for s in range(16):
+        for it in items:
+            it["oa"].zero_()
+            it["ob"].zero_()
+        bench.step(ctx, items, lanes)
+        torch.cuda.synchronize()
+        bad += [(s, c) for c, it in enumerate(items)
+                if not (torch.equal(it["oa"], ref[c][0]) and torch.equal(it["ob"], ref[c][1]))]
+    assert not bad, f"(step, ciphertext) with wrong bits: {bad[:10]}"
+    assert ctx.poll_status()
