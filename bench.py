@@ -37,6 +37,7 @@ METRIC = "KeySwitch ops/s at N=2^16, ell=24, dnum=3"
 UNIT = "KeySwitch/s"
 WORKLOAD = "HRotate(5^r)+KeySwitch N=2^16 ell=24 k=8 dnum=3 54-bit primes"
 STREAMS = 8
+BATCH_STREAMS = 2  # the library's default split of a batched call (ckks_batch_streams)
 
 
 def load_peaks():
@@ -197,6 +198,12 @@ def measure_batched(ctx, ckks, torch, reps=5):
     outs = [(ctx.empty(ell), ctx.empty(ell)) for ell in levels]
     ws = ctx.batch_workspace(levels)
     keys = [key] * len(levels)
+    by_split = {}
+    for nst in (1, 2, 3, 4):  # ckks_batch_streams: the batch cut over this many streams
+        ctx.batch_streams(nst)
+        t = _timed(torch, lambda: ctx.keyswitch_batch(a, None, levels, None, keys, outs=outs, ws=ws), reps)
+        by_split[nst] = {"ms_per_batch": t, "keyswitch_per_s": len(levels) / t * 1e3}
+    ctx.batch_streams(BATCH_STREAMS)
     t_batch = _timed(torch, lambda: ctx.keyswitch_batch(a, None, levels, None, keys, outs=outs, ws=ws), reps)
     ws1 = ctx.workspace(ckks.OP_KEYSWITCH, L)
 
@@ -248,8 +255,10 @@ def measure_batched(ctx, ckks, torch, reps=5):
     return {"shape": "64 KeySwitch, ell uniform in {4..24} (seeded), N=2^16, k=8, dnum=3, one shared key",
             "levels_sum": sum(levels),
             "batched": {"ms_per_batch": t_batch, "keyswitch_per_s": n / t_batch * 1e3,
+                        "batch_streams": BATCH_STREAMS,
                         "launches": sum(v[1] for v in prof.values()),
                         "kernel_ms": {k: v[0] for k, v in prof.items() if v[1]}},
+            "by_batch_streams": by_split,
             "graph_replay": {"ms_per_batch": t_graph, "keyswitch_per_s": n / t_graph * 1e3},
             "compressed_key": {"ms_per_batch": t_comp, "keyswitch_per_s": n / t_comp * 1e3,
                                "key_bytes": key_b_bytes},

@@ -125,6 +125,7 @@ _SIGS = {
                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "ckks_server_selftest_timeout": (_i, [_vp, ctypes.c_uint32]),
     "ckks_fuse_select": (_i, [_vp, _i, ctypes.POINTER(_i)]),
+    "ckks_batch_streams": (_i, [_vp, _i]),
     "ckks_butterfly_peak_sink_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
     "ckks_butterfly_peak": (_i, [_vp, _i, _vp, _vp, ctypes.POINTER(ctypes.c_float),
                                  ctypes.POINTER(ctypes.c_double)]),
@@ -359,6 +360,10 @@ class Context:
         """Launch the bounded-wait self-test (ckks_selftest_bounded_wait): a wait
         on a barrier nothing arrives on, which gives up after limit_us."""
         _check(lib().ckks_selftest_bounded_wait(self._h, int(limit_us), _stream(stream)), self._h)
+
+    def batch_streams(self, n):
+        """Streams a batched call is split over (ckks_batch_streams, 1 .. 4)."""
+        _check(lib().ckks_batch_streams(self._h, int(n)))
 
     def fuse_modup(self, on=True):
         """Run single KeySwitches and one-rotation HRotates through the fused

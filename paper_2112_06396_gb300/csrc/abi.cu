@@ -447,10 +447,20 @@ extern "C" int ckks_ctx_create(const ckks_params *prm, int device, ckks_ctx **ou
         if (err == cudaSuccess && u.n) err = cudaMemcpy(u.dst, u.src, u.n, cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemset(c->d_status, 0, sizeof(int));
     if (err == cudaSuccess) err = ntt_set_attributes(c);
+    for (int i = 0; i < ckks_ctx::kAux && err == cudaSuccess; ++i) {
+        err = cudaStreamCreateWithFlags(&c->aux[i], cudaStreamNonBlocking);
+        if (err == cudaSuccess) err = cudaEventCreateWithFlags(&c->join_ev[i], cudaEventDisableTiming);
+    }
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming);
     // the caller's current device is restored; a failure to do so fails the call
     const cudaError_t back = cudaSetDevice(prev);
     if (err == cudaSuccess) err = back;
     if (err != cudaSuccess) {
+        for (int i = 0; i < ckks_ctx::kAux; ++i) {
+            if (c->aux[i]) cudaStreamDestroy(c->aux[i]);
+            if (c->join_ev[i]) cudaEventDestroy(c->join_ev[i]);
+        }
+        if (c->fork_ev) cudaEventDestroy(c->fork_ev);
         cudaFree(c->d_block);
         delete c;
         return CKKS_ECUDA;
@@ -470,6 +480,11 @@ extern "C" int ckks_ctx_destroy(ckks_ctx *c) {
         c->prof_pool.push_back(r.b);
     }
     for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
+    for (int i = 0; i < ckks_ctx::kAux; ++i) {
+        if (c->aux[i]) cudaStreamDestroy(c->aux[i]);
+        if (c->join_ev[i]) cudaEventDestroy(c->join_ev[i]);
+    }
+    if (c->fork_ev) cudaEventDestroy(c->fork_ev);
     cudaFree(c->d_block);  // a device pointer is freed whichever device is current
     const cudaError_t back = cudaSetDevice(prev);
     if (err == cudaSuccess) err = back;
@@ -1194,9 +1209,52 @@ static int batch_back(ckks_ctx *ctx, const KsBatchDesc &d, bool rescale, cudaStr
     return CKKS_OK;
 }
 
-// Runs a batch in groups of kMaxCts entries.  An entry's workspace is its ws
-// when set, else the next entry_ws_words region of w (batch order).
+static int run_batch_on(ckks_ctx *ctx, int n, const BatchEntry *e, u64 *w, cudaStream_t st, int *status);
+
+// Runs a batch.  An entry's workspace is its ws when set, else the next
+// entry_ws_words region of w (batch order).  With ctx->batch_split > 1 and at
+// least four entries per part, the entries are cut into that many parts of
+// about equal limb counts, run as independent batches on the caller's stream
+// and ctx->batch_split - 1 more, forked from and joined back to the caller's
+// stream by events: the parts' steps overlap on the GPU (a transform of one
+// part beside the inner product of another).  Same bits as unsplit.
 int ckks::run_batch(ckks_ctx *ctx, int n, const BatchEntry *e, u64 *w, cudaStream_t st, int *status) {
+    const int parts = std::min(ctx->batch_split, n / 4);
+    std::unique_lock<std::mutex> lock(ctx->aux_mu, std::try_to_lock);
+    if (parts < 2 || !lock.owns_lock()) return run_batch_on(ctx, n, e, w, st, status);
+    // every entry's workspace fixed before the cut
+    std::vector<BatchEntry> all(e, e + n);
+    long long total = 0;
+    for (int c = 0; c < n; ++c) {
+        if (all[c].ws == nullptr) {
+            all[c].ws = w;
+            w += entry_ws_words(ctx, all[c].kind, all[c].ell);
+        }
+        total += all[c].ell;
+    }
+    CK(cudaEventRecord(ctx->fork_ev, st));
+    for (int i = 1; i < parts; ++i) CK(cudaStreamWaitEvent(ctx->aux[i - 1], ctx->fork_ev, 0));
+    int c0 = 0;
+    long long done = 0;
+    for (int i = 0; i < parts; ++i) {
+        int c1 = c0;
+        if (i == parts - 1) c1 = n;
+        else
+            while (c1 < n && (done + all[c1].ell) * parts <= total * (i + 1)) done += all[c1++].ell;
+        if (c1 == c0 && c1 < n) done += all[c1++].ell;
+        cudaStream_t s = i == 0 ? st : ctx->aux[i - 1];
+        RC(run_batch_on(ctx, c1 - c0, all.data() + c0, nullptr, s, status));
+        c0 = c1;
+    }
+    for (int i = 1; i < parts; ++i) {
+        CK(cudaEventRecord(ctx->join_ev[i - 1], ctx->aux[i - 1]));
+        CK(cudaStreamWaitEvent(st, ctx->join_ev[i - 1], 0));
+    }
+    return CKKS_OK;
+}
+
+// Runs a batch in groups of kMaxCts entries on one stream.
+static int run_batch_on(ckks_ctx *ctx, int n, const BatchEntry *e, u64 *w, cudaStream_t st, int *status) {
     for (int c0 = 0; c0 < n; c0 += kMaxCts) {
         KsBatchDesc d{};
         d.n = std::min(n - c0, kMaxCts);
@@ -1702,6 +1760,12 @@ extern "C" int ckks_butterfly_peak(ckks_ctx *ctx, int rounds, void *sink, ckks_s
     cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     CK(err);
+    return CKKS_OK;
+}
+
+extern "C" int ckks_batch_streams(ckks_ctx *ctx, int nstreams) {
+    if (ctx == nullptr || nstreams < 1 || nstreams > ckks_ctx::kAux + 1) return CKKS_EINVAL;
+    ctx->batch_split = nstreams;
     return CKKS_OK;
 }
 

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstddef>
+#include <mutex>
 #include <unordered_map>
 #include <vector>
 
@@ -20,6 +21,14 @@ struct ckks_ctx {
     bool tc_lazy;                     // its outputs stay below 8t without a final reduction
     bool fuse_on = false;             // single KeySwitch / one-rotation HRotate through modup_ip_kernel
                                       // (ckks_fuse_select)
+    // Batched calls split over `batch_split` streams: the caller's and
+    // batch_split - 1 of these, forked and joined by events.  One call at a
+    // time holds them (aux_mu); a call that finds them taken runs unsplit.
+    static constexpr int kAux = 3;
+    int batch_split = 2;
+    cudaStream_t aux[kAux] = {};
+    cudaEvent_t fork_ev = nullptr, join_ev[kAux] = {};
+    std::mutex aux_mu;
     std::vector<u64> primes;          // L + k: q_0..q_{L-1}, p_0..p_{k-1}
     // device tables (one allocation)
     void *d_block;

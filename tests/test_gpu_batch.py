@@ -174,6 +174,63 @@ def test_batch_captured_in_a_cuda_graph(cfg1):
         assert torch.equal(ga, wa) and torch.equal(gb, wb)
 
 
+def test_batch_split_over_streams(cfg1):
+    """ckks_batch_streams: a batch of 16 KeySwitch / HRotate entries at uneven
+    levels cut over 1 to 4 streams gives the same bits every time, equal to the
+    oracle on sampled entries, and a split batch captured in a CUDA graph (the
+    fork and join of the streams become graph edges) replays to the same bits."""
+    S = cfg1
+    P, ctx = S.P, S.ctx
+    levels = [6, 2, 5, 3, 6, 1, 4, 6, 2, 5, 3, 6, 1, 4, 5, 6]
+    g = 5
+    relin = S.key(0, "gpu/split/relin")[0]
+    rot = S.key(g, "gpu/split/rot")[0]
+    cts = [S.ct(ell, f"gpu/split/{i}") for i, ell in enumerate(levels)]
+    da = [dev(a) for a, _ in cts]
+    db = [dev(b) if i % 3 == 1 else None for i, (_, b) in enumerate(cts)]
+    gal = [g if i % 3 == 1 else 1 for i in range(len(levels))]
+    keys = [dev(rot) if i % 3 == 1 else dev(relin) for i in range(len(levels))]
+    results = []
+    try:
+        for nst in (1, 2, 3, 4):
+            ctx.batch_streams(nst)
+            outs = ctx.keyswitch_batch(da, db, levels, gal, keys)
+            results.append([(host(u), host(v)) for u, v in outs])
+        for r in results[1:]:
+            for i, ((u0, v0), (u, v)) in enumerate(zip(results[0], r)):
+                np.testing.assert_array_equal(u, u0, err_msg=f"entry {i}")
+                np.testing.assert_array_equal(v, v0, err_msg=f"entry {i}")
+        for i in (0, 1, 5, 13):
+            a, b = cts[i]
+            if i % 3 == 1:
+                ((ra, rb),) = S.o.hrotate(P, levels[i], a, b, [g], [rot])
+            else:
+                ra, rb = S.o.keyswitch(P, levels[i], a, relin)
+            np.testing.assert_array_equal(results[0][i][0], ra, err_msg=f"entry {i} vs oracle")
+            np.testing.assert_array_equal(results[0][i][1], rb, err_msg=f"entry {i} vs oracle")
+        ctx.batch_streams(4)
+        outs = [(ctx.empty(ell), ctx.empty(ell)) for ell in levels]
+        ws = ctx.batch_workspace(levels)
+        st = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(st):
+            ctx.keyswitch_batch(da, db, levels, gal, keys, outs=outs, ws=ws, stream=st)  # warm-up
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=st):
+            ctx.keyswitch_batch(da, db, levels, gal, keys, outs=outs, ws=ws, stream=st)
+        for o in outs:
+            o[0].zero_()
+            o[1].zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        for i, (u, v) in enumerate(outs):
+            np.testing.assert_array_equal(host(u), results[0][i][0], err_msg=f"graph entry {i}")
+            np.testing.assert_array_equal(host(v), results[0][i][1], err_msg=f"graph entry {i}")
+    finally:
+        ctx.batch_streams(2)
+
+
 @pytest.mark.parametrize("which", ["cfg1", "cfg_odd"])
 def test_hrotate_batch_hoisted_rotations(request, which):
     """Several ciphertexts at uneven levels, each rotated by several Galois
