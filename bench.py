@@ -528,6 +528,13 @@ def measure_other_rows(ctx, ckks, torch, reps=5):
 
     per_level = [_timed(torch, lambda i=i: level(i), reps) for i in range(3)]
     c2s_ms = _timed(torch, lambda: [level(i) for i in range(3)], reps)
+    # where the time of the first level goes (measurement hook, one stream)
+    ctx.profile(True)
+    ctx.profile_reset()
+    level(0)
+    torch.cuda.synchronize()
+    prof_l0 = {k: {"ms": v[0], "launches": v[1]} for k, v in ctx.profile_read().items() if v[1]}
+    ctx.profile(False)
     # the same three levels with every rotation key compressed (Sec. 5.3): rows b_j
     # only, a_j regenerated from a seed inside the kernels
     full_levels = levels
@@ -564,6 +571,7 @@ def measure_other_rows(ctx, ckks, torch, reps=5):
         "ptmatvecmult": {"shape": "CoeffToSlot-shaped: 3 levels at ell 24, 23, 22; 8 baby x 4 giant steps, "
                                   "stride 32^level, 32 diagonals and 10 keys per level (30 keys), rescaled",
                          "ms_per_level": per_level, "ms_coeff_to_slot": c2s_ms,
+                         "level0_kernels": prof_l0,
                          "coeff_to_slot_per_s": 1e3 / c2s_ms,
                          "compressed_keys": {"ms_per_level": per_level_c, "ms_coeff_to_slot": c2s_ms_c,
                                              "coeff_to_slot_per_s": 1e3 / c2s_ms_c,
@@ -801,6 +809,8 @@ def run_gpu(args, rank, world, local_rank):
     primes = ckks.ckks_gen_primes(BITS, LOGN, L + K_SP)
     ctx = ckks.Context(LOGN, primes[:L], primes[L:], DNUM, device=local_rank)
     tune_choice, tune_times = [0, 0, 0, 0], []
+    if args.fuse:
+        ctx.fuse_modup(True)
     if not args.no_tune:
         tune_choice, tune_times = ctx.autotune(limbs=128)  # NTT tile shapes for this GPU (ckks_autotune)
     torch.cuda.synchronize()
@@ -970,7 +980,7 @@ def run_gpu(args, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded residues; keys from a seeded ternary secret)",
-            "config": {**base_config(C), "parallelism": f"replicas x{world}",
+            "config": {**base_config(C), "parallelism": f"replicas x{world}", "fused_dataflow": bool(args.fuse),
                        "ntt_tile_shapes": {"choice": tune_choice, "ms": [round(t, 4) for t in tune_times],
                                            "legend": "[column pass <=48 limbs, column pass larger, block pass <=48, "
                                                      "block pass larger]; 0 default width, 1 half, 2 double"}},
@@ -1051,6 +1061,36 @@ def run_profile_batch(args):
     return 0
 
 
+def run_profile_pmv(args):
+    """A small case for ncu: `--profile-pmv` runs the first CoeffToSlot-shaped
+    PtMatVecMult level (ell=24, 8 baby x 4 giant steps, 32 diagonals, 10 keys)
+    `--warmup` + `--steps` times; nothing is printed but a completion line."""
+    import torch
+
+    from paper_2112_06396_gb300 import ckks
+
+    primes = ckks.ckks_gen_primes(BITS, LOGN, L + K_SP)
+    ctx = ckks.Context(LOGN, primes[:L], primes[L:], DNUM)
+    N = ctx.N
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(ctx.device)
+    nb, ng = 8, 4
+    s = dev(synth.ternary(N, "bench/rows/s"))
+    g_baby = [1] + [pow(5, i, 2 * N) for i in range(1, nb)]
+    g_giant = [1] + [pow(5, t * nb, 2 * N) for t in range(1, ng)]
+    kb = [None] + [_keygen(ctx, torch, s, g, f"bench/rows/l0/kb{i}") for i, g in enumerate(g_baby) if i > 0]
+    kg = [None] + [_keygen(ctx, torch, s, g, f"bench/rows/l0/kg{t}") for t, g in enumerate(g_giant) if t > 0]
+    diags = [dev(synth.uniform_residues(ctx.ext_primes(L), N, f"bench/rows/l0/M{d}")) for d in range(nb * ng)]
+    a = dev(synth.uniform_residues(ctx.q, N, "bench/rows/a"))
+    b = dev(synth.uniform_residues(ctx.q, N, "bench/rows/b"))
+    oa, ob = ctx.empty(L - 1), ctx.empty(L - 1)
+    ws = ctx.workspace(ckks.OP_PTMATVEC, L, ng)
+    for _ in range(args.warmup + args.steps):
+        ctx.ptmatvecmult(a, b, L, nb, ng, g_baby, g_giant, kb, kg, diags, True, oa, ob, ws)
+    torch.cuda.synchronize()
+    print(f"profile case done: {args.warmup + args.steps} PtMatVecMult levels at ell={L}", flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1066,6 +1106,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-rows", action="store_true", help="skip the Rescale / PtMatVecMult side measurements")
     ap.add_argument("--no-tune", action="store_true", help="keep the default NTT tile shapes (no autotuning)")
+    ap.add_argument("--profile-pmv", action="store_true",
+                    help="profiling case: only run PtMatVecMult levels (no JSON line)")
+    ap.add_argument("--fuse", action="store_true",
+                    help="run the headline's HRotates through the fused ModUp tail + KSKInnerProd kernel")
     ap.add_argument("--profile-batch", type=int, default=0,
                     help="profiling case: only run this many batched KeySwitches at uneven levels (no JSON line)")
     args = ap.parse_args()
@@ -1080,6 +1124,8 @@ def main():
         args.warmup = 3
     if args.profile_batch:
         return run_profile_batch(args)
+    if args.profile_pmv:
+        return run_profile_pmv(args)
     return run_gpu(args, rank, world, local_rank)
 
 

@@ -279,7 +279,12 @@ int ckks_newmult_sum(ckks_ctx *ctx, int n, const uint64_t *const *d_a1, const ui
  * basis, (c_a, c_b) = ModDown(acc), rotated by g_giant[t] (Algorithm 3) when
  * t > 0; the sum over t is rescaled by q_{ell-1} when rescale != 0.  Output
  * [ell'][N] with ell' = ell-1 if rescale else ell.  All arrays are host
- * arrays of device pointers / values.  Workspace CKKS_OP_PTMATVEC(ng). */
+ * arrays of device pointers / values.  Workspace CKKS_OP_PTMATVEC(ng).
+ * With at most 8 giant steps, 64 diagonals and 4 digits, one kernel forms
+ * every giant step's accumulator (each baby-step key and diagonal read once)
+ * and the giant steps t >= 1 run on the context's streams (as for
+ * ckks_batch_streams: forked from and joined back to `stream` by events, or on
+ * `stream` itself when another call holds them). */
 int ckks_ptmatvecmult(ckks_ctx *ctx, const uint64_t *d_a, const uint64_t *d_b, int level, int nb, int ng,
                       const uint32_t *g_baby, const uint32_t *g_giant, const uint64_t *const *key_baby,
                       const uint64_t *const *key_giant, const uint64_t *const *d_diag, int rescale,

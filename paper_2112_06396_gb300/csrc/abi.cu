@@ -876,7 +876,7 @@ static HrLayout hr_layout(const ckks_ctx *c, int ell) {
 }
 
 struct PmvLayout {
-    size_t ext, acc, tmp, ct, res, rot, total;
+    size_t ext, acc, tmp, ct, res, rot, chain, chain_words, total;
 };
 // acc holds one (a, b) accumulator pair per giant step when every giant step
 // runs in one launch (pmv_all_kernel), else one pair reused per giant step.
@@ -891,6 +891,12 @@ static PmvLayout pmv_layout(const ckks_ctx *c, int ell, int ng) {
     o.res = o.ct + size_t(2) * ell * N;
     o.rot = o.res + size_t(2) * ell * N;
     o.total = o.rot + (ng > 1 ? words_rotate(c, ell) : 0);
+    // every giant step t >= 1 of the one-launch path has its own ModDown scratch,
+    // rotated input, rotated output and Rotate workspace, so the giant steps can
+    // run on separate streams
+    o.chain = o.total;
+    o.chain_words = (std::max(size_t(ell), words_moddown2(c, ell)) + size_t(4) * ell) * N + words_rotate(c, ell);
+    if (nacc > 1) o.total = o.chain + size_t(ng - 1) * o.chain_words;
     return o;
 }
 
@@ -1556,18 +1562,46 @@ extern "C" int ckks_ptmatvecmult(ckks_ctx *ctx, const uint64_t *a, const uint64_
         }
         for (int d = 0; d < nb * ng; ++d) pa.diag[d] = diag[d];
         CK(launch_pmv_all(ctx, pa, st));
+        // The giant steps are independent until they are summed: step 0 is
+        // ModDown'ed into res on the caller's stream; step t >= 1 (ModDown, then
+        // Rotate by its giant element into its own output) runs on a context
+        // stream when the call holds them (forked and joined by events), else on
+        // the caller's stream; then res += the rotated steps.
         const u64 *noadd[2] = {nullptr, nullptr};
+        std::unique_lock<std::mutex> lock(ctx->aux_mu, std::try_to_lock);
+        const bool split = lock.owns_lock() && ng > 1;
+        if (split) {
+            CK(cudaEventRecord(ctx->fork_ev, st));
+            for (int i = 0; i < std::min(ng - 1, ckks_ctx::kAux); ++i)
+                CK(cudaStreamWaitEvent(ctx->aux[i], ctx->fork_ev, 0));
+        }
+        PolySum sum{};
+        sum.acc[0] = res_a;
+        sum.acc[1] = res_b;
         for (int t = 0; t < ng; ++t) {
             const u64 *in[2] = {pa.acc_a[t], pa.acc_b[t]};
             if (t == 0) {
                 u64 *out[2] = {res_a, res_b};
                 RC(moddown_polys(ctx, ell, 2, in, out, noadd, 1, 0, w + lo.tmp, w + lo.tmp + size_t(2) * k * N, st));
-            } else {
-                u64 *out[2] = {ct_a, ct_b};
-                RC(moddown_polys(ctx, ell, 2, in, out, noadd, 1, 0, w + lo.tmp, w + lo.tmp + size_t(2) * k * N, st));
-                RC(rotate_core(ctx, ct_a, ct_b, ell, g_giant[t], key_giant[t], res_a, res_b, 1, w + lo.rot, st));
+                continue;
             }
+            u64 *ch = w + lo.chain + size_t(t - 1) * lo.chain_words;
+            u64 *tmp = ch, *cta = tmp + std::max(size_t(ell), words_moddown2(ctx, ell)) * N;
+            u64 *ctb = cta + size_t(ell) * N, *oa_t = ctb + size_t(ell) * N, *ob_t = oa_t + size_t(ell) * N;
+            u64 *rws = ob_t + size_t(ell) * N;
+            cudaStream_t s2 = split ? ctx->aux[(t - 1) % ckks_ctx::kAux] : st;
+            u64 *out[2] = {cta, ctb};
+            RC(moddown_polys(ctx, ell, 2, in, out, noadd, 1, 0, tmp, tmp + size_t(2) * k * N, s2));
+            RC(rotate_core(ctx, cta, ctb, ell, g_giant[t], key_giant[t], oa_t, ob_t, 0, rws, s2));
+            sum.in[0][sum.n] = oa_t;
+            sum.in[1][sum.n++] = ob_t;
         }
+        if (split)
+            for (int i = 0; i < std::min(ng - 1, ckks_ctx::kAux); ++i) {
+                CK(cudaEventRecord(ctx->join_ev[i], ctx->aux[i]));
+                CK(cudaStreamWaitEvent(st, ctx->join_ev[i], 0));
+            }
+        CK(launch_poly_sum(ctx, sum, ell, st));
     }
     for (int t = 0; t < ng && !pmv_all_supported(ctx, ell, nb, ng); ++t) {
         PmvArgs pa{};

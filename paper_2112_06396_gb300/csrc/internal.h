@@ -203,6 +203,13 @@ struct PmvAllArgs {
     uint8_t compressed[kMaxRot];
 };
 bool pmv_all_supported(const ckks_ctx *ctx, int ell, int nb, int ng);
+// acc[p] += sum_j in[p][j] (mod each prime) over ell limbs, p = 0, 1
+struct PolySum {
+    u64 *acc[2];
+    const u64 *in[2][kMaxGiant];
+    int n;
+};
+cudaError_t launch_poly_sum(const ckks_ctx *ctx, const PolySum &S, int ell, cudaStream_t st);
 cudaError_t launch_pmv_all(const ckks_ctx *ctx, const PmvAllArgs &a, cudaStream_t st);
 
 cudaError_t launch_automorph(const ckks_ctx *ctx, const u64 *in, u64 *out, int nlimbs, uint32_t g, cudaStream_t st);

@@ -480,7 +480,7 @@ cudaError_t launch_pmv_accum(const ckks_ctx *ctx, const PmvArgs &a, cudaStream_t
 // Automorph gather stays inside aligned 32-slot blocks): the NG x 2 128-bit
 // accumulators live in registers.  Grid (slot tile, extended position).
 template <int BETA, int NG, bool COMP>
-__global__ void __launch_bounds__(256) pmv_all_kernel(const __grid_constant__ PmvAllArgs A,
+__global__ void __launch_bounds__(256, 3) pmv_all_kernel(const __grid_constant__ PmvAllArgs A,
                                                       const PrimeInfo *__restrict__ pinfo,
                                                       const ulonglong2 *__restrict__ Pmod, int logN, int L, int k,
                                                       int alpha) {
@@ -595,6 +595,35 @@ cudaError_t launch_pmv_all(const ckks_ctx *ctx, const PmvAllArgs &a, cudaStream_
 #undef CKKS_PMV_B
 #undef CKKS_PMV_G
 #undef CKKS_PMV
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ sum of polynomials
+// acc[i] = (acc[i] + sum_j in_j[i]) mod q_i over the first ell primes, for two
+// polynomials at once (the giant steps of PtMatVecMult computed apart).
+__global__ void __launch_bounds__(256) poly_sum_kernel(const __grid_constant__ PolySum S,
+                                                       const PrimeInfo *__restrict__ pinfo, int logN) {
+    const size_t N = size_t(1) << logN;
+    const uint32_t n0 = (blockIdx.x * blockDim.x + threadIdx.x) * 2;
+    if (n0 >= N) return;
+    const int i = blockIdx.y, poly = blockIdx.z;
+    const u64 p = pinfo[i].p;
+    const size_t o = size_t(i) * N + n0;
+    ulonglong2 a = ld2(S.acc[poly] + o);
+    for (int j = 0; j < S.n; j++) {
+        const ulonglong2 x = ld2(S.in[poly][j] + o);
+        a.x = add_mod(a.x, x.x, p);
+        a.y = add_mod(a.y, x.y, p);
+    }
+    st2(S.acc[poly] + o, a);
+}
+
+cudaError_t launch_poly_sum(const ckks_ctx *ctx, const PolySum &S, int ell, cudaStream_t st) {
+    if (S.n == 0) return cudaSuccess;
+    const int threads = 256;
+    dim3 grid(unsigned((ctx->N / 2 + threads - 1) / threads), unsigned(ell), 2u);
+    ProfScope ps(ctx, K_ELEMWISE, 2.0 * ell * (S.n + 1), st);
+    poly_sum_kernel<<<grid, threads, 0, st>>>(S, ctx->d_pinfo, ctx->logN);
     return cudaGetLastError();
 }
 
