@@ -374,10 +374,12 @@ int ckks_bconv_select(ckks_ctx *ctx, int tensor_cores, int *available);
 int ckks_fuse_select(ckks_ctx *ctx, int on, int *available);
 
 /* Streams of a batched call (no counterpart in the paper): the batched calls
- * (ckks_keyswitch_batch, ckks_hrotate_batch's rotations run unsplit,
- * ckks_mult_batch, ckks_newmult_batch, the serving loop's batches) cut a batch
- * of at least 4 * nstreams entries into nstreams parts of about equal limb
- * counts and run them on the caller's stream and nstreams - 1 streams of the
+ * (ckks_keyswitch_batch, ckks_mult_batch, ckks_newmult_batch, the serving
+ * loop's batches) cut a batch of at least 4 * nstreams entries into nstreams
+ * parts of about equal limb counts (ckks_hrotate_batch: its ciphertexts, each
+ * with all its rotations, into parts of about equal rotation counts, at least
+ * four rotations per part) and run them on the caller's stream and
+ * nstreams - 1 streams of the
  * context, forked from and joined back to the caller's stream with events, so
  * that the parts' pipeline steps overlap (a transform of one part beside the
  * inner product of another).  The call stays asynchronous on the caller's

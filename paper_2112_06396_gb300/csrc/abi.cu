@@ -1399,16 +1399,41 @@ extern "C" int ckks_hrotate_batch(ckks_ctx *ctx, int n, const uint64_t *const *a
         for (int i = 0; i < cnt; ++i) d.ct[i] = v[i];
         return d;
     };
-    for (int c0 = 0; c0 < n; c0 += kMaxCts) {  // ModUp of every ciphertext, once
-        const KsBatchDesc d = desc(owners.data() + c0, std::min(n - c0, kMaxCts));
-        CK(launch_ntt_batch(ctx, d, PH_INTT_A, st));
-        CK(launch_bconv_batch(ctx, d, GM_MODUP, st));
-        CK(launch_ntt_batch(ctx, d, PH_NTT_UP, st));
+    // ciphertexts [c0, c1) with their rotations [i0, i1): ModUp of each
+    // ciphertext once, then every rotation's inner product and ModDown
+    auto run_part = [&](int c0, int c1, int i0, int i1, cudaStream_t s2) -> int {
+        for (int c = c0; c < c1; c += kMaxCts) {
+            const KsBatchDesc d = desc(owners.data() + c, std::min(c1 - c, kMaxCts));
+            CK(launch_ntt_batch(ctx, d, PH_INTT_A, s2));
+            CK(launch_bconv_batch(ctx, d, GM_MODUP, s2));
+            CK(launch_ntt_batch(ctx, d, PH_NTT_UP, s2));
+        }
+        for (int i = i0; i < i1; i += kMaxCts) {
+            const KsBatchDesc d = desc(all.data() + i, std::min(i1 - i, kMaxCts));
+            CK(launch_inner_prod_batch(ctx, d, s2));
+            RC(batch_back(ctx, d, false, s2));
+        }
+        return CKKS_OK;
+    };
+    // as in run_batch: with ctx->batch_split > 1 and at least four rotations
+    // per part, the ciphertexts (each with all its rotations) are cut into parts
+    // of about equal rotation counts on the context's streams
+    const int parts = std::min({ctx->batch_split, n, m / 4});
+    std::unique_lock<std::mutex> lock(ctx->aux_mu, std::try_to_lock);
+    if (parts < 2 || !lock.owns_lock()) return run_part(0, n, 0, m, st);
+    CK(cudaEventRecord(ctx->fork_ev, st));
+    for (int i = 1; i < parts; ++i) CK(cudaStreamWaitEvent(ctx->aux[i - 1], ctx->fork_ev, 0));
+    int c0 = 0, i0 = 0;
+    for (int pt = 0; pt < parts; ++pt) {
+        int c1 = c0, i1 = i0;
+        while (c1 < n && (c1 == c0 || pt == parts - 1 || (i1 + nrot[c1]) * parts <= m * (pt + 1))) i1 += nrot[c1++];
+        RC(run_part(c0, c1, i0, i1, pt == 0 ? st : ctx->aux[pt - 1]));
+        c0 = c1;
+        i0 = i1;
     }
-    for (int i0 = 0; i0 < m; i0 += kMaxCts) {  // every rotation: inner product and ModDown
-        const KsBatchDesc d = desc(all.data() + i0, std::min(m - i0, kMaxCts));
-        CK(launch_inner_prod_batch(ctx, d, st));
-        RC(batch_back(ctx, d, false, st));
+    for (int i = 1; i < parts; ++i) {
+        CK(cudaEventRecord(ctx->join_ev[i - 1], ctx->aux[i - 1]));
+        CK(cudaStreamWaitEvent(st, ctx->join_ev[i - 1], 0));
     }
     return CKKS_OK;
 }
