@@ -309,7 +309,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // bconv_split_kernel: the representative matters), group KG-1 the
         // bias entry 2048, the rest zeros
         const int pt = tid - kTcEpiWarps * 32;
-        const int m = pt & 127, par = pt >> 7;  // row m, groups g = 2i + par
+        // row m; the groups g = 2i + par of kPars parities starting at par0
+        constexpr int kPars = 256 / (kTcProdWarps * 32);
+        const int m = pt & 127, par0 = (pt >> 7) * kPars;
         int it = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
             const int s = it & 1, xs = it % kTcXStages;
@@ -318,14 +320,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 give_up();
                 break;
             }
-            u64 x[KG / 2];
             const u64 *xrow = Xs + size_t(xs) * (KG - 1) * 128 + m;
+            uint4 *row = As + s * (128 * KG) + (m >> 3) * (KG * 8) + (m & 7);
+#pragma unroll
+            for (int pr = 0; pr < kPars; ++pr) {
+            const int par = par0 + pr;
+            u64 x[KG / 2];
 #pragma unroll
             for (int i = 0; i < KG / 2; ++i) {
                 const int g = 2 * i + par;
                 x[i] = g < n_src ? xrow[g * 128] : 0;
             }
-            uint4 *row = As + s * (128 * KG) + (m >> 3) * (KG * 8) + (m & 7);
 #pragma unroll
             for (int i = 0; i < KG / 2; ++i) {
                 const int g = 2 * i + par;
@@ -340,6 +345,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     v.x = 0x6800u;  // f16 2048
                 }
                 row[g * 8] = v;
+            }
             }
             tc::fence_async_smem();
             // the source stage is handed back only now, after every value read

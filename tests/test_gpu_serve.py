@@ -168,16 +168,16 @@ def test_memory_admission_limits_what_runs(pool):
     srv.close()
 
 
-def test_serving_mix_ring_degree_n15_against_the_oracle(oracle_lib):
-    """A served mix at N = 2^15 with 54-bit primes and levels up to 12 (L = 12,
-    k = 4, dnum = 3) beside N = 2^12 requests: every request equals its single
-    call, and a sample of each operation (the largest level first) equals the
-    oracle."""
+def test_serving_config_shapes_against_the_oracle(oracle_lib):
+    """The serving configuration's shapes: N = 2^16 and 2^15, L = 24, k = 8,
+    dnum = 3, 54-bit primes, levels uniform in {3..24}, a mixed served run: every
+    request equals its single call, and one request of each operation at
+    N = 2^16 (the largest level first) and one at N = 2^15 equal the oracle."""
     from paper_2112_06396_gb300 import serving
 
-    big = Pool(oracle_lib, shapes=((15, 12, 4, 3, 54), (12, 12, 4, 3, 54)), tag="gpu/serve15")
-    srv, handles = _server(big, 1 << 32, 16, 3)
-    reqs = big.requests(24, "gpu/serve15/mix", min_level=3)
+    big = Pool(oracle_lib, shapes=((16, 24, 8, 3, 54), (15, 24, 8, 3, 54)), tag="gpu/serve16")
+    srv, handles = _server(big, 1 << 34, 16, 3)
+    reqs = big.requests(24, "gpu/serve16/mix", min_level=3)
     for r in reqs:
         r["key"] = handles[r["ctx"]][r["kkey"]]
     results, stats = serving.replay(srv, reqs)
@@ -190,12 +190,13 @@ def test_serving_mix_ring_degree_n15_against_the_oracle(oracle_lib):
         ra, rb = big.alone(r)
         np.testing.assert_array_equal(ga, ra, err_msg=f"request {i} vs alone")
         np.testing.assert_array_equal(gb, rb, err_msg=f"request {i} vs alone")
-        if r["ctx"] == 0 and checked.get(r["op"], 0) < 1:
+        tag = r["op"] if r["ctx"] == 0 else "n15"
+        if checked.get(tag, 0) < 1:
             oa, ob = big.oracle(r)
             np.testing.assert_array_equal(ga, oa, err_msg=f"request {i} ({r['op']}, ell {r['level']}) vs oracle")
             np.testing.assert_array_equal(gb, ob, err_msg=f"request {i} vs oracle")
-            checked[r["op"]] = checked.get(r["op"], 0) + 1
-    assert len(checked) >= 3, checked
+            checked[tag] = 1
+    assert len(checked) >= 4, checked
     srv.close()
 
 
