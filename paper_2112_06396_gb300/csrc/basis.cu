@@ -452,7 +452,21 @@ static void launch_tc_kg(const ckks_ctx *ctx, const GMAP &gm, int ngroups, int c
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     const int tiles = ctx->N / 128;
     const int rows = ngroups * chunks;
-    const int per = std::max(1, std::min(tiles, ctx->sms / rows));
+    // CTAs per (group, chunk): each SM runs one CTA at a time and a CTA its tiles
+    // one after the other, so the launch takes about waves * ceil(tiles / per)
+    // tile times plus a fixed cost (B image, tensor memory, pipeline fill: about
+    // two tiles) per wave; pick the count that minimises it (a batch has more
+    // (group, chunk) rows than SMs, a single operation a few)
+    int per = 1;
+    long best = -1;
+    for (int c = 1; c <= std::min(tiles, 256); ++c) {
+        const long waves = (long(rows) * c + ctx->sms - 1) / ctx->sms;
+        const long cost = waves * ((tiles + c - 1) / c + 2);
+        if (best < 0 || cost <= best) {  // ties: more CTAs
+            best = cost;
+            per = c;
+        }
+    }
     const dim3 grid(static_cast<unsigned>(per), static_cast<unsigned>(rows));
     kern<<<grid, kTcThreads, smem, st>>>(gm, chunks, chunk, ctx->d_pinfo, ctx->logN, ctx->tc_lazy ? 1 : 0, status);
 }
