@@ -50,6 +50,9 @@ struct ckks_ctx {
     // NTT tile shape per pass (0 column, 1 block) and batch class (count <=
     // kTuneSmallBatch, larger): 0 default width, 1 half, 2 double (ntt_autotune)
     int ntt_csel[2][2] = {{0, 0}, {0, 0}};
+    // NTT radix split per direction (0 forward, 1 inverse) and batch class:
+    // pass C runs floor(logN/2) + split stages, split in {-1, 0, 1} (ntt_autotune)
+    int ntt_split[2][2] = {{0, 0}, {0, 0}};
     // compressed keys registered with ckks_key_register_seed: device pointer of
     // the rows b_j -> seed of the rows a_j
     std::unordered_map<const u64 *, u64> comp_keys;
@@ -152,6 +155,14 @@ struct InnerArgs {
     u64 seed = 0;
 };
 cudaError_t launch_inner_prod(const ckks_ctx *ctx, const InnerArgs &a, cudaStream_t st);
+// Batched KSKInnerProd with a compressed key: consecutive entries with one key,
+// at most kIpGroup of them, share a CTA (entries start[g] .. start[g+1]-1 form
+// group g).
+constexpr int kIpGroup = kMaxCts;
+struct IpGroups {
+    int n;
+    uint8_t start[kMaxCts + 1];
+};
 cudaError_t launch_inner_prod_batch(const ckks_ctx *ctx, const KsBatchDesc &d, cudaStream_t st);
 cudaError_t launch_tensor(const ckks_ctx *ctx, const TensorBatch &T, cudaStream_t st);
 cudaError_t launch_key_a_fill(const ckks_ctx *ctx, u64 seed, int j0, int ndig, u64 *dst, cudaStream_t st);

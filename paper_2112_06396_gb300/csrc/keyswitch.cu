@@ -172,7 +172,8 @@ cudaError_t launch_inner_prod(const ckks_ctx *ctx, const InnerArgs &a, cudaStrea
 // (position i), a special prime p_m to every entry (position ell + m); CTAs of
 // entries below a chain prime exit at once.  Each entry reads its own digits
 // through its own Galois element and writes its u, v into its workspace.
-template <int BMAX, bool COMP>
+// Full keys only (a batch with a compressed key goes to the grouped kernel).
+template <int BMAX>
 __global__ void __launch_bounds__(256) inner_prod_batch_kernel(const __grid_constant__ KsBatchDesc d,
                                                                const PrimeInfo *__restrict__ pinfo,
                                                                const ulonglong2 *__restrict__ Pmod) {
@@ -199,24 +200,8 @@ __global__ void __launch_bounds__(256) inner_prod_batch_kernel(const __grid_cons
                 const bool own = t < ell && (t / alpha) == j;
                 const u64 *src = own ? ct.a + size_t(t) * N : lo.extp + (size_t(j) * lo.ext + t) * N;
                 dv[j] = ld2_perm(src, n0, g, logN);
-                if (COMP && ct.compressed) {
-                    kb[j] = ld2(key + (size_t(j) * LK + pi) * N + n0);
-                } else {
-                    ka[j] = ld2(key + ((size_t(j) * 2 + 0) * LK + pi) * N + n0);
-                    kb[j] = ld2(key + ((size_t(j) * 2 + 1) * LK + pi) * N + n0);
-                }
-            }
-        }
-        if (COMP && ct.compressed) {
-            // the key's uniform half, regenerated while the loads are in flight
-            const u64 q = pinfo[pi].p;
-            const int shift = __clzll(q);
-#pragma unroll
-            for (int j = 0; j < BMAX; j++) {
-                if (j < beta) {
-                    const u64 e = (u64(j) * LK + pi) * N + n0;
-                    ka[j] = make_ulonglong2(key_a_element(ct.seed, e, q, shift), key_a_element(ct.seed, e + 1, q, shift));
-                }
+                ka[j] = ld2(key + ((size_t(j) * 2 + 0) * LK + pi) * N + n0);
+                kb[j] = ld2(key + ((size_t(j) * 2 + 1) * LK + pi) * N + n0);
             }
         }
 #pragma unroll
@@ -229,21 +214,12 @@ __global__ void __launch_bounds__(256) inner_prod_batch_kernel(const __grid_cons
             }
         }
     } else {
-        const u64 q = pinfo[pi].p;
-        const int shift = __clzll(q);
         for (int j = 0; j < beta; j++) {
             const bool own = t < ell && (t / alpha) == j;
             const u64 *src = own ? ct.a + size_t(t) * N : lo.extp + (size_t(j) * lo.ext + t) * N;
             const ulonglong2 dv = ld2_perm(src, n0, g, logN);
-            ulonglong2 a2, b2;
-            if (COMP && ct.compressed) {
-                const u64 e = (u64(j) * LK + pi) * N + n0;
-                a2 = make_ulonglong2(key_a_element(ct.seed, e, q, shift), key_a_element(ct.seed, e + 1, q, shift));
-                b2 = ld2(key + (size_t(j) * LK + pi) * N + n0);
-            } else {
-                a2 = ld2(key + ((size_t(j) * 2 + 0) * LK + pi) * N + n0);
-                b2 = ld2(key + ((size_t(j) * 2 + 1) * LK + pi) * N + n0);
-            }
+            const ulonglong2 a2 = ld2(key + ((size_t(j) * 2 + 0) * LK + pi) * N + n0);
+            const ulonglong2 b2 = ld2(key + ((size_t(j) * 2 + 1) * LK + pi) * N + n0);
             mac128(ul0, uh0, dv.x, a2.x);
             mac128(ul1, uh1, dv.y, a2.y);
             mac128(vl0, vh0, dv.x, b2.x);
@@ -264,26 +240,210 @@ __global__ void __launch_bounds__(256) inner_prod_batch_kernel(const __grid_cons
     st2(lo.uv + (size_t(lo.ext) + t) * N + n0, make_ulonglong2(reduce128(vl0, vh0, P), reduce128(vl1, vh1, P)));
 }
 
+// Batched KSKInnerProd for batches that hold a compressed key.  Consecutive
+// entries that use the same key (same rows, same compression and seed) form
+// groups (sized by the launcher); the grid is (group, coefficient tile, prime
+// of the extended basis).  A CTA regenerates (or loads) the key rows of its tile
+// once and serves every entry of its group with them, so a compressed key
+// shared across a batch is generated once per group instead of once per entry.
+// (With full keys the per-entry kernel above is faster: a shared key row comes
+// from L2 after the first entry, and holding the rows across entries costs
+// registers, hence resident warps.)  A chain prime q_i belongs to the entries
+// with ell > i (position i), a special prime p_m to every entry (position
+// ell + m); the key rows are those of the deepest digit among the group's
+// entries at this prime.  Each entry reads its own digits through its own
+// Galois element and writes its u, v into its workspace; the next entry's
+// digits are fetched while the current one is accumulated.
+template <int BMAX>
+__global__ void __launch_bounds__(256, 4) inner_prod_group_kernel(const __grid_constant__ KsBatchDesc d,
+                                                               const __grid_constant__ IpGroups G,
+                                                               const PrimeInfo *__restrict__ pinfo,
+                                                               const ulonglong2 *__restrict__ Pmod) {
+    const int c0 = G.start[blockIdx.x], c1 = G.start[blockIdx.x + 1];
+    const int pi = blockIdx.z;
+    const int logN = d.logN;
+    const size_t N = size_t(1) << logN;
+    const uint32_t n0 = (blockIdx.y * blockDim.x + threadIdx.x) * 2;
+    if (n0 >= N) return;
+    const int LK = d.L + d.k, alpha = d.alpha;
+    // entries of the group that own this prime, and the deepest digit among them
+    int bmax = 0;
+    for (int c = c0; c < c1; ++c) {
+        const int ell = d.ct[c].ell;
+        if (pi >= d.L || pi < ell) bmax = max(bmax, (ell + alpha - 1) / alpha);
+    }
+    if (bmax == 0) return;
+    const CtDesc &first = d.ct[c0];
+    const u64 *key = first.key;
+    const bool comp = first.compressed;  // this group's key
+    const PrimeInfo P = pinfo[pi];
+    constexpr int KB = BMAX > 0 ? BMAX : 1;
+    if constexpr (BMAX > 0) {
+        ulonglong2 ka[KB], kb[KB], dv[KB], nx[KB];
+#pragma unroll
+        for (int j = 0; j < KB; j++) {
+            if (j < bmax) {
+                if (comp) {
+                    kb[j] = ld2(key + (size_t(j) * LK + pi) * N + n0);
+                } else {
+                    ka[j] = ld2(key + ((size_t(j) * 2 + 0) * LK + pi) * N + n0);
+                    kb[j] = ld2(key + ((size_t(j) * 2 + 1) * LK + pi) * N + n0);
+                }
+            }
+        }
+        // the first owning entry's digits, in flight with the key rows
+        int c = c0;
+        while (c < c1 && !(pi >= d.L || pi < d.ct[c].ell)) ++c;
+        auto fetch = [&](int e, ulonglong2 *out) {
+            const CtDesc &ct = d.ct[e];
+            const int ell = ct.ell, t = pi < d.L ? pi : ell + (pi - d.L);
+            const CtLayout lo = ct_layout(d, ct);
+#pragma unroll
+            for (int j = 0; j < KB; j++) {
+                if (j < lo.beta) {
+                    const bool own = t < ell && (t / alpha) == j;
+                    const u64 *src = own ? ct.a + size_t(t) * N : lo.extp + (size_t(j) * lo.ext + t) * N;
+                    out[j] = ld2_perm(src, n0, ct.galois, logN);
+                }
+            }
+        };
+        fetch(c, dv);
+        if (comp) {
+            // the key's uniform half, regenerated while the loads are in flight
+            const int shift = __clzll(P.p);
+#pragma unroll
+            for (int j = 0; j < KB; j++) {
+                if (j < bmax) {
+                    const u64 e = (u64(j) * LK + pi) * N + n0;
+                    ka[j] = make_ulonglong2(key_a_element(first.seed, e, P.p, shift),
+                                            key_a_element(first.seed, e + 1, P.p, shift));
+                }
+            }
+        }
+        while (c < c1) {
+            int next = c + 1;
+            while (next < c1 && !(pi >= d.L || pi < d.ct[next].ell)) ++next;
+            if (next < c1) fetch(next, nx);
+            const CtDesc &ct = d.ct[c];
+            const int ell = ct.ell, t = pi < d.L ? pi : ell + (pi - d.L);
+            const CtLayout lo = ct_layout(d, ct);
+            u64 ul0 = 0, uh0 = 0, ul1 = 0, uh1 = 0, vl0 = 0, vh0 = 0, vl1 = 0, vh1 = 0;
+#pragma unroll
+            for (int j = 0; j < KB; j++) {
+                if (j < lo.beta) {
+                    mac128(ul0, uh0, dv[j].x, ka[j].x);
+                    mac128(ul1, uh1, dv[j].y, ka[j].y);
+                    mac128(vl0, vh0, dv[j].x, kb[j].x);
+                    mac128(vl1, vh1, dv[j].y, kb[j].y);
+                }
+            }
+            if (ct.merged && t < ell) {
+                // NewMult: PModUp(b3), PModUp(c3) join the sums before the one reduction
+                const u64 pm = Pmod[pi].x;
+                const ulonglong2 b = ld2(ct.add[0] + size_t(t) * N + n0), cc = ld2(ct.add[1] + size_t(t) * N + n0);
+                mac128(ul0, uh0, b.x, pm);
+                mac128(ul1, uh1, b.y, pm);
+                mac128(vl0, vh0, cc.x, pm);
+                mac128(vl1, vh1, cc.y, pm);
+            }
+            st2(lo.uv + size_t(t) * N + n0, make_ulonglong2(reduce128(ul0, uh0, P), reduce128(ul1, uh1, P)));
+            st2(lo.uv + (size_t(lo.ext) + t) * N + n0,
+                make_ulonglong2(reduce128(vl0, vh0, P), reduce128(vl1, vh1, P)));
+#pragma unroll
+            for (int j = 0; j < KB; j++) dv[j] = nx[j];
+            c = next;
+        }
+    } else {
+        // dnum > 4: key rows re-read per entry (from L2 after the first), digits looped
+        const int shift = __clzll(P.p);
+        for (int c = c0; c < c1; ++c) {
+            const CtDesc &ct = d.ct[c];
+            const int ell = ct.ell;
+            if (pi < d.L && pi >= ell) continue;
+            const int t = pi < d.L ? pi : ell + (pi - d.L);
+            const CtLayout lo = ct_layout(d, ct);
+            u64 ul0 = 0, uh0 = 0, ul1 = 0, uh1 = 0, vl0 = 0, vh0 = 0, vl1 = 0, vh1 = 0;
+            for (int j = 0; j < lo.beta; j++) {
+                const bool own = t < ell && (t / alpha) == j;
+                const u64 *src = own ? ct.a + size_t(t) * N : lo.extp + (size_t(j) * lo.ext + t) * N;
+                const ulonglong2 dv = ld2_perm(src, n0, ct.galois, logN);
+                ulonglong2 a2, b2;
+                if (comp) {
+                    const u64 e = (u64(j) * LK + pi) * N + n0;
+                    a2 = make_ulonglong2(key_a_element(first.seed, e, P.p, shift),
+                                         key_a_element(first.seed, e + 1, P.p, shift));
+                    b2 = ld2(key + (size_t(j) * LK + pi) * N + n0);
+                } else {
+                    a2 = ld2(key + ((size_t(j) * 2 + 0) * LK + pi) * N + n0);
+                    b2 = ld2(key + ((size_t(j) * 2 + 1) * LK + pi) * N + n0);
+                }
+                mac128(ul0, uh0, dv.x, a2.x);
+                mac128(ul1, uh1, dv.y, a2.y);
+                mac128(vl0, vh0, dv.x, b2.x);
+                mac128(vl1, vh1, dv.y, b2.y);
+            }
+            if (ct.merged && t < ell) {
+                const u64 pm = Pmod[pi].x;
+                const ulonglong2 b = ld2(ct.add[0] + size_t(t) * N + n0), cc = ld2(ct.add[1] + size_t(t) * N + n0);
+                mac128(ul0, uh0, b.x, pm);
+                mac128(ul1, uh1, b.y, pm);
+                mac128(vl0, vh0, cc.x, pm);
+                mac128(vl1, vh1, cc.y, pm);
+            }
+            st2(lo.uv + size_t(t) * N + n0, make_ulonglong2(reduce128(ul0, uh0, P), reduce128(ul1, uh1, P)));
+            st2(lo.uv + (size_t(lo.ext) + t) * N + n0,
+                make_ulonglong2(reduce128(vl0, vh0, P), reduce128(vl1, vh1, P)));
+        }
+    }
+}
+
 cudaError_t launch_inner_prod_batch(const ckks_ctx *ctx, const KsBatchDesc &d, cudaStream_t st) {
     if (d.n == 0) return cudaSuccess;
     int units = 0;
     for (int c = 0; c < d.n; ++c) units += d.ct[c].ell + d.k;
     const int threads = 256;
-    dim3 grid(unsigned(d.n), unsigned((ctx->N / 2 + threads - 1) / threads), unsigned(ctx->L + ctx->k));
+    const unsigned tiles = unsigned((ctx->N / 2 + threads - 1) / threads);
     ProfScope ps(ctx, K_INNER, units, st);
     bool comp = false;
     for (int c = 0; c < d.n; ++c) comp = comp || d.ct[c].compressed;
-#define CKKS_IPB(B)                                                                                                \
-    (comp ? inner_prod_batch_kernel<B, true><<<grid, threads, 0, st>>>(d, ctx->d_pinfo, ctx->d_Pmod)             \
-          : inner_prod_batch_kernel<B, false><<<grid, threads, 0, st>>>(d, ctx->d_pinfo, ctx->d_Pmod))
-    switch (ctx->dnum) {
-    case 1: CKKS_IPB(1); break;
-    case 2: CKKS_IPB(2); break;
-    case 3: CKKS_IPB(3); break;
-    case 4: CKKS_IPB(4); break;
-    default: CKKS_IPB(0);
-    }
+    if (!comp) {
+        dim3 grid(unsigned(d.n), tiles, unsigned(ctx->L + ctx->k));
+#define CKKS_IPB(B) inner_prod_batch_kernel<B><<<grid, threads, 0, st>>>(d, ctx->d_pinfo, ctx->d_Pmod)
+        switch (ctx->dnum) {
+        case 1: CKKS_IPB(1); break;
+        case 2: CKKS_IPB(2); break;
+        case 3: CKKS_IPB(3); break;
+        case 4: CKKS_IPB(4); break;
+        default: CKKS_IPB(0);
+        }
 #undef CKKS_IPB
+        return cudaGetLastError();
+    }
+    // groups of consecutive entries with one key (rows, compression, seed), as
+    // large as the launch allows while it keeps at least 8 CTAs per SM (fewer
+    // key generations, enough CTAs to fill the GPU at small N); with more than
+    // 4 digits the rows are not held in registers, so groups of one
+    const long per_entry = long(tiles) * (ctx->L + ctx->k);
+    const long fill = std::max(1L, per_entry * d.n / (8L * ctx->sms));
+    const int cap = ctx->dnum <= 4 ? int(std::min<long>(fill, kIpGroup)) : 1;
+    IpGroups G{};
+    G.start[0] = 0;
+    for (int c = 1; c <= d.n; ++c) {
+        const CtDesc &a = d.ct[G.start[G.n]];
+        const bool cut = c == d.n || c - G.start[G.n] >= cap || d.ct[c].key != a.key ||
+                         d.ct[c].compressed != a.compressed || (a.compressed && d.ct[c].seed != a.seed);
+        if (cut) G.start[++G.n] = uint8_t(c);
+    }
+    dim3 grid(unsigned(G.n), tiles, unsigned(ctx->L + ctx->k));
+#define CKKS_IPG(B) inner_prod_group_kernel<B><<<grid, threads, 0, st>>>(d, G, ctx->d_pinfo, ctx->d_Pmod)
+    switch (ctx->dnum) {
+    case 1: CKKS_IPG(1); break;
+    case 2: CKKS_IPG(2); break;
+    case 3: CKKS_IPG(3); break;
+    case 4: CKKS_IPG(4); break;
+    default: CKKS_IPG(0);
+    }
+#undef CKKS_IPG
     return cudaGetLastError();
 }
 

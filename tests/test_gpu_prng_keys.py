@@ -176,3 +176,65 @@ def test_registered_compressed_key_wide_primes(oracle_lib):
         np.testing.assert_array_equal(host(u), ru)
         np.testing.assert_array_equal(host(v), rv)
     S.ctx.unregister_compressed_key(kb)
+
+
+@pytest.mark.parametrize("shape", [(16, 7, 3, 3, 54), (12, 12, 2, 6, 50)], ids=["n16_dnum3", "n12_dnum6"])
+def test_batch_runs_of_shared_compressed_keys(oracle_lib, shape):
+    """A batch whose entries come in runs sharing one key (compressed keys
+    registered with the context, and full keys, in one call): consecutive
+    entries with one compressed key are served by one CTA per tile and prime,
+    the key half generated once per group (at N=2^16 the launch is large
+    enough for groups as long as the runs).  Runs of 1 to 5 entries, uneven
+    levels (so a group's entries own different chain primes and digit counts;
+    one run starts with an entry at level 1), KeySwitch and HRotate entries in
+    one run, dnum 3 (digits held in registers) and 6 (digits looped, groups of
+    one): every entry equals the same batch with expanded keys, and the oracle
+    on a sample.  The batch runs as one part on one stream."""
+    S = Setup(oracle_lib, *shape)
+    P, ctx = S.P, S.ctx
+    ctx.batch_streams(1)
+    g = 25
+    sr, sg = synth.stream_seed("gpu/prng/runs/relin"), synth.stream_seed("gpu/prng/runs/rot")
+    kr, ref_r = _seeded_key(S, 0, sr, "gpu/prng/runs/relin")
+    kg, ref_g = _seeded_key(S, g, sg, "gpu/prng/runs/rot")
+    full_r, full_g = ctx.ksk_expand(kr, sr), ctx.ksk_expand(kg, sg)
+    ctx.register_compressed_key(kr, sr)
+    ctx.register_compressed_key(kg, sg)
+    try:
+        L = P.L
+        # (key, expanded key, oracle key, rotation?) per entry, in runs
+        plan = ([(kg, full_g, ref_g, True)] * 3 + [(full_r, full_r, ref_r, False)] * 2 +
+                [(kr, full_r, ref_r, False)] * 5 + [(kg, full_g, ref_g, True)] + [(full_g, full_g, ref_g, True)])
+        levels = [1, L, 2, L, 3, 1, L - 1, 2, L, max(1, L // 2), L, 4]
+        a, b, gal, keys, fulls = [], [], [], [], []
+        for i, ((k, f, _, rot), ell) in enumerate(zip(plan, levels)):
+            ai, bi = S.ct(ell, f"gpu/prng/runs/{i}")
+            a.append(dev(ai))
+            b.append(dev(bi) if rot else None)
+            gal.append(g if rot else 1)
+            keys.append(k)
+            fulls.append(f)
+        got = ctx.keyswitch_batch(a, b, levels, gal, keys)
+        want = ctx.keyswitch_batch(a, b, levels, gal, fulls)
+        for i, ((ga, gb), (wa, wb)) in enumerate(zip(got, want)):
+            assert torch.equal(ga, wa) and torch.equal(gb, wb), i
+        for i in (1, 6, 8):
+            ell, ref = levels[i], plan[i][2]
+            ai = host(a[i])
+            if b[i] is None:
+                ru, rv = S.o.keyswitch(P, ell, ai, ref)
+            else:
+                ((ru, rv),) = S.o.hrotate(P, ell, ai, host(b[i]), [g], [ref])
+            np.testing.assert_array_equal(host(got[i][0]), ru)
+            np.testing.assert_array_equal(host(got[i][1]), rv)
+        # single KeySwitch calls with the full and the compressed key
+        ru, rv = S.o.keyswitch(P, L, host(a[3]), ref_r)
+        for k in (full_r, kr):
+            u, v = ctx.keyswitch(a[3], L, k)
+            np.testing.assert_array_equal(host(u), ru)
+            np.testing.assert_array_equal(host(v), rv)
+        assert ctx.poll_status()
+    finally:
+        ctx.unregister_compressed_key(kr)
+        ctx.unregister_compressed_key(kg)
+        ctx.batch_streams(2)
