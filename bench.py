@@ -808,11 +808,11 @@ def run_gpu(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     primes = ckks.ckks_gen_primes(BITS, LOGN, L + K_SP)
     ctx = ckks.Context(LOGN, primes[:L], primes[L:], DNUM, device=local_rank)
-    tune_choice, tune_times = [0, 0, 0, 0], []
+    tune_choice, tune_times = [0] * 8, []
     if args.fuse:
         ctx.fuse_modup(True)
     if not args.no_tune:
-        tune_choice, tune_times = ctx.autotune(limbs=128)  # NTT tile shapes for this GPU (ckks_autotune)
+        tune_choice, tune_times = ctx.autotune(limbs=128)  # NTT tile shapes and radix splits for this GPU (ckks_autotune)
     torch.cuda.synchronize()
     C = args.batch
     items = make_workload(ctx, C, rank, torch)
@@ -983,7 +983,9 @@ def run_gpu(args, rank, world, local_rank):
             "config": {**base_config(C), "parallelism": f"replicas x{world}", "fused_dataflow": bool(args.fuse),
                        "ntt_tile_shapes": {"choice": tune_choice, "ms": [round(t, 4) for t in tune_times],
                                            "legend": "[column pass <=48 limbs, column pass larger, block pass <=48, "
-                                                     "block pass larger]; 0 default width, 1 half, 2 double"}},
+                                                     "block pass larger]: 0 default width, 1 half, 2 double; then "
+                                                     "radix split [forward <=48, forward larger, inverse <=48, "
+                                                     "inverse larger]: block pass floor(logN/2)+split stages"}},
             "clocks": clk, "gpu_launches": int(round(launches_per_step * args.steps)),
             "wall_s_timed": t_wall,
             "hbm": {"compulsory_bytes_per_keyswitch": ks_bytes,

@@ -334,17 +334,25 @@ int ckks_keyswitch_batch_seeded(ckks_ctx *ctx, int n, const uint64_t *const *d_a
 
 /* NTT autotuner (no counterpart in the paper).  Each NTT pass (the column
  * pass and the block pass of the two-pass transform) exists in three tile
- * shapes (CTA widths: the default, half, double) for logN >= 14 with primes
- * below 2^57.  ckks_autotune times every shape, forward and inverse, on 24
- * limbs and on min(128, ws_bytes / (8N)) limbs of the workspace (zeroed, then
- * transformed in place), synchronises the stream, and keeps the fastest shape
- * per pass and per launch size (<= 48 limbs, larger) in the context.
- * choice (optional, 4 ints): [column pass small, column pass large, block pass
- * small, block pass large], 0 = default, 1 = half width, 2 = double width.
- * times (optional, 12 floats): ms per forward+inverse pass for
- * [(pass * 2 + size class) * 3 + shape], the order of choice.  ckks_tune_set applies a saved
- * choice.  Results are identical for every shape; only the speed changes.
- * Contexts outside the tuned range keep the default (choice all 0). */
+ * shapes (CTA widths: the default, half, double), and each transform in three
+ * radix splits (the block pass runs floor(logN/2) + split stages, the column
+ * pass the rest; split -1, 0 or +1, the other shapes at split 0 only), for
+ * logN >= 14 with primes below 2^57.  ckks_autotune times every width,
+ * forward and inverse, on 24 limbs and on min(128, ws_bytes / (8N)) limbs of
+ * the workspace (zeroed, then transformed in place); then, with the widths
+ * chosen, every split of a whole forward and of a whole inverse transform.
+ * It synchronises the stream and keeps the fastest width per pass and launch
+ * size (<= 48 limbs, larger) and the fastest split per direction and launch
+ * size (ties to split 0) in the context.
+ * choice (optional, 8 ints): [column pass small, column pass large, block pass
+ * small, block pass large] with 0 = default, 1 = half width, 2 = double width,
+ * then [forward small, forward large, inverse small, inverse large] splits in
+ * {-1, 0, 1}.  times (optional, 24 floats): ms per forward+inverse pass for
+ * [(pass * 2 + size class) * 3 + width], then ms per transform for
+ * 12 + [(direction * 2 + size class) * 3 + split + 1].  ckks_tune_set applies
+ * a saved choice (8 ints; EINVAL for a value out of range).  Results are
+ * identical for every shape and split; only the speed changes.  Contexts
+ * outside the tuned range keep the default (choice all 0). */
 int ckks_autotune(ckks_ctx *ctx, void *ws, size_t ws_bytes, ckks_stream_t stream, int *choice, float *times);
 int ckks_tune_set(ckks_ctx *ctx, const int *choice);
 

@@ -324,10 +324,13 @@ class Context:
         return bool(done.value)
 
     def autotune(self, limbs=128, stream=None, cache=None):
-        """Time the NTT tile shapes and keep the fastest (ckks_autotune).
-        Returns (choice[4], times_ms[12]).  With cache (a JSON file path), a
-        choice stored for this GPU model and parameter shape is applied without
-        timing, and a new one is stored."""
+        """Time the NTT tile shapes and radix splits and keep the fastest
+        (ckks_autotune).  Returns (choice[8], times_ms[24]): the widths of the
+        column and block pass per launch size (0 default, 1 half, 2 double),
+        then the radix split of the forward and inverse transform per launch
+        size (-1, 0, +1).  With cache (a JSON file path), a choice stored for
+        this GPU model and parameter shape is applied without timing, and a new
+        one is stored."""
         import json
 
         key = None
@@ -338,12 +341,12 @@ class Context:
                     saved = json.load(f)
             except (OSError, ValueError):
                 saved = {}
-            if key in saved:
+            if key in saved and len(saved[key].get("choice", [])) == 8:
                 self.tune_set(saved[key]["choice"])
                 return list(saved[key]["choice"]), list(saved[key]["times_ms"])
         ws = torch.empty((limbs, self.N), dtype=torch.uint64, device=self.device)
-        ch = (_i * 4)()
-        tm = (ctypes.c_float * 12)()
+        ch = (_i * 8)()
+        tm = (ctypes.c_float * 24)()
         _check(lib().ckks_autotune(self._h, _p(ws), limbs * self.N * 8, _stream(stream), ch, tm), self._h)
         choice, times = list(ch), list(tm)
         if cache is not None:
@@ -353,7 +356,10 @@ class Context:
         return choice, times
 
     def tune_set(self, choice):
-        ch = (_i * 4)(*[int(x) for x in choice])
+        """Apply a tuner choice (8 ints, the layout autotune returns)."""
+        if len(choice) != 8:
+            raise CkksError("tune_set: choice must hold 8 ints (4 widths, 4 radix splits)")
+        ch = (_i * 8)(*[int(x) for x in choice])
         _check(lib().ckks_tune_set(self._h, ch))
 
     def selftest_bounded_wait(self, limit_us, stream=None):

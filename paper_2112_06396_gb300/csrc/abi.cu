@@ -1775,18 +1775,21 @@ extern "C" int ckks_autotune(ckks_ctx *ctx, void *ws, size_t ws_bytes, ckks_stre
     const int small = 24;
     if (large < small) return CKKS_EINVAL;
     if (times)
-        for (int i = 0; i < 12; ++i) times[i] = 0.f;
+        for (int i = 0; i < 24; ++i) times[i] = 0.f;
     CK(ntt_autotune(ctx, static_cast<u64 *>(ws), small, large, (cudaStream_t)stream, times));
-    if (choice)
+    if (choice) {
         for (int i = 0; i < 4; ++i) choice[i] = ctx->ntt_csel[i / 2][i % 2];
+        for (int i = 0; i < 4; ++i) choice[4 + i] = ctx->ntt_split[i / 2][i % 2];
+    }
     return CKKS_OK;
 }
 
 extern "C" int ckks_tune_set(ckks_ctx *ctx, const int *choice) {
     if (ctx == nullptr || choice == nullptr) return CKKS_EINVAL;
     for (int i = 0; i < 4; ++i)
-        if (choice[i] < 0 || choice[i] > 2) return CKKS_EINVAL;
+        if (choice[i] < 0 || choice[i] > 2 || choice[4 + i] < -1 || choice[4 + i] > 1) return CKKS_EINVAL;
     for (int i = 0; i < 4; ++i) ctx->ntt_csel[i / 2][i % 2] = choice[i];
+    for (int i = 0; i < 4; ++i) ctx->ntt_split[i / 2][i % 2] = choice[4 + i];
     return CKKS_OK;
 }
 

@@ -7,10 +7,11 @@
 // the inverse is the Gentleman-Sande network with psi^-brv(2^s + i) and the
 // factor N^-1 folded into its last stage.
 //
-// GB300 layout: a limb (N words) is viewed as a 2^L1 x 2^L2 matrix (L1 =
-// ceil(logN/2)).  Pass S runs the first L1 stages down the columns (rows are
-// 2^L2 words apart), pass C the last L2 stages inside each contiguous block
-// of 2^L2 words.  One CTA owns C columns (pass S) or C blocks (pass C); each
+// GB300 layout: a limb (N words) is viewed as a 2^L1 x 2^L2 matrix (by
+// default L1 = ceil(logN/2); the autotuner may move one stage from one pass
+// to the other, the radix split).  Pass S runs the first L1 stages down the
+// columns (rows are 2^L2 words apart), pass C the last L2 stages inside each
+// contiguous block of 2^L2 words.  One CTA owns C columns (pass S) or C blocks (pass C); each
 // thread holds E = 2^A words in registers, runs A stages there, the tile is
 // transposed once through shared memory, and the remaining B = LOGR - A
 // stages run in registers again.  Global loads and stores are coalesced (the
@@ -64,7 +65,7 @@ __device__ __forceinline__ void gs_bfly(u64 &X, u64 &Y, ulonglong2 w, u64 p, u64
     }
 }
 
-template <int LOGN, int LOGR, int A, int C, bool INV, bool CONTIG, bool EPI, bool SMALLP, class MAP>
+template <int LOGN, int L2, int LOGR, int A, int C, bool INV, bool CONTIG, bool EPI, bool SMALLP, class MAP>
 __global__ void __launch_bounds__((1 << (LOGR - A)) * C, (A <= 4 ? 1024 : 512) / ((1 << (LOGR - A)) * C))
 ntt_pass_kernel(const __grid_constant__ MAP map, const PrimeInfo *__restrict__ pinfo,
                 const ulonglong2 *__restrict__ tw_all) {
@@ -78,7 +79,6 @@ ntt_pass_kernel(const __grid_constant__ MAP map, const PrimeInfo *__restrict__ p
     extern __shared__ u64 sm[];
 
     // every shift is a compile-time constant and every index fits 32 bits
-    constexpr int L2 = LOGN >> 1;
     constexpr int L1 = LOGN - L2;
     constexpr uint32_t N = 1u << LOGN;
     constexpr int logN = LOGN;
@@ -523,13 +523,16 @@ modup_ip_kernel(const __grid_constant__ FusedIpArgs F, const PrimeInfo *__restri
 namespace {
 
 // CSEL picks the CTA width (the tile shape): 0 = the default below, 1 = half
-// of it, 2 = twice it.  The autotuner (ntt_autotune) chooses per pass and per
-// batch size; widths other than the default exist for logN >= 14 with small
-// primes (the key-switching shapes), elsewhere every CSEL maps to 0.
-template <int LOGN, bool INV, bool CONTIG, bool EPI, bool SMALLP, int CSEL, class MAP>
+// of it, 2 = twice it.  SPL moves the radix split: L2 = floor(logN/2) + SPL
+// stages in pass C, the rest in pass S.  The autotuner (ntt_autotune) chooses
+// the width per pass and batch size, and the split per direction and batch
+// size (both passes of a transform share it); shapes other than the default
+// exist for logN >= 14 with small primes (the key-switching shapes), and a
+// split other than 0 only with the default width.
+template <int LOGN, int SPL, bool INV, bool CONTIG, bool EPI, bool SMALLP, int CSEL, class MAP>
 cudaError_t launch_one_p(const MAP &m, int count, const ckks_ctx *ctx, cudaStream_t st, bool set_attr) {
     // pass S transforms columns of 2^L1 rows, pass C blocks of 2^L2 words
-    constexpr int L2 = LOGN >> 1, L1 = LOGN - L2;
+    constexpr int L2 = (LOGN >> 1) + SPL, L1 = LOGN - L2;
     constexpr int LOGR = CONTIG ? L2 : L1;
     constexpr int OTHER = CONTIG ? L1 : L2;
     constexpr int A = (LOGR + 1) / 2;
@@ -544,7 +547,7 @@ cudaError_t launch_one_p(const MAP &m, int count, const ckks_ctx *ctx, cudaStrea
     constexpr int WANT = BASE / TPC > 0 ? BASE / TPC : 1;
     constexpr int C = WANT < (1 << OTHER) ? WANT : (1 << OTHER);
     const size_t smem = CONTIG ? size_t(C) * (R + TPC) * 8 : size_t(R) * C * 8 + size_t(R) * 16;
-    auto kern = ntt_pass_kernel<LOGN, LOGR, A, C, INV, CONTIG, EPI, SMALLP, MAP>;
+    auto kern = ntt_pass_kernel<LOGN, L2, LOGR, A, C, INV, CONTIG, EPI, SMALLP, MAP>;
     if (set_attr) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     dim3 grid(count, (1 << OTHER) / C);
     kern<<<grid, TPC * C, smem, st>>>(m, ctx->d_pinfo, INV ? ctx->d_tw_inv : ctx->d_tw_fwd);
@@ -552,19 +555,25 @@ cudaError_t launch_one_p(const MAP &m, int count, const ckks_ctx *ctx, cudaStrea
 }
 
 template <int LOGN, bool INV, bool CONTIG, bool EPI, class MAP>
-cudaError_t launch_one(const MAP &m, int count, const ckks_ctx *ctx, cudaStream_t st, bool set_attr, int csel) {
+cudaError_t launch_one(const MAP &m, int count, const ckks_ctx *ctx, cudaStream_t st, bool set_attr, int csel,
+                       int split) {
     constexpr bool TUNED = LOGN >= 14;
+    constexpr int SM1 = TUNED ? -1 : 0, SP1 = TUNED ? 1 : 0;
     if (set_attr) {
-        cudaError_t e = launch_one_p<LOGN, INV, CONTIG, EPI, false, 0>(m, count, ctx, st, true);
-        if (e == cudaSuccess) e = launch_one_p<LOGN, INV, CONTIG, EPI, true, 0>(m, count, ctx, st, true);
-        if (TUNED && e == cudaSuccess) e = launch_one_p<LOGN, INV, CONTIG, EPI, true, TUNED ? 1 : 0>(m, count, ctx, st, true);
-        if (TUNED && e == cudaSuccess) e = launch_one_p<LOGN, INV, CONTIG, EPI, true, TUNED ? 2 : 0>(m, count, ctx, st, true);
+        cudaError_t e = launch_one_p<LOGN, 0, INV, CONTIG, EPI, false, 0>(m, count, ctx, st, true);
+        if (e == cudaSuccess) e = launch_one_p<LOGN, 0, INV, CONTIG, EPI, true, 0>(m, count, ctx, st, true);
+        if (TUNED && e == cudaSuccess) e = launch_one_p<LOGN, 0, INV, CONTIG, EPI, true, TUNED ? 1 : 0>(m, count, ctx, st, true);
+        if (TUNED && e == cudaSuccess) e = launch_one_p<LOGN, 0, INV, CONTIG, EPI, true, TUNED ? 2 : 0>(m, count, ctx, st, true);
+        if (TUNED && e == cudaSuccess) e = launch_one_p<LOGN, SM1, INV, CONTIG, EPI, true, 0>(m, count, ctx, st, true);
+        if (TUNED && e == cudaSuccess) e = launch_one_p<LOGN, SP1, INV, CONTIG, EPI, true, 0>(m, count, ctx, st, true);
         return e;
     }
-    if (!ctx->small_primes) return launch_one_p<LOGN, INV, CONTIG, EPI, false, 0>(m, count, ctx, st, false);
-    if (TUNED && csel == 1) return launch_one_p<LOGN, INV, CONTIG, EPI, true, TUNED ? 1 : 0>(m, count, ctx, st, false);
-    if (TUNED && csel == 2) return launch_one_p<LOGN, INV, CONTIG, EPI, true, TUNED ? 2 : 0>(m, count, ctx, st, false);
-    return launch_one_p<LOGN, INV, CONTIG, EPI, true, 0>(m, count, ctx, st, false);
+    if (!ctx->small_primes) return launch_one_p<LOGN, 0, INV, CONTIG, EPI, false, 0>(m, count, ctx, st, false);
+    if (TUNED && split < 0) return launch_one_p<LOGN, SM1, INV, CONTIG, EPI, true, 0>(m, count, ctx, st, false);
+    if (TUNED && split > 0) return launch_one_p<LOGN, SP1, INV, CONTIG, EPI, true, 0>(m, count, ctx, st, false);
+    if (TUNED && csel == 1) return launch_one_p<LOGN, 0, INV, CONTIG, EPI, true, TUNED ? 1 : 0>(m, count, ctx, st, false);
+    if (TUNED && csel == 2) return launch_one_p<LOGN, 0, INV, CONTIG, EPI, true, TUNED ? 2 : 0>(m, count, ctx, st, false);
+    return launch_one_p<LOGN, 0, INV, CONTIG, EPI, true, 0>(m, count, ctx, st, false);
 }
 
 // The tuned width of a pass for a launch of `count` limbs (-1: use the table).
@@ -573,18 +582,26 @@ inline int csel_for(const ckks_ctx *ctx, bool contig, int count, int force) {
     return ctx->ntt_csel[contig ? 1 : 0][count > kTuneSmallBatch ? 1 : 0];
 }
 
+// The tuned radix split of a transform of `count` limbs (both passes).
+inline int split_for(const ckks_ctx *ctx, bool inv, int count) {
+    return ctx->ntt_split[inv ? 1 : 0][count > kTuneSmallBatch ? 1 : 0];
+}
+
+// split: the radix split both passes of this transform use (split_for, or 0
+// where another kernel runs the other pass with the default split).
 template <bool INV, bool CONTIG, bool EPI, class MAP>
-cudaError_t dispatch(const MAP &m, int count, const ckks_ctx *ctx, cudaStream_t st, bool set_attr, int force = -1) {
+cudaError_t dispatch(const MAP &m, int count, const ckks_ctx *ctx, cudaStream_t st, bool set_attr, int split,
+                     int force = -1) {
     const int cs = csel_for(ctx, CONTIG, count, force);
     switch (ctx->logN) {
-    case 10: return launch_one<10, INV, CONTIG, EPI>(m, count, ctx, st, set_attr, cs);
-    case 11: return launch_one<11, INV, CONTIG, EPI>(m, count, ctx, st, set_attr, cs);
-    case 12: return launch_one<12, INV, CONTIG, EPI>(m, count, ctx, st, set_attr, cs);
-    case 13: return launch_one<13, INV, CONTIG, EPI>(m, count, ctx, st, set_attr, cs);
-    case 14: return launch_one<14, INV, CONTIG, EPI>(m, count, ctx, st, set_attr, cs);
-    case 15: return launch_one<15, INV, CONTIG, EPI>(m, count, ctx, st, set_attr, cs);
-    case 16: return launch_one<16, INV, CONTIG, EPI>(m, count, ctx, st, set_attr, cs);
-    case 17: return launch_one<17, INV, CONTIG, EPI>(m, count, ctx, st, set_attr, cs);
+    case 10: return launch_one<10, INV, CONTIG, EPI>(m, count, ctx, st, set_attr, cs, split);
+    case 11: return launch_one<11, INV, CONTIG, EPI>(m, count, ctx, st, set_attr, cs, split);
+    case 12: return launch_one<12, INV, CONTIG, EPI>(m, count, ctx, st, set_attr, cs, split);
+    case 13: return launch_one<13, INV, CONTIG, EPI>(m, count, ctx, st, set_attr, cs, split);
+    case 14: return launch_one<14, INV, CONTIG, EPI>(m, count, ctx, st, set_attr, cs, split);
+    case 15: return launch_one<15, INV, CONTIG, EPI>(m, count, ctx, st, set_attr, cs, split);
+    case 16: return launch_one<16, INV, CONTIG, EPI>(m, count, ctx, st, set_attr, cs, split);
+    case 17: return launch_one<17, INV, CONTIG, EPI>(m, count, ctx, st, set_attr, cs, split);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -593,41 +610,43 @@ template <class MAP>
 cudaError_t set_attributes_for(const ckks_ctx *ctx) {
     MAP m{};
     cudaError_t err;
-    if ((err = dispatch<false, false, false>(m, 0, ctx, nullptr, true)) != cudaSuccess) return err;
-    if ((err = dispatch<false, true, false>(m, 0, ctx, nullptr, true)) != cudaSuccess) return err;
-    if ((err = dispatch<false, true, true>(m, 0, ctx, nullptr, true)) != cudaSuccess) return err;
-    if ((err = dispatch<true, true, false>(m, 0, ctx, nullptr, true)) != cudaSuccess) return err;
-    return dispatch<true, false, false>(m, 0, ctx, nullptr, true);
+    if ((err = dispatch<false, false, false>(m, 0, ctx, nullptr, true, 0)) != cudaSuccess) return err;
+    if ((err = dispatch<false, true, false>(m, 0, ctx, nullptr, true, 0)) != cudaSuccess) return err;
+    if ((err = dispatch<false, true, true>(m, 0, ctx, nullptr, true, 0)) != cudaSuccess) return err;
+    if ((err = dispatch<true, true, false>(m, 0, ctx, nullptr, true, 0)) != cudaSuccess) return err;
+    return dispatch<true, false, false>(m, 0, ctx, nullptr, true, 0);
 }
 
 // Two passes of one transform: the second runs in place on the first's output.
 template <class MAP>
 cudaError_t run_fwd(MAP m, int count, bool epi, const ckks_ctx *ctx, cudaStream_t st) {
     cudaError_t err;
+    const int split = split_for(ctx, false, count);
     m.second = 0;
     {
         ProfScope ps(ctx, K_NTT_FWD, count, st);
-        err = dispatch<false, false, false>(m, count, ctx, st, false);
+        err = dispatch<false, false, false>(m, count, ctx, st, false, split);
     }
     if (err != cudaSuccess) return err;
     m.second = 1;
     ProfScope ps(ctx, K_NTT_FWD, count, st);
-    if (epi) return dispatch<false, true, true>(m, count, ctx, st, false);
-    return dispatch<false, true, false>(m, count, ctx, st, false);
+    if (epi) return dispatch<false, true, true>(m, count, ctx, st, false, split);
+    return dispatch<false, true, false>(m, count, ctx, st, false, split);
 }
 
 template <class MAP>
 cudaError_t run_inv(MAP m, int count, const ckks_ctx *ctx, cudaStream_t st) {
     cudaError_t err;
+    const int split = split_for(ctx, true, count);
     m.second = 0;
     {
         ProfScope ps(ctx, K_NTT_INV, count, st);
-        err = dispatch<true, true, false>(m, count, ctx, st, false);
+        err = dispatch<true, true, false>(m, count, ctx, st, false, split);
     }
     if (err != cudaSuccess) return err;
     m.second = 1;
     ProfScope ps(ctx, K_NTT_INV, count, st);
-    return dispatch<true, false, false>(m, count, ctx, st, false);
+    return dispatch<true, false, false>(m, count, ctx, st, false, split);
 }
 
 }  // namespace
@@ -753,8 +772,8 @@ cudaError_t launch_modup_ip(const ckks_ctx *ctx, const FusedIpArgs &f, cudaStrea
     return modup_ip_dispatch(ctx, f, st, false);
 }
 
-// Pass S alone of the forward transform (src -> dst, lazy values): the fused
-// ModUp tail runs pass C.
+// Pass S alone of the forward transform (src -> dst, lazy values), with the
+// default radix split: the fused ModUp tail runs pass C.
 cudaError_t launch_ntt_fwd_colpass(const ckks_ctx *ctx, const NttBatch &b, cudaStream_t st) {
     if (b.count == 0) return cudaSuccess;
     MapList m;
@@ -763,11 +782,11 @@ cudaError_t launch_ntt_fwd_colpass(const ckks_ctx *ctx, const NttBatch &b, cudaS
     m.e.mode = EPI_STORE;
     m.second = 0;
     ProfScope ps(ctx, K_NTT_FWD, b.count, st);
-    return dispatch<false, false, false>(m, b.count, ctx, st, false);
+    return dispatch<false, false, false>(m, b.count, ctx, st, false, 0);
 }
 
-// Pass S alone of the inverse transform, in place on dst (pass C ran in the
-// fused ModUp tail).
+// Pass S alone of the inverse transform, in place on dst, with the default
+// radix split (pass C ran in the fused ModUp tail).
 cudaError_t launch_ntt_inv_colpass(const ckks_ctx *ctx, const NttBatch &b, cudaStream_t st) {
     if (b.count == 0) return cudaSuccess;
     MapList m;
@@ -776,7 +795,7 @@ cudaError_t launch_ntt_inv_colpass(const ckks_ctx *ctx, const NttBatch &b, cudaS
     m.e.mode = EPI_STORE;
     m.second = 1;
     ProfScope ps(ctx, K_NTT_INV, b.count, st);
-    return dispatch<true, false, false>(m, b.count, ctx, st, false);
+    return dispatch<true, false, false>(m, b.count, ctx, st, false, 0);
 }
 
 // ------------------------------------------------------------------ butterfly ceiling
@@ -826,10 +845,15 @@ size_t bfly_peak_sink_words(const ckks_ctx *ctx) { return size_t(ctx->sms) * 4 *
 // Times every CTA width of the column pass (S) and the block pass (C), forward
 // and inverse together, on `small` and `large` limbs of scratch data (in
 // place, values are transformed and transformed back), and keeps the fastest
-// per pass and batch-size class in the context.  scratch: at least
-// large * N words.  Returns the chosen widths through ctx->ntt_csel.
+// per pass and batch-size class; then, with those widths, times whole forward
+// and whole inverse transforms at each radix split (0, -1, +1: pass C gets
+// floor(logN/2) + split stages) and keeps the fastest per direction and class
+// (ties to the default).  scratch: at least large * N words.  The choices go
+// to ctx->ntt_csel and ctx->ntt_split; times_out (24 floats, ms per run) gets
+// the widths' times at [(pass * 2 + class) * 3 + width] and the splits' at
+// 12 + [(direction * 2 + class) * 3 + split + 1].
 cudaError_t ntt_autotune(ckks_ctx *ctx, u64 *scratch, int small, int large, cudaStream_t st, float *times_out) {
-    if (ctx->logN < 14 || !ctx->small_primes) return cudaSuccess;  // one width only
+    if (ctx->logN < 14 || !ctx->small_primes) return cudaSuccess;  // one shape only
     cudaEvent_t e0, e1;
     cudaError_t err = cudaEventCreate(&e0);
     if (err != cudaSuccess) return err;
@@ -840,6 +864,19 @@ cudaError_t ntt_autotune(ckks_ctx *ctx, u64 *scratch, int small, int large, cuda
     const bool prof = ctx->prof_on;
     ctx->prof_on = false;
     err = cudaMemsetAsync(scratch, 0, size_t(large) * ctx->N * sizeof(u64), st);
+    // ms per run of `run` (one warm-up, then 5 timed runs)
+    auto timed = [&](auto run, float *ms) {
+        cudaError_t e2 = run();
+        if (e2 != cudaSuccess) return e2;
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 5 && e2 == cudaSuccess; ++r) e2 = run();
+        cudaEventRecord(e1, st);
+        if (e2 == cudaSuccess) e2 = cudaEventSynchronize(e1);
+        float t = 0.f;
+        if (e2 == cudaSuccess) e2 = cudaEventElapsedTime(&t, e0, e1);
+        *ms = t / 5;
+        return e2;
+    };
     const int counts[2] = {small, large};
     for (int bucket = 0; bucket < 2 && err == cudaSuccess; ++bucket) {
         const int count = counts[bucket];
@@ -851,34 +888,54 @@ cudaError_t ntt_autotune(ckks_ctx *ctx, u64 *scratch, int small, int large, cuda
             m.b.prime[l] = uint16_t(l % (ctx->L + ctx->k));
         }
         m.e.mode = EPI_STORE;
+        m.second = 1;
         for (int contig = 0; contig < 2 && err == cudaSuccess; ++contig) {
             float best = 1e30f;
             int pick = 0;
             for (int cs = 0; cs < 3 && err == cudaSuccess; ++cs) {
                 auto run = [&]() {
-                    m.second = 1;
-                    cudaError_t e2 = contig ? dispatch<false, true, false>(m, count, ctx, st, false, cs)
-                                            : dispatch<false, false, false>(m, count, ctx, st, false, cs);
+                    cudaError_t e2 = contig ? dispatch<false, true, false>(m, count, ctx, st, false, 0, cs)
+                                            : dispatch<false, false, false>(m, count, ctx, st, false, 0, cs);
                     if (e2 == cudaSuccess)
-                        e2 = contig ? dispatch<true, true, false>(m, count, ctx, st, false, cs)
-                                    : dispatch<true, false, false>(m, count, ctx, st, false, cs);
+                        e2 = contig ? dispatch<true, true, false>(m, count, ctx, st, false, 0, cs)
+                                    : dispatch<true, false, false>(m, count, ctx, st, false, 0, cs);
                     return e2;
                 };
-                err = run();  // warm-up
-                if (err != cudaSuccess) break;
-                cudaEventRecord(e0, st);
-                for (int r = 0; r < 5 && err == cudaSuccess; ++r) err = run();
-                cudaEventRecord(e1, st);
-                if (err == cudaSuccess) err = cudaEventSynchronize(e1);
                 float ms = 0.f;
-                if (err == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
-                if (times_out) times_out[(contig * 2 + bucket) * 3 + cs] = ms / 5;
+                err = timed(run, &ms);
+                if (err != cudaSuccess) break;
+                if (times_out) times_out[(contig * 2 + bucket) * 3 + cs] = ms;
                 if (ms < best) {
                     best = ms;
                     pick = cs;
                 }
             }
             ctx->ntt_csel[contig][bucket] = pick;
+        }
+        for (int inv = 0; inv < 2 && err == cudaSuccess; ++inv) {
+            float best = 1e30f;
+            int pick = 0;
+            const int order[3] = {0, -1, 1};
+            for (int o = 0; o < 3 && err == cudaSuccess; ++o) {
+                const int sp = order[o];
+                auto run = [&]() {
+                    cudaError_t e2 = inv ? dispatch<true, true, false>(m, count, ctx, st, false, sp)
+                                         : dispatch<false, false, false>(m, count, ctx, st, false, sp);
+                    if (e2 == cudaSuccess)
+                        e2 = inv ? dispatch<true, false, false>(m, count, ctx, st, false, sp)
+                                 : dispatch<false, true, false>(m, count, ctx, st, false, sp);
+                    return e2;
+                };
+                float ms = 0.f;
+                err = timed(run, &ms);
+                if (err != cudaSuccess) break;
+                if (times_out) times_out[12 + (inv * 2 + bucket) * 3 + sp + 1] = ms;
+                if (ms < best) {
+                    best = ms;
+                    pick = sp;
+                }
+            }
+            ctx->ntt_split[inv][bucket] = pick;
         }
     }
     ctx->prof_on = prof;

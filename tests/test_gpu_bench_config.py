@@ -63,14 +63,15 @@ def test_bench_step_matches_oracle(oracle_lib):
         np.testing.assert_array_equal(first[c][1], rb)
 
 
-@pytest.mark.parametrize("choice", [[0, 0, 0, 0], [1, 1, 1, 1], [2, 2, 1, 0]])
+@pytest.mark.parametrize("choice", [[0, 0, 0, 0, 0, 0, 0, 0], [1, 1, 1, 1, 0, 0, 0, 0], [2, 2, 1, 0, 0, 0, 0, 0],
+                                    [0, 0, 0, 0, -1, -1, -1, -1], [0, 0, 0, 0, 1, 1, 1, 1]])
 def test_concurrent_streams_equal_one_at_a_time(choice):
     """Sixteen HRotates on 8 streams, repeated, against the same HRotates run
-    one at a time, for several NTT tile shapes.  The tensor-core conversion
-    keeps a ring of source stages per CTA; with other kernels sharing the SMs
-    (the small tile shapes put the most CTAs beside it) a stage handed back too
-    early was overwritten before it was fully read.  Every output of every step
-    must carry the one-at-a-time bits (tolerance 0)."""
+    one at a time, for several NTT tile shapes and radix splits.  The
+    tensor-core conversion keeps a ring of source stages per CTA; with other
+    kernels sharing the SMs (the small tile shapes put the most CTAs beside it)
+    a stage handed back too early was overwritten before it was fully read.
+    Every output of every step must carry the one-at-a-time bits (tolerance 0)."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import bench
