@@ -878,12 +878,12 @@ def run_gpu(args, rank, world, local_rank):
     for (ha, hb), it in zip(pin_in, items):
         ha.copy_(it["a"].cpu())
         hb.copy_(it["b"].cpu())
-    # two sets of device inputs and outputs, alternating between steps, so that
-    # a step's host-to-device copies overlap the previous step's compute and
-    # device-to-host copies; every reuse of a buffer waits (by event) for the
-    # last read of it: the HRotate that read an input set, the copy back that
-    # read an output set
-    NB = 2
+    # sets of device inputs and outputs (--e2e-sets), taken in turn by the
+    # steps, so that a step's host-to-device copies overlap the previous steps'
+    # compute and device-to-host copies; every reuse of a buffer waits (by
+    # event) for the last read of it: the HRotate that read an input set, the
+    # copy back that read an output set
+    NB = max(1, args.e2e_sets)
     dev_in = [[(ctx.empty(L), ctx.empty(L)) for _ in range(C)] for _ in range(NB)]
     dev_out = [[(ctx.empty(L), ctx.empty(L)) for _ in range(C)] for _ in range(NB)]
     in_free = [[None] * C for _ in range(NB)]
@@ -1011,6 +1011,7 @@ def run_gpu(args, rank, world, local_rank):
                          "share_of_kernel_time": share},
             "kernels": by_class,
             "e2e": {"value": job_throughput(world, C, e2e_steps, e2e_ms), "unit": UNIT, "compute_streams": args.e2e_streams,
+                    "buffer_sets": NB,
                     "steps": e2e_steps, "h2d_bytes_per_step": bytes_io,
                     "d2h_bytes_per_step": bytes_io, "matches_device_result": ok},
         }
@@ -1102,6 +1103,8 @@ def main():
     ap.add_argument("--streams", type=int, default=8, help="CUDA streams the independent ciphertexts are spread over")
     ap.add_argument("--e2e-streams", type=int, default=4,
                     help="compute streams of the end-to-end measurement (host copies run on two more)")
+    ap.add_argument("--e2e-sets", type=int, default=3,
+                    help="sets of device input and output buffers the end-to-end steps rotate through")
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--oracle-procs", type=int, default=0,
                     help="oracle processes for the CPU baseline and the reference arm (0: one per host core)")
