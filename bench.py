@@ -1041,8 +1041,9 @@ def run_gpu(args, rank, world, local_rank):
 
 def run_profile_batch(args):
     """A small case for ncu: `--profile-batch n` batched KeySwitches at levels
-    uniform in {4..24} (the first n of the 64-entry workload), one shared key,
-    `--warmup` + `--steps` calls; nothing is printed but a completion line."""
+    uniform in {4..24} (the first n of the 64-entry workload), one shared key
+    (compressed, rows b only, with `--profile-compressed`), `--warmup` +
+    `--steps` calls; nothing is printed but a completion line."""
     import torch
 
     from paper_2112_06396_gb300 import ckks
@@ -1053,14 +1054,22 @@ def run_profile_batch(args):
     dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(ctx.device)
     levels = synth.uniform_ints(64, 4, 24, "batch/levels")[:args.profile_batch]
     s = dev(synth.ternary(N, "bench/batch/s"))
-    key = _keygen(ctx, torch, s, 0, "bench/batch/key")
+    seeds = None
+    if args.profile_compressed:
+        seed = synth.stream_seed("bench/batch/seed")
+        e_key = np.stack([synth.gaussian(N, f"bench/batch/key/e{j}") for j in range(DNUM)])
+        key = ctx.keygen_ksk_seeded(s, dev(e_key), seed, 0)
+        seeds = [seed] * len(levels)
+    else:
+        key = _keygen(ctx, torch, s, 0, "bench/batch/key")
     a = [dev(synth.uniform_residues(ctx.q[:ell], N, f"bench/batch/ct{i}")) for i, ell in enumerate(levels)]
     outs = [(ctx.empty(ell), ctx.empty(ell)) for ell in levels]
     ws = ctx.batch_workspace(levels)
     for _ in range(args.warmup + args.steps):
-        ctx.keyswitch_batch(a, None, levels, None, [key] * len(levels), outs=outs, ws=ws)
+        ctx.keyswitch_batch(a, None, levels, None, [key] * len(levels), outs=outs, ws=ws, seeds=seeds)
     torch.cuda.synchronize()
-    print(f"profile case done: {len(levels)} batched KeySwitches, levels {levels}", flush=True)
+    print(f"profile case done: {len(levels)} batched KeySwitches, levels {levels}, "
+          f"{'compressed' if seeds else 'full'} key", flush=True)
     return 0
 
 
@@ -1117,6 +1126,8 @@ def main():
                     help="run the headline's HRotates through the fused ModUp tail + KSKInnerProd kernel")
     ap.add_argument("--profile-batch", type=int, default=0,
                     help="profiling case: only run this many batched KeySwitches at uneven levels (no JSON line)")
+    ap.add_argument("--profile-compressed", action="store_true",
+                    help="with --profile-batch: the shared key compressed (rows b only, a from a seed)")
     args = ap.parse_args()
     global STREAMS
     STREAMS = args.streams
