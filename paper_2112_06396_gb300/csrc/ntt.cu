@@ -74,8 +74,6 @@ ntt_pass_kernel(const __grid_constant__ MAP map, const PrimeInfo *__restrict__ p
     constexpr int E = 1 << A;     // words per thread
     constexpr int R = 1 << LOGR;  // rows per column
     constexpr int RS = R + TPC;   // pass-C smem row stride (one pad word per E rows)
-    constexpr int NT = TPC * C;
-    constexpr int TILE = CONTIG ? C * RS : R * C;
     extern __shared__ u64 sm[];
 
     // every shift is a compile-time constant and every index fits 32 bits
@@ -105,15 +103,13 @@ ntt_pass_kernel(const __grid_constant__ MAP map, const PrimeInfo *__restrict__ p
     auto twi = [&](int sigma, int r) -> uint32_t {
         return (1u << (s0 + sigma)) + (prefix << sigma) + (uint32_t(r) >> (LOGR - sigma));
     };
-    // Pass S uses only the twiddles 1 .. R-1 of this prime: stage them in shared memory.
-    ulonglong2 *stw = reinterpret_cast<ulonglong2 *>(sm + TILE);
-    if (!CONTIG) {
-        for (int i = tid; i < R; i += NT) stw[i] = ld_keep(&tw[i]);
-        __syncthreads();
-    }
+    // Twiddles come through L1 (the prime's table stays in L2): pass S reads only
+    // entries 1 .. R-1, which every CTA of the prime on this SM shares.  (Staging
+    // them in shared memory cost 4 KB per CTA, which other kernels of a
+    // concurrent step need on the same SM.)
     auto TW = [&](int sigma, int r) -> ulonglong2 {
         const size_t i = twi(sigma, r);
-        return CONTIG ? ld_keep(&tw[i]) : stw[i];
+        return ld_keep(&tw[i]);
     };
     // Pass C: one thread asks the TMA unit to pull this CTA's twiddle ranges
     // (stage sigma uses C * 2^sigma consecutive entries) and, for the ModDown
@@ -546,7 +542,7 @@ cudaError_t launch_one_p(const MAP &m, int count, const ckks_ctx *ctx, cudaStrea
     constexpr int BASE = (CONTIG ? 64 : 128) * (CSEL == 2 ? 2 : 1) / (CSEL == 1 ? 2 : 1);
     constexpr int WANT = BASE / TPC > 0 ? BASE / TPC : 1;
     constexpr int C = WANT < (1 << OTHER) ? WANT : (1 << OTHER);
-    const size_t smem = CONTIG ? size_t(C) * (R + TPC) * 8 : size_t(R) * C * 8 + size_t(R) * 16;
+    const size_t smem = CONTIG ? size_t(C) * (R + TPC) * 8 : size_t(R) * C * 8;
     auto kern = ntt_pass_kernel<LOGN, L2, LOGR, A, C, INV, CONTIG, EPI, SMALLP, MAP>;
     if (set_attr) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     dim3 grid(count, (1 << OTHER) / C);
