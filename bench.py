@@ -813,6 +813,8 @@ def run_gpu(args, rank, world, local_rank):
         ctx.fuse_modup(True)
     if not args.no_tune:
         tune_choice, tune_times = ctx.autotune(limbs=128)  # NTT tile shapes and radix splits for this GPU (ckks_autotune)
+    # the step keeps `streams` HRotates running at once (ckks_concurrency_hint)
+    ctx.concurrency_hint(args.streams)
     torch.cuda.synchronize()
     C = args.batch
     items = make_workload(ctx, C, rank, torch)
@@ -897,6 +899,7 @@ def run_gpu(args, rank, world, local_rank):
     # fewer compute streams than the device-only run: the first ciphertexts
     # finish sooner, so their outputs start back over the host link earlier
     lanes_e = Lanes(ctx, args.e2e_streams, torch, ckks)
+    ctx.concurrency_hint(args.e2e_streams)
 
     def e2e_step(s):
         b = s % NB
@@ -981,6 +984,7 @@ def run_gpu(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded residues; keys from a seeded ternary secret)",
             "config": {**base_config(C), "parallelism": f"replicas x{world}", "fused_dataflow": bool(args.fuse),
+                       "concurrency_hint": args.streams,
                        "ntt_tile_shapes": {"choice": tune_choice, "ms": [round(t, 4) for t in tune_times],
                                            "legend": "[column pass <=48 limbs, column pass larger, block pass <=48, "
                                                      "block pass larger]: 0 default width, 1 half, 2 double; then "
@@ -1011,15 +1015,17 @@ def run_gpu(args, rank, world, local_rank):
                          "share_of_kernel_time": share},
             "kernels": by_class,
             "e2e": {"value": job_throughput(world, C, e2e_steps, e2e_ms), "unit": UNIT, "compute_streams": args.e2e_streams,
-                    "buffer_sets": NB,
+                    "buffer_sets": NB, "concurrency_hint": args.e2e_streams,
                     "steps": e2e_steps, "h2d_bytes_per_step": bytes_io,
                     "d2h_bytes_per_step": bytes_io, "matches_device_result": ok},
         }
         if not args.no_rows:
+            ctx.concurrency_hint(args.streams)  # the headline step again
             sweep = measure_rotation_sweep(ctx, items, lanes, torch)
             fused = measure_fused(ctx, ckks, items, lanes, torch)
             del items, lanes, lane1, lanes_e, dev_in, dev_out
             torch.cuda.empty_cache()
+            ctx.concurrency_hint(1)  # the other rows: calls alone or batched calls
             line["other_rows"] = measure_other_rows(ctx, ckks, torch)
             line["other_rows"]["rotation_sweep"] = sweep
             line["other_rows"]["fused_dataflow"] = fused

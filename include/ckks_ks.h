@@ -381,6 +381,18 @@ int ckks_bconv_select(ckks_ctx *ctx, int tensor_cores, int *available);
  * effect for later calls. */
 int ckks_fuse_select(ckks_ctx *ctx, int on, int *available);
 
+/* Concurrency hint (no counterpart in the paper): the number of operations
+ * the caller keeps running at once on this context (calls on that many
+ * streams, say).  The tensor-core basis conversion sizes its grid for a 1/n
+ * share of the SMs: fewer, longer CTAs per (group, chunk), which pay their
+ * fixed cost (tensor-memory allocation, B image, pipeline fill) less often
+ * while the other operations fill the SMs.  n = 1 (the default) sizes every
+ * launch for the GPU alone, the lowest latency for one call; on one GB300 the
+ * 8-stream HRotate step at N=2^16, ell=24 runs about 3% faster with n = 8
+ * and a call alone about 20% slower.  Same residues bit for bit.  n: 1 .. 64,
+ * CKKS_EINVAL outside.  Takes effect for later calls. */
+int ckks_concurrency_hint(ckks_ctx *ctx, int n);
+
 /* Streams of a batched call (no counterpart in the paper): the batched calls
  * (ckks_keyswitch_batch, ckks_mult_batch, ckks_newmult_batch, the serving
  * loop's batches) cut a batch of at least 4 * nstreams entries into nstreams

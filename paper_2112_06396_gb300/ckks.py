@@ -126,6 +126,7 @@ _SIGS = {
     "ckks_server_selftest_timeout": (_i, [_vp, ctypes.c_uint32]),
     "ckks_fuse_select": (_i, [_vp, _i, ctypes.POINTER(_i)]),
     "ckks_batch_streams": (_i, [_vp, _i]),
+    "ckks_concurrency_hint": (_i, [_vp, _i]),
     "ckks_butterfly_peak_sink_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
     "ckks_butterfly_peak": (_i, [_vp, _i, _vp, _vp, ctypes.POINTER(ctypes.c_float),
                                  ctypes.POINTER(ctypes.c_double)]),
@@ -370,6 +371,11 @@ class Context:
     def batch_streams(self, n):
         """Streams a batched call is split over (ckks_batch_streams, 1 .. 4)."""
         _check(lib().ckks_batch_streams(self._h, int(n)))
+
+    def concurrency_hint(self, n):
+        """Operations the caller runs at once on this context (ckks_concurrency_hint,
+        1 .. 64): the basis conversion sizes its grids for a 1/n share of the GPU."""
+        _check(lib().ckks_concurrency_hint(self._h, int(n)))
 
     def fuse_modup(self, on=True):
         """Run single KeySwitches and one-rotation HRotates through the fused

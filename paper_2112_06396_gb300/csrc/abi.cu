@@ -1825,6 +1825,12 @@ extern "C" int ckks_butterfly_peak(ckks_ctx *ctx, int rounds, void *sink, ckks_s
     return CKKS_OK;
 }
 
+extern "C" int ckks_concurrency_hint(ckks_ctx *ctx, int n) {
+    if (ctx == nullptr || n < 1 || n > 64) return CKKS_EINVAL;
+    ctx->concurrency = n;
+    return CKKS_OK;
+}
+
 extern "C" int ckks_batch_streams(ckks_ctx *ctx, int nstreams) {
     if (ctx == nullptr || nstreams < 1 || nstreams > ckks_ctx::kAux + 1) return CKKS_EINVAL;
     ctx->batch_split = nstreams;

@@ -456,11 +456,16 @@ static void launch_tc_kg(const ckks_ctx *ctx, const GMAP &gm, int ngroups, int c
     // one after the other, so the launch takes about waves * ceil(tiles / per)
     // tile times plus a fixed cost (B image, tensor memory, pipeline fill: about
     // two tiles) per wave; pick the count that minimises it (a batch has more
-    // (group, chunk) rows than SMs, a single operation a few)
+    // (group, chunk) rows than SMs, a single operation a few).  The waves are
+    // counted on the launch's share of the SMs: all of them for an operation
+    // alone, 1/n of them when the caller runs n operations at once
+    // (ckks_concurrency_hint), where fewer, longer CTAs pay the fixed cost less
+    // often and the other operations fill the SMs.
+    const int share = std::max(1, ctx->sms / std::max(1, ctx->concurrency));
     int per = 1;
     long best = -1;
     for (int c = 1; c <= std::min(tiles, 256); ++c) {
-        const long waves = (long(rows) * c + ctx->sms - 1) / ctx->sms;
+        const long waves = (long(rows) * c + share - 1) / share;
         const long cost = waves * ((tiles + c - 1) / c + 2);
         if (best < 0 || cost <= best) {  // ties: more CTAs
             best = cost;

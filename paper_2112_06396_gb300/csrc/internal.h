@@ -20,6 +20,7 @@ struct ckks_ctx {
     bool tc_on = true;                // use it when available (ckks_bconv_select can switch it off)
     bool tc_lazy;                     // its outputs stay below 8t without a final reduction
     bool fuse_on = false;             // single KeySwitch / one-rotation HRotate through modup_ip_kernel
+    int concurrency = 1;              // operations the caller runs at once (ckks_concurrency_hint)
                                       // (ckks_fuse_select)
     // Batched calls split over `batch_split` streams: the caller's and
     // batch_split - 1 of these, forked and joined by events.  One call at a

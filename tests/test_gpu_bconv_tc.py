@@ -132,6 +132,41 @@ def test_headline_shape(cfgB, r):
     assert ctx.poll_status()
 
 
+@pytest.mark.parametrize("hint", [8, 64])
+def test_concurrency_hint_headline(cfgB, hint):
+    """ckks_concurrency_hint sizes the tensor-core conversion for a 1/hint share
+    of the SMs (hint 64: one or two CTAs per group walking all 512 tiles): an
+    HRotate, a ModUp of every digit and a ModDown at N=2^16, ell=24 equal the
+    oracle, and a batch of four KeySwitches equals the same batch at hint 1."""
+    S = cfgB
+    P, ctx = S.P, S.ctx
+    g = 5
+    key = S.key(g, "gpu/tc/B/key1")[0]
+    a, b = S.ct(P.L, "gpu/tc/B/ct")
+    da, db, dk = dev(a), dev(b), dev(key)
+    levels = [24, 9, 17, 24]
+    xs = [dev(S.ct(ell, f"gpu/tc/B/hint/{i}")[0]) for i, ell in enumerate(levels)]
+    ref = [_h(o) for o in ctx.keyswitch_batch(xs, None, levels, None, [dk] * 4)]
+    x = dev(S.ct(P.L, "gpu/tc/B/hint/x")[0])
+    ctx.concurrency_hint(hint)
+    try:
+        oa, ob = _h(ctx.hrotate(da, db, P.L, [g], [dk])[0])
+        (ra, rb), = S.o.hrotate(P, P.L, a, b, [g], [key])
+        np.testing.assert_array_equal(oa, ra)
+        np.testing.assert_array_equal(ob, rb)
+        for j in range(P.beta(P.L)):
+            np.testing.assert_array_equal(host(ctx.modup(da, P.L, j)), S.o.modup(P, P.L, j, a))
+        ext = synth.uniform_residues(P.ext_primes(P.L), P.N, "gpu/tc/B/hint/ext")
+        np.testing.assert_array_equal(host(ctx.moddown(dev(ext), P.L)), S.o.moddown(P, P.L, ext))
+        got = [_h(o) for o in ctx.keyswitch_batch(xs, None, levels, None, [dk] * 4)]
+        for (ga, gb), (wa, wb) in zip(got, ref):
+            np.testing.assert_array_equal(ga, wa)
+            np.testing.assert_array_equal(gb, wb)
+        assert ctx.poll_status()
+    finally:
+        ctx.concurrency_hint(1)
+
+
 @pytest.fixture(scope="module")
 def cfg1(oracle_lib):
     return Setup(oracle_lib, 12, 6, 3, 2, 50)

@@ -4,7 +4,8 @@ The headline step is run exactly as bench.py times it: 16 HRotates (Alg. 4,
 r = 1, Galois element 5^(c+1) for ciphertext c) at N=2^16, ell=24, k=8,
 dnum=3 with 54-bit primes, one rotation key per ciphertext generated on the
 GPU, the ciphertexts spread over 8 streams with a workspace each, NTT tile
-shapes autotuned, the tensor-core basis conversion on.  Every step must give
+shapes autotuned, the concurrency hint at the stream count, the tensor-core
+basis conversion on.  Every step must give
 the same bits, and sampled ciphertexts (first, middle, last) must equal the
 oracle bit for bit, keys included.
 """
@@ -31,6 +32,7 @@ def test_bench_step_matches_oracle(oracle_lib):
     assert primes == o.gen_primes(bench.BITS, bench.LOGN, L + bench.K_SP)
     ctx = ckks.Context(bench.LOGN, primes[:L], primes[L:], bench.DNUM)
     ctx.autotune(limbs=128)
+    ctx.concurrency_hint(bench.STREAMS)
     items = bench.make_workload(ctx, 16, 0, torch)
     lanes = bench.Lanes(ctx, bench.STREAMS, torch, ckks)
 
@@ -81,6 +83,7 @@ def test_concurrent_streams_equal_one_at_a_time(choice):
     primes = ckks.ckks_gen_primes(bench.BITS, bench.LOGN, L + bench.K_SP)
     ctx = ckks.Context(bench.LOGN, primes[:L], primes[L:], bench.DNUM)
     ctx.tune_set(choice)
+    ctx.concurrency_hint(bench.STREAMS)
     items = bench.make_workload(ctx, 16, 0, torch)
     one = bench.Lanes(ctx, 1, torch, ckks)
     ref = []
