@@ -343,7 +343,9 @@ int ckks_keyswitch_batch_seeded(ckks_ctx *ctx, int n, const uint64_t *const *d_a
  * chosen, every split of a whole forward and of a whole inverse transform.
  * It synchronises the stream and keeps the fastest width per pass and launch
  * size (<= 48 limbs, larger) and the fastest split per direction and launch
- * size (ties to split 0) in the context.
+ * size in the context; the default width (split) is kept unless another is
+ * faster by 0.5% (3%), since closer timings are within the spread of launches
+ * timed alone.
  * choice (optional, 8 ints): [column pass small, column pass large, block pass
  * small, block pass large] with 0 = default, 1 = half width, 2 = double width,
  * then [forward small, forward large, inverse small, inverse large] splits in

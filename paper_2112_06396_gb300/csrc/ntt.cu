@@ -843,8 +843,11 @@ size_t bfly_peak_sink_words(const ckks_ctx *ctx) { return size_t(ctx->sms) * 4 *
 // place, values are transformed and transformed back), and keeps the fastest
 // per pass and batch-size class; then, with those widths, times whole forward
 // and whole inverse transforms at each radix split (0, -1, +1: pass C gets
-// floor(logN/2) + split stages) and keeps the fastest per direction and class
-// (ties to the default).  scratch: at least large * N words.  The choices go
+// floor(logN/2) + split stages) and keeps the fastest per direction and class.
+// The default shape is kept unless another is faster by a margin (0.5% for a
+// width, 3% for a split): closer timings are within the run-to-run spread of
+// launches timed alone, and inside a step of concurrent calls an unbalanced
+// split measured up to 12% slower.  scratch: at least large * N words.  The choices go
 // to ctx->ntt_csel and ctx->ntt_split; times_out (24 floats, ms per run) gets
 // the widths' times at [(pass * 2 + class) * 3 + width] and the splits' at
 // 12 + [(direction * 2 + class) * 3 + split + 1].
@@ -860,17 +863,19 @@ cudaError_t ntt_autotune(ckks_ctx *ctx, u64 *scratch, int small, int large, cuda
     const bool prof = ctx->prof_on;
     ctx->prof_on = false;
     err = cudaMemsetAsync(scratch, 0, size_t(large) * ctx->N * sizeof(u64), st);
-    // ms per run of `run` (one warm-up, then 5 timed runs)
+    // ms per run of `run` (two warm-up runs, then 10 timed runs)
+    constexpr int kReps = 10;
     auto timed = [&](auto run, float *ms) {
         cudaError_t e2 = run();
+        if (e2 == cudaSuccess) e2 = run();
         if (e2 != cudaSuccess) return e2;
         cudaEventRecord(e0, st);
-        for (int r = 0; r < 5 && e2 == cudaSuccess; ++r) e2 = run();
+        for (int r = 0; r < kReps && e2 == cudaSuccess; ++r) e2 = run();
         cudaEventRecord(e1, st);
         if (e2 == cudaSuccess) e2 = cudaEventSynchronize(e1);
         float t = 0.f;
         if (e2 == cudaSuccess) e2 = cudaEventElapsedTime(&t, e0, e1);
-        *ms = t / 5;
+        *ms = t / kReps;
         return e2;
     };
     const int counts[2] = {small, large};
@@ -885,9 +890,16 @@ cudaError_t ntt_autotune(ckks_ctx *ctx, u64 *scratch, int small, int large, cuda
         }
         m.e.mode = EPI_STORE;
         m.second = 1;
+        // the fastest option, unless it beats the default (option 0) by less than
+        // the margin
+        auto choose = [](const float *t, float margin) {
+            int f = 0;
+            for (int o = 1; o < 3; ++o)
+                if (t[o] < t[f]) f = o;
+            return t[f] < t[0] * (1.f - margin) ? f : 0;
+        };
         for (int contig = 0; contig < 2 && err == cudaSuccess; ++contig) {
-            float best = 1e30f;
-            int pick = 0;
+            float t[3] = {0.f, 0.f, 0.f};
             for (int cs = 0; cs < 3 && err == cudaSuccess; ++cs) {
                 auto run = [&]() {
                     cudaError_t e2 = contig ? dispatch<false, true, false>(m, count, ctx, st, false, 0, cs)
@@ -897,23 +909,16 @@ cudaError_t ntt_autotune(ckks_ctx *ctx, u64 *scratch, int small, int large, cuda
                                     : dispatch<true, false, false>(m, count, ctx, st, false, 0, cs);
                     return e2;
                 };
-                float ms = 0.f;
-                err = timed(run, &ms);
+                err = timed(run, &t[cs]);
                 if (err != cudaSuccess) break;
-                if (times_out) times_out[(contig * 2 + bucket) * 3 + cs] = ms;
-                if (ms < best) {
-                    best = ms;
-                    pick = cs;
-                }
+                if (times_out) times_out[(contig * 2 + bucket) * 3 + cs] = t[cs];
             }
-            ctx->ntt_csel[contig][bucket] = pick;
+            if (err == cudaSuccess) ctx->ntt_csel[contig][bucket] = choose(t, 0.005f);
         }
         for (int inv = 0; inv < 2 && err == cudaSuccess; ++inv) {
-            float best = 1e30f;
-            int pick = 0;
-            const int order[3] = {0, -1, 1};
+            float t[3] = {0.f, 0.f, 0.f};  // splits 0, -1, +1
             for (int o = 0; o < 3 && err == cudaSuccess; ++o) {
-                const int sp = order[o];
+                const int sp = o == 0 ? 0 : (o == 1 ? -1 : 1);
                 auto run = [&]() {
                     cudaError_t e2 = inv ? dispatch<true, true, false>(m, count, ctx, st, false, sp)
                                          : dispatch<false, false, false>(m, count, ctx, st, false, sp);
@@ -922,16 +927,14 @@ cudaError_t ntt_autotune(ckks_ctx *ctx, u64 *scratch, int small, int large, cuda
                                  : dispatch<false, true, false>(m, count, ctx, st, false, sp);
                     return e2;
                 };
-                float ms = 0.f;
-                err = timed(run, &ms);
+                err = timed(run, &t[o]);
                 if (err != cudaSuccess) break;
-                if (times_out) times_out[12 + (inv * 2 + bucket) * 3 + sp + 1] = ms;
-                if (ms < best) {
-                    best = ms;
-                    pick = sp;
-                }
+                if (times_out) times_out[12 + (inv * 2 + bucket) * 3 + sp + 1] = t[o];
             }
-            ctx->ntt_split[inv][bucket] = pick;
+            if (err == cudaSuccess) {
+                const int o = choose(t, 0.03f);
+                ctx->ntt_split[inv][bucket] = o == 0 ? 0 : (o == 1 ? -1 : 1);
+            }
         }
     }
     ctx->prof_on = prof;

@@ -84,14 +84,19 @@ def test_autotune_picks_a_timed_shape(cfg14):
     choice, times = cfg14.ctx.autotune(limbs=64)
     assert len(choice) == 8 and len(times) == 24
     assert all(0 <= c <= 2 for c in choice[:4]) and all(-1 <= c <= 1 for c in choice[4:])
+    # the fastest shape, unless it beats the default by less than the tuner's
+    # margin (0.5% for a width, 3% for a split); times are in the order
+    # [default, half, double] and [split -1, 0, +1]
     for i, c in enumerate(choice[:4]):
         row = times[i * 3:(i + 1) * 3]
         assert all(t > 0 for t in row)
-        assert row[c] == min(row)
+        fastest = min(range(3), key=lambda o: row[o])
+        assert c == (fastest if row[fastest] < row[0] * 0.995 else 0)
     for i, c in enumerate(choice[4:]):
         row = times[12 + i * 3:12 + (i + 1) * 3]
         assert all(t > 0 for t in row)
-        assert row[c + 1] == min(row)
+        fastest = min(range(3), key=lambda o: row[o])
+        assert c + 1 == (fastest if row[fastest] < row[1] * 0.97 else 1)
     with pytest.raises(ckks.CkksError):
         cfg14.ctx.tune_set([0, 3, 0, 0, 0, 0, 0, 0])
     with pytest.raises(ckks.CkksError):
