@@ -468,7 +468,9 @@ def measure_fused(ctx, ckks, items, lanes, torch, reps=10):
     for on in (False, True):
         ctx.fuse_modup(on)
         ms_step = _timed(torch, lambda: step(ctx, items, lanes), reps)
+        ctx.concurrency_hint(1)  # a call alone: grids sized for the whole GPU
         ms_one = _timed(torch, alone, 20)
+        ctx.concurrency_hint(len(lanes.streams))
         out["fused" if on else "default"] = {"ms_per_step": ms_step, "keyswitch_per_s": len(items) / ms_step * 1e3,
                                               "hrotate_alone_us": ms_one * 1e3,
                                               "launches_per_hrotate": 9 if on else 11}
@@ -852,6 +854,10 @@ def run_gpu(args, rank, world, local_rank):
     # ---- per-kernel-class device time on the launch stream (measurement hook),
     # one stream so that every bracketed launch runs alone
     lane1 = Lanes(ctx, 1, torch, ckks)
+    # one stream, every launch sized for the GPU alone (concurrency hint 1): the
+    # kernel classes' shares of a step, with no launch stretched by a grid sized
+    # for concurrent work
+    ctx.concurrency_hint(1)
     ctx.profile(True)
     ctx.profile_reset()
     prof_steps = max(1, min(args.steps, 10))
@@ -860,6 +866,7 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.synchronize()
     prof = ctx.profile_read()
     ctx.profile(False)
+    ctx.concurrency_hint(args.streams)
     launches_per_step = sum(v[1] for v in prof.values()) / prof_steps
     by_class = {k: {"ms_per_step": v[0] / prof_steps, "launches_per_step": v[1] / prof_steps} for k, v in prof.items()}
 
@@ -1006,8 +1013,8 @@ def run_gpu(args, rank, world, local_rank):
                                      "butterflies_per_step": bfly_per_step, "achieved": achieved_in_step,
                                      "frac": achieved_in_step / peak_gbfly,
                                      "frac_of_measured_peak": achieved_in_step / bfly_peak["gbfly_s"],
-                                     "how": "share of kernel time (one-stream hook) x ms_per_step of the timed "
-                                            "multi-stream region"},
+                                     "how": "share of kernel time (one-stream hook, launches sized for the GPU "
+                                            "alone) x ms_per_step of the timed multi-stream region"},
                          "traffic": None if tr is None else tr * limb_transforms / ntt_launch,
                          "algorithmic_bytes_per_launch": bytes_per_launch, "hbm_gbs_achieved": hbm_achieved,
                          "hbm_frac_of_measured": hbm_achieved / peaks["hbm_gbs"], "peak_src": peaks["src"],
