@@ -903,8 +903,8 @@ def run_gpu(args, rank, world, local_rank):
     # and its outputs leave as soon as it is done
     h2d, d2h = torch.cuda.Stream(), torch.cuda.Stream()
 
-    # fewer compute streams than the device-only run: the first ciphertexts
-    # finish sooner, so their outputs start back over the host link earlier
+    # compute streams of the end-to-end run (--e2e-streams; the device-only
+    # run's 8 by default)
     lanes_e = Lanes(ctx, args.e2e_streams, torch, ckks)
     ctx.concurrency_hint(args.e2e_streams)
 
@@ -1123,7 +1123,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--batch", type=int, default=16, help="ciphertexts (each with its own key) per step")
     ap.add_argument("--streams", type=int, default=8, help="CUDA streams the independent ciphertexts are spread over")
-    ap.add_argument("--e2e-streams", type=int, default=4,
+    ap.add_argument("--e2e-streams", type=int, default=8,
                     help="compute streams of the end-to-end measurement (host copies run on two more)")
     ap.add_argument("--e2e-sets", type=int, default=3,
                     help="sets of device input and output buffers the end-to-end steps rotate through")
