@@ -11,6 +11,7 @@
 #include "batch.cuh"
 #include "common.cuh"
 #include "internal.h"
+#include "launch_policy.h"
 #include "tc.cuh"
 
 #include <algorithm>
@@ -461,17 +462,7 @@ static void launch_tc_kg(const ckks_ctx *ctx, const GMAP &gm, int ngroups, int c
     // alone, 1/n of them when the caller runs n operations at once
     // (ckks_concurrency_hint), where fewer, longer CTAs pay the fixed cost less
     // often and the other operations fill the SMs.
-    const int share = std::max(1, ctx->sms / std::max(1, ctx->concurrency));
-    int per = 1;
-    long best = -1;
-    for (int c = 1; c <= std::min(tiles, 256); ++c) {
-        const long waves = (long(rows) * c + share - 1) / share;
-        const long cost = waves * ((tiles + c - 1) / c + 2);
-        if (best < 0 || cost <= best) {  // ties: more CTAs
-            best = cost;
-            per = c;
-        }
-    }
+    const int per = policy::tc_ctas_per_row(tiles, rows, policy::sm_share(ctx->sms, ctx->concurrency));
     const dim3 grid(static_cast<unsigned>(per), static_cast<unsigned>(rows));
     kern<<<grid, kTcThreads, smem, st>>>(gm, chunks, chunk, ctx->d_pinfo, ctx->logN, ctx->tc_lazy ? 1 : 0, status);
 }

@@ -10,6 +10,7 @@
 #include "batch.cuh"
 #include "common.cuh"
 #include "internal.h"
+#include "launch_policy.h"
 #include "prng.cuh"
 
 #include <algorithm>
@@ -423,17 +424,12 @@ cudaError_t launch_inner_prod_batch(const ckks_ctx *ctx, const KsBatchDesc &d, c
     // large as the launch allows while it keeps at least 8 CTAs per SM (fewer
     // key generations, enough CTAs to fill the GPU at small N); with more than
     // 4 digits the rows are not held in registers, so groups of one
-    const long per_entry = long(tiles) * (ctx->L + ctx->k);
-    const long fill = std::max(1L, per_entry * d.n / (8L * ctx->sms));
-    const int cap = ctx->dnum <= 4 ? int(std::min<long>(fill, kIpGroup)) : 1;
+    const int cap = policy::ip_group_cap(long(tiles) * (ctx->L + ctx->k), d.n, ctx->sms, ctx->dnum, kIpGroup);
     IpGroups G{};
-    G.start[0] = 0;
-    for (int c = 1; c <= d.n; ++c) {
-        const CtDesc &a = d.ct[G.start[G.n]];
-        const bool cut = c == d.n || c - G.start[G.n] >= cap || d.ct[c].key != a.key ||
-                         d.ct[c].compressed != a.compressed || (a.compressed && d.ct[c].seed != a.seed);
-        if (cut) G.start[++G.n] = uint8_t(c);
-    }
+    G.n = policy::ip_groups(d.n, cap, [&](int a, int c) {
+        const CtDesc &x = d.ct[a], &y = d.ct[c];
+        return y.key == x.key && y.compressed == x.compressed && (!x.compressed || y.seed == x.seed);
+    }, G.start);
     dim3 grid(unsigned(G.n), tiles, unsigned(ctx->L + ctx->k));
 #define CKKS_IPG(B) inner_prod_group_kernel<B><<<grid, threads, 0, st>>>(d, G, ctx->d_pinfo, ctx->d_Pmod)
     switch (ctx->dnum) {

@@ -21,6 +21,7 @@
 #include "batch.cuh"
 #include "common.cuh"
 #include "internal.h"
+#include "launch_policy.h"
 #include "prng.cuh"
 #include "tc.cuh"
 
@@ -890,14 +891,6 @@ cudaError_t ntt_autotune(ckks_ctx *ctx, u64 *scratch, int small, int large, cuda
         }
         m.e.mode = EPI_STORE;
         m.second = 1;
-        // the fastest option, unless it beats the default (option 0) by less than
-        // the margin
-        auto choose = [](const float *t, float margin) {
-            int f = 0;
-            for (int o = 1; o < 3; ++o)
-                if (t[o] < t[f]) f = o;
-            return t[f] < t[0] * (1.f - margin) ? f : 0;
-        };
         for (int contig = 0; contig < 2 && err == cudaSuccess; ++contig) {
             float t[3] = {0.f, 0.f, 0.f};
             for (int cs = 0; cs < 3 && err == cudaSuccess; ++cs) {
@@ -913,7 +906,7 @@ cudaError_t ntt_autotune(ckks_ctx *ctx, u64 *scratch, int small, int large, cuda
                 if (err != cudaSuccess) break;
                 if (times_out) times_out[(contig * 2 + bucket) * 3 + cs] = t[cs];
             }
-            if (err == cudaSuccess) ctx->ntt_csel[contig][bucket] = choose(t, 0.005f);
+            if (err == cudaSuccess) ctx->ntt_csel[contig][bucket] = policy::tune_choose(t, 0.005f);
         }
         for (int inv = 0; inv < 2 && err == cudaSuccess; ++inv) {
             float t[3] = {0.f, 0.f, 0.f};  // splits 0, -1, +1
@@ -932,7 +925,7 @@ cudaError_t ntt_autotune(ckks_ctx *ctx, u64 *scratch, int small, int large, cuda
                 if (times_out) times_out[12 + (inv * 2 + bucket) * 3 + sp + 1] = t[o];
             }
             if (err == cudaSuccess) {
-                const int o = choose(t, 0.03f);
+                const int o = policy::tune_choose(t, 0.03f);
                 ctx->ntt_split[inv][bucket] = o == 0 ? 0 : (o == 1 ? -1 : 1);
             }
         }
