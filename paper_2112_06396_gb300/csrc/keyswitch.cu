@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(256, 4) inner_prod_group_kernel(const __grid_c
     const PrimeInfo P = pinfo[pi];
     constexpr int KB = BMAX > 0 ? BMAX : 1;
     if constexpr (BMAX > 0) {
-        ulonglong2 ka[KB], kb[KB], dv[KB], nx[KB];
+        ulonglong2 ka[KB], kb[KB], dv[KB], nx[KB] = {};  // slots the next entry lacks stay 0
 #pragma unroll
         for (int j = 0; j < KB; j++) {
             if (j < bmax) {
@@ -295,6 +295,7 @@ __global__ void __launch_bounds__(256, 4) inner_prod_group_kernel(const __grid_c
         // the first owning entry's digits, in flight with the key rows
         int c = c0;
         while (c < c1 && !(pi >= d.L || pi < d.ct[c].ell)) ++c;
+        // entry e's digits at this prime into out[0 .. beta-1]
         auto fetch = [&](int e, ulonglong2 *out) {
             const CtDesc &ct = d.ct[e];
             const int ell = ct.ell, t = pi < d.L ? pi : ell + (pi - d.L);
