@@ -11,10 +11,10 @@
 // default L1 = ceil(logN/2); the autotuner may move one stage from one pass
 // to the other, the radix split).  Pass S runs the first L1 stages down the
 // columns (rows are 2^L2 words apart), pass C the last L2 stages inside each
-// contiguous block of 2^L2 words.  One CTA owns C columns (pass S) or C blocks (pass C); each
-// thread holds E = 2^A words in registers, runs A stages there, the tile is
-// transposed once through shared memory, and the remaining B = LOGR - A
-// stages run in registers again.  Global loads and stores are coalesced (the
+// contiguous block of 2^L2 words.  One CTA owns C columns (pass S) or C blocks
+// (pass C); each thread holds E = 2^A words in registers, runs A stages there,
+// the tile is transposed once through shared memory, and the remaining
+// B = LOGR - A stages run in registers again.  Global loads and stores are coalesced (the
 // contiguous-pass output is re-staged through shared memory).  Values stay in
 // [0, 4p) between stages (Harvey's lazy butterflies) and are fully reduced
 // only when the transform ends.
@@ -846,11 +846,12 @@ size_t bfly_peak_sink_words(const ckks_ctx *ctx) { return size_t(ctx->sms) * 4 *
 // and whole inverse transforms at each radix split (0, -1, +1: pass C gets
 // floor(logN/2) + split stages) and keeps the fastest per direction and class.
 // The default shape is kept unless another is faster by a margin (0.5% for a
-// width, 3% for a split): closer timings are within the run-to-run spread of
-// launches timed alone, and inside a step of concurrent calls an unbalanced
-// split measured up to 12% slower.  scratch: at least large * N words.  The choices go
-// to ctx->ntt_csel and ctx->ntt_split; times_out (24 floats, ms per run) gets
-// the widths' times at [(pass * 2 + class) * 3 + width] and the splits' at
+// width, 3% for a split; policy::tune_choose): closer timings are within the
+// run-to-run spread of launches timed alone, and inside a step of concurrent
+// calls an unbalanced split measured up to 12% slower.  scratch: at least
+// large * N words.  The choices go to ctx->ntt_csel and ctx->ntt_split;
+// times_out (24 floats, ms per run) gets the widths' times at
+// [(pass * 2 + class) * 3 + width] and the splits' at
 // 12 + [(direction * 2 + class) * 3 + split + 1].
 cudaError_t ntt_autotune(ckks_ctx *ctx, u64 *scratch, int small, int large, cudaStream_t st, float *times_out) {
     if (ctx->logN < 14 || !ctx->small_primes) return cudaSuccess;  // one shape only
