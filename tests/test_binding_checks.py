@@ -191,3 +191,23 @@ def test_server_requests_are_checked(env):
     srv.submit_keyswitch(5, poly(4), 4, 0, poly(4), poly(4))  # unknown context: left to the library
     assert rec.calls[-1] == "ckks_server_submit"
     srv.close()
+
+
+def test_tuning_and_scheduling_knobs(env):
+    """tune_set takes the 8-int choice that autotune returns (4 widths, 4 radix
+    splits) and rejects any other length before the library call; the
+    concurrency hint, batch streams and fusion switch reach the library."""
+    ctx, rec = env
+    ctx.tune_set([0, 2, 1, 0, -1, 0, 1, 0])
+    assert rec.calls[-1] == "ckks_tune_set"
+    for bad in ([0, 0, 0, 0], [0] * 9, []):
+        n = len(rec.calls)
+        with pytest.raises(ckks.CkksError):
+            ctx.tune_set(bad)
+        assert len(rec.calls) == n
+    ctx.concurrency_hint(8)
+    assert rec.calls[-1] == "ckks_concurrency_hint"
+    ctx.batch_streams(2)
+    assert rec.calls[-1] == "ckks_batch_streams"
+    ctx.fuse_modup(False)
+    assert rec.calls[-1] == "ckks_fuse_select"
